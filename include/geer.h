@@ -1,0 +1,166 @@
+/*
+ * geer.h -- C ABI of the GB300 GEER engine: epsilon-approximate pairwise
+ * effective resistance (Yang & Tang, "Efficient Estimation of Pairwise
+ * Effective Resistance", arXiv 2312.06123).
+ *
+ * The engine answers the query of Definition 2: for node pairs (s, t) of an
+ * undirected, unweighted, connected, non-bipartite graph (Section 2.1), it
+ * returns r'(s,t) with |r(s,t) - r'(s,t)| <= eps with probability >= 1-delta,
+ * r(s,t) being the effective resistance of Definition 1 / Eq. (1). It runs
+ * GEER (Algorithm 3): the truncation length l of Eq. (6), then SMM
+ * iterations (Algorithm 2) until the greedy switch of Eq. (17), then AMC
+ * (Algorithm 1) for the remaining l - l_b steps, r' = r_b + r_f.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: GER_OK (0) or a negative GER_ERR_* code; on error no
+ *     output is written and ger_last_error() describes the failure.
+ *   - No C++ exception crosses this boundary.
+ *   - Node ids are int32 in [0, n). Host pointers unless the name ends in
+ *     _dev (device pointers on the graph's device).
+ *   - A ger_graph handle is not thread-safe; separate handles are.
+ *   - Results are deterministic for a given (graph, lambda, options, seed,
+ *     query index in the batch, eps): the walk random numbers are keyed by
+ *     (seed, query index, batch, walk, step) with Philox4x32-10.
+ */
+#ifndef GEER_H
+#define GEER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define GER_OK                 0
+#define GER_ERR_INVALID       -1  /* bad argument (null pointer, eps <= 0, q < 0, ...) */
+#define GER_ERR_NODE_RANGE    -2  /* a query node outside [0, n) */
+#define GER_ERR_CSR           -3  /* CSR not canonical: unsorted, self-loop, duplicate, asymmetric */
+#define GER_ERR_DISCONNECTED  -4  /* graph not connected (Section 2.1 assumes it is) */
+#define GER_ERR_BIPARTITE     -5  /* bipartite graph: lambda_n = -1 and Eq. (6) is undefined */
+#define GER_ERR_OOM           -6  /* device or host allocation failed */
+#define GER_ERR_CUDA          -7  /* a CUDA runtime call failed */
+#define GER_ERR_TIMEOUT       -8  /* a bounded device-side wait gave up */
+#define GER_ERR_CAPACITY      -9  /* a query outgrew a workspace limit (see ger_options) */
+#define GER_ERR_NO_LAMBDA    -10  /* spectral bound neither computed nor set */
+
+/* precision of the SMM vectors (series and statistics are FP64 always) */
+#define GER_FP64 0
+#define GER_FP32 1
+
+/* switch policy between SMM and AMC */
+#define GER_SWITCH_RULE  0  /* Eq. (17): stop SMM once the support volume exceeds h(l - l_b) */
+#define GER_SWITCH_FIXED 2  /* run exactly min(fixed_ell_b, l) SMM iterations; fixed_ell_b < 0 means l */
+
+/* truncation length formula */
+#define GER_ELL_REFINED 0   /* Eq. (6), Theorem 1 */
+#define GER_ELL_PENG    1   /* Eq. (5), Peng et al. */
+
+typedef struct ger_graph ger_graph; /* opaque; owns the device copy of the graph */
+
+typedef struct ger_options {
+    double   delta;         /* failure probability delta (paper default 0.01) */
+    int32_t  tau;           /* maximum number of AMC batches tau (paper default 5), 1..20 */
+    int32_t  precision;     /* GER_FP32 (default) or GER_FP64 */
+    int32_t  per_query;     /* 0: all queries of the batch together; 1: one query at a time */
+    int32_t  switch_policy; /* GER_SWITCH_RULE (default) or GER_SWITCH_FIXED */
+    int32_t  fixed_ell_b;   /* used by GER_SWITCH_FIXED */
+    int32_t  ell_formula;   /* GER_ELL_REFINED (default) or GER_ELL_PENG */
+    uint64_t seed;          /* walk RNG seed */
+    int64_t  sparse_cap;    /* max SMM push volume per query step on the sparse path (0: default) */
+} ger_options;
+
+/* Per-query statistics (all optional outputs). */
+typedef struct ger_query_stats {
+    int32_t  ell;        /* truncation length l, Eq. (6) (or Eq. (5)) */
+    int32_t  ell_b;      /* SMM iterations run (Algorithm 3) */
+    int32_t  batches;    /* AMC batches run (Algorithm 1), 0 if l_f = 0 */
+    int32_t  flags;      /* reserved, 0 */
+    int64_t  eta0;       /* walk pairs in the first AMC batch */
+    int64_t  walks;      /* walk pairs over all batches */
+    int64_t  walk_steps; /* single-walk steps over all batches */
+    double   r_b;        /* SMM part, Eq. (16) r*_b */
+    double   r_f;        /* AMC estimate of Eq. (16) r*_f */
+    double   psi;        /* Eq. (9) at l_f = l - l_b */
+    double   f_last;     /* empirical Bernstein error of the last batch, Eq. (7) */
+    double   volume;     /* sum_{V_s} d + sum_{V_t} d after the last SMM iteration, Eq. (17) */
+    double   h;          /* h(l - l_b) at the last SMM iteration */
+    uint64_t checksum;   /* wrapping sum over all walks of a hash of (endpoint, walk, batch) */
+} ger_query_stats;
+
+/* Fill *opt with the defaults: delta 0.01, tau 5, FP32, batched, rule, refined l, seed 3. */
+void ger_default_options(ger_options *opt);
+
+/*
+ * Load a graph given as canonical CSR: row_ptr[0..n] (int64, row_ptr[0] == 0),
+ * col_idx[0..row_ptr[n]) with every neighbour list sorted ascending, no
+ * self-loops, no duplicates, and every edge stored in both rows (the
+ * undirected, unweighted graph of Section 2.1). The graph must be connected
+ * and non-bipartite (Section 2.1). The arrays are copied to `device`; the
+ * caller keeps ownership of its inputs. On success *out owns the device copy
+ * until ger_free().
+ * Errors: GER_ERR_INVALID, GER_ERR_CSR, GER_ERR_DISCONNECTED,
+ * GER_ERR_BIPARTITE, GER_ERR_OOM, GER_ERR_CUDA.
+ */
+int ger_load_csr(int64_t n, const int64_t *row_ptr, const int32_t *col_idx, int device,
+                 ger_graph **out);
+
+/* Release the handle and every device buffer it owns. Null is a no-op. */
+void ger_free(ger_graph *g);
+
+/* Graph size: n and the number of stored (directed) entries 2m. */
+int ger_graph_size(const ger_graph *g, int64_t *n, int64_t *nnz);
+
+/*
+ * Spectral bound lambda = max(|lambda_2|, |lambda_n|) of P = D^-1 A, the
+ * once-per-graph preprocessing of Section 3.1 that Eq. (6) needs. Computed on
+ * the device (FP64 Lanczos with full re-orthogonalisation on D^-1/2 A D^-1/2,
+ * deflated by its top eigenvector) on first call and cached; lam2 and lamn
+ * (nullable) receive lambda_2 and lambda_n.
+ */
+int ger_spectral_bound(ger_graph *g, double *lambda, double *lam2, double *lamn);
+
+/* Inject lambda (0 <= lambda < 1) instead of computing it (e.g. to share one
+   value between runs). */
+int ger_set_spectral_bound(ger_graph *g, double lambda);
+
+/*
+ * Answer q queries r_out[i] ~ r(s[i], t[i]) at error eps (Algorithm 3).
+ * s, t: q node ids each (host); r_out: q doubles (host); stats: q entries
+ * (host, nullable); opt: nullable (defaults). s[i] == t[i] gives exactly 0
+ * (Definition 1). The query's index i keys its walk random numbers.
+ * Errors: GER_ERR_INVALID, GER_ERR_NODE_RANGE, GER_ERR_NO_LAMBDA (cannot
+ * happen: lambda is computed on demand), GER_ERR_CAPACITY, GER_ERR_OOM,
+ * GER_ERR_CUDA.
+ */
+int ger_query_batch(ger_graph *g, int64_t q, const int32_t *s, const int32_t *t, double eps,
+                    const ger_options *opt, double *r_out, ger_query_stats *stats);
+
+/* As ger_query_batch, with a per-query error eps[i] (host). */
+int ger_query_batch_eps(ger_graph *g, int64_t q, const int32_t *s, const int32_t *t,
+                        const double *eps, const ger_options *opt, double *r_out,
+                        ger_query_stats *stats);
+
+/*
+ * Device-resident variant: s_dev, t_dev, eps_dev (q entries each), r_dev (q
+ * doubles) and stats_dev (q ger_query_stats, nullable) live on the graph's
+ * device; work is issued on `stream` (a cudaStream_t, null = default
+ * stream) and the call returns once it has completed. Node ids are checked
+ * on the device; an out-of-range id yields GER_ERR_NODE_RANGE.
+ */
+int ger_query_batch_dev(ger_graph *g, int64_t q, const int32_t *s_dev, const int32_t *t_dev,
+                        const double *eps_dev, const ger_options *opt, double *r_dev,
+                        ger_query_stats *stats_dev, void *stream);
+
+/* Thread-local description of the last error of this thread. */
+const char *ger_last_error(void);
+
+/* Number of kernels this library has launched in this process (every node
+   of a replayed CUDA graph counts). */
+int64_t ger_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GEER_H */
