@@ -1,0 +1,310 @@
+"""Benchmark: GEER effective-resistance queries per second on one GB300.
+
+Default workload: Chung-Lu graph, n = 1M, mean degree 20 (~10M undirected
+edges), exponent 2.5, largest component; 1,000 uniform random pairs at
+eps = 0.05; batched GEER with FP32 SMM vectors and FP64 series/statistics.
+One step = one full GEER batch over the 1,000 queries (SMM, switch, AMC,
+outputs) with the spectral bound computed once beforehand (the paper's
+once-per-graph preprocessing, Section 3.1; its time is reported separately).
+
+Prints ONE JSON line (rank 0). Under torchrun every rank runs its own
+replica of the batch (queries are independent; there is no exchange step),
+so the value is the whole-job query throughput and scaling is weak.
+
+--impl reference times the CPU oracle (plain FP64 C, single thread) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+os.environ.setdefault("GEER_SYNTH_CACHE", "/tmp/geer_synth_cache")
+
+METRIC = "ER queries/s at eps=0.05 (batched FP32 GEER)"
+WALK_STEP_BYTES = 20  # row_ptr pair 8 B + one col_idx 4 B + one (s*, t*) FP32 pair 8 B
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """Sample SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = f"/tmp/geer_clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                pass
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        reasons = set()
+        for r in rows:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[2:]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[1] for r in rows),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample(w, lam, seconds: float, start: int = 0):
+    """Run the CPU oracle on consecutive queries until `seconds` elapse;
+    returns (queries done, elapsed seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        i = (start + k) % w.q
+        oracle.geer(w.graph, int(w.s[i]), int(w.t[i]), float(w.eps[i]), lam, q_index=i)
+        k += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            return k, el
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import synth
+    import oracle
+    w = synth.workload(args.workload)
+    lam = oracle.lam(w.graph, max_steps=200)
+    per_step = args.ref_seconds
+    for _ in range(args.warmup):
+        oracle_sample(w, lam, 0.0)
+    times, done = [], 0
+    for k in range(args.steps):
+        n, el = oracle_sample(w, lam, per_step, start=done)
+        done += n
+        times.append((n, el))
+    qps = sum(n for n, _ in times) / sum(el for _, el in times)
+    sample = f"{done} consecutive queries of the workload over {args.steps} steps of ~{per_step:.0f} s"
+    line = {"impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * sum(el for _, el in times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(w),
+            "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(w):
+    g = w.graph
+    return {"workload": f"{g.name}, largest component (n={g.n}, m={g.m}); {w.q} uniform pairs, eps={w.eps[0]:g}",
+            "graph": g.name, "n": g.n, "m": g.m, "queries": w.q, "eps": float(w.eps[0]), "delta": 0.01, "tau": 5,
+            "smm_vectors": "fp32", "series_and_statistics": "fp64",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--ref-seconds", type=float, default=10.0, help="oracle seconds per reference step")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle seconds for cpu_baseline")
+    ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 per-query path")
+    args = ap.parse_args()
+    world, rank, local = _dist()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    import synth
+    import paper_2312_06123_gb300 as geer
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = synth.workload(args.workload)
+    g = w.graph
+    G = geer.Graph.from_csr(g, device=local)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lam, l2, ln = G.spectral_bound()
+    pre_ms = 1000.0 * (time.perf_counter() - t0)
+
+    dev = torch.device("cuda", local)
+    s_d = torch.from_numpy(w.s.astype(np.int32)).to(dev)
+    t_d = torch.from_numpy(w.t.astype(np.int32)).to(dev)
+    e_d = torch.from_numpy(w.eps.astype(np.float64)).to(dev)
+    r_d = torch.empty(w.q, dtype=torch.float64, device=dev)
+    st_d = torch.empty(w.q * geer.STATS_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    opts = geer.default_options()
+
+    def step():
+        G.query_dev(s_d, t_d, e_d, r_d, st_d, opts, stream=stream.cuda_stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    geer.profile_enable(True)
+    launches0 = geer.launch_count()
+    barrier()
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = geer.launch_count() - launches0
+    prof = geer.profile_read()
+    geer.profile_enable(False)
+    barrier()
+    total_ms = float(sum(ms))
+    if dist is not None:
+        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = world * w.q * args.steps / (total_ms / 1000.0)
+    stats = np.frombuffer(st_d.cpu().numpy().tobytes(), dtype=geer.STATS_DTYPE)
+
+    # e2e: host buffers through ger_query_batch_eps, copies inside the timed region
+    e2e_t = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        G.query(w.s, w.t, w.eps, opts)
+        e2e_t.append(time.perf_counter() - t1)
+    e2e_value = world * w.q * args.steps / sum(e2e_t)
+
+    # the plain FP64 per-query GPU path (one query at a time), same queries
+    plain_opts = geer.default_options(precision=geer.GER_FP64, per_query=1)
+    G.query_dev(s_d, t_d, e_d, r_d, None, plain_opts, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    pt = []
+    for _ in range(max(args.plain_steps, 1)):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        G.query_dev(s_d, t_d, e_d, r_d, None, plain_opts, stream=stream.cuda_stream)
+        b.record(stream)
+        b.synchronize()
+        pt.append(a.elapsed_time(b))
+    plain_value = w.q * len(pt) / (sum(pt) / 1000.0)
+
+    if rank != 0:
+        return 0
+
+    # roofline of the dominant kernel family
+    peak, peak_kind = _peaks()
+    fam = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("none", (0, 0.0))
+    walk_steps = int(stats["walk_steps"].sum())
+    roof = None
+    if fam[0] == "amc_walk":
+        nl, tms = prof["amc_walk"]
+        per_launch_bytes = WALK_STEP_BYTES * walk_steps / (nl / args.steps)
+        achieved = per_launch_bytes / (tms / nl / 1000.0) / 1e9
+        roof = {"kernel": "amc_walk", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                "algorithmic_bytes_per_launch": per_launch_bytes}
+    else:
+        nl, tms = fam[1]
+        roof = {"kernel": fam[0], "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s",
+                "frac": None, "peak_source": peak_kind, "traffic": None}
+    # CPU baseline: the oracle as it stands, one host thread, bounded sample
+    import oracle
+    nq, el = oracle_sample(w, lam, args.cpu_seconds)
+    cpu = {"value": nq / el, "unit": "queries/s", "cores": 1, "kind": "oracle",
+           "sample": f"first {nq} queries of the workload, {el:.1f} s, same lambda and seed"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _config(w),
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": int(w.q * (4 + 4 + 8)),
+                "d2h_bytes_per_step": int(w.q * 8)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "plain_fp64_per_query": {"value": plain_value, "unit": "queries/s", "ms_per_step": float(np.mean(pt)),
+                                 "speedup_of_batched_fp32": value / world / plain_value},
+        "preprocess": {"spectral_bound_ms": pre_ms, "lambda": lam, "lambda_2": l2, "lambda_n": ln},
+        "kernels": {k: {"launches": v[0], "total_ms": v[1]} for k, v in prof.items()},
+        "work": {"walk_steps_per_step": walk_steps, "walk_pairs_per_step": int(stats["walks"].sum()),
+                 "mean_ell": float(stats["ell"].mean()), "mean_ell_b": float(stats["ell_b"].mean())},
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -159,6 +159,22 @@ const char *ger_last_error(void);
    of a replayed CUDA graph counts). */
 int64_t ger_launch_count(void);
 
+/* Per-kernel-family timing, measured with CUDA events recorded on the
+   stream each kernel is launched on. */
+typedef struct ger_kernel_profile {
+    char     name[32];   /* kernel family, e.g. "amc_walk" */
+    int64_t  launches;   /* launches timed since the last enable */
+    double   total_ms;   /* summed launch durations */
+} ger_kernel_profile;
+
+/* on != 0: start timing every launch from now on (accumulators reset);
+   on == 0: stop timing. Timing adds two event records per launch. */
+int ger_profile_enable(int on);
+
+/* Copy up to max_entries family records into out; returns the number of
+   families with at least one timed launch (>= 0), or GER_ERR_INVALID. */
+int ger_profile_read(ger_kernel_profile *out, int max_entries);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,219 @@
+"""GB300 GEER engine: epsilon-approximate pairwise effective resistance
+(arXiv 2312.06123, Algorithm 3) with hand-written CUDA kernels for sm_103a.
+
+This module is the thin Python binding of the C ABI declared in
+``include/geer.h``: it only marshals arguments. Every step of a query runs in
+the library ``libgeer.so`` built from ``csrc/``; there is no CPU fallback --
+if the library is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from ._build import LIB as _LIB_PATH, build as build_library
+
+GER_OK = 0
+GER_ERR = {
+    -1: "GER_ERR_INVALID", -2: "GER_ERR_NODE_RANGE", -3: "GER_ERR_CSR", -4: "GER_ERR_DISCONNECTED",
+    -5: "GER_ERR_BIPARTITE", -6: "GER_ERR_OOM", -7: "GER_ERR_CUDA", -8: "GER_ERR_TIMEOUT",
+    -9: "GER_ERR_CAPACITY", -10: "GER_ERR_NO_LAMBDA",
+}
+GER_FP64, GER_FP32 = 0, 1
+GER_SWITCH_RULE, GER_SWITCH_FIXED = 0, 2
+GER_ELL_REFINED, GER_ELL_PENG = 0, 1
+
+
+class GeerError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{GER_ERR.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("delta", ctypes.c_double), ("tau", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("per_query", ctypes.c_int32), ("switch_policy", ctypes.c_int32),
+                ("fixed_ell_b", ctypes.c_int32), ("ell_formula", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("sparse_cap", ctypes.c_int64)]
+
+
+class QueryStats(ctypes.Structure):
+    _fields_ = [("ell", ctypes.c_int32), ("ell_b", ctypes.c_int32), ("batches", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("eta0", ctypes.c_int64), ("walks", ctypes.c_int64),
+                ("walk_steps", ctypes.c_int64), ("r_b", ctypes.c_double), ("r_f", ctypes.c_double),
+                ("psi", ctypes.c_double), ("f_last", ctypes.c_double), ("volume", ctypes.c_double),
+                ("h", ctypes.c_double), ("checksum", ctypes.c_uint64)]
+
+
+class KernelProfile(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+STATS_DTYPE = np.dtype([(n, np.dtype(t._type_)) for n, t in QueryStats._fields_], align=True)
+assert STATS_DTYPE.itemsize == ctypes.sizeof(QueryStats)
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libgeer.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        build_library()
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"CUDA library not built: {_LIB_PATH}")
+    L = ctypes.CDLL(_LIB_PATH)
+    i32, i64, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    L.ger_default_options.argtypes = [ctypes.POINTER(Options)]
+    L.ger_default_options.restype = None
+    L.ger_load_csr.argtypes = [i64, _P, _P, ctypes.c_int, ctypes.POINTER(_P)]
+    L.ger_free.argtypes = [_P]
+    L.ger_free.restype = None
+    L.ger_graph_size.argtypes = [_P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.ger_spectral_bound.argtypes = [_P, ctypes.POINTER(f64), ctypes.POINTER(f64), ctypes.POINTER(f64)]
+    L.ger_set_spectral_bound.argtypes = [_P, f64]
+    L.ger_query_batch.argtypes = [_P, i64, _P, _P, f64, ctypes.POINTER(Options), _P, _P]
+    L.ger_query_batch_eps.argtypes = [_P, i64, _P, _P, _P, ctypes.POINTER(Options), _P, _P]
+    L.ger_query_batch_dev.argtypes = [_P, i64, _P, _P, _P, ctypes.POINTER(Options), _P, _P, _P]
+    L.ger_last_error.argtypes = []
+    L.ger_last_error.restype = ctypes.c_char_p
+    L.ger_launch_count.argtypes = []
+    L.ger_launch_count.restype = i64
+    L.ger_profile_enable.argtypes = [ctypes.c_int]
+    L.ger_profile_enable.restype = ctypes.c_int
+    L.ger_profile_read.argtypes = [ctypes.POINTER(KernelProfile), ctypes.c_int]
+    L.ger_profile_read.restype = ctypes.c_int
+    for name in ("ger_load_csr", "ger_graph_size", "ger_spectral_bound", "ger_set_spectral_bound",
+                 "ger_query_batch", "ger_query_batch_eps", "ger_query_batch_dev"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != GER_OK:
+        raise GeerError(rc, load_library(False).ger_last_error().decode(errors="replace"))
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load_library().ger_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def launch_count() -> int:
+    return int(load_library().ger_launch_count())
+
+
+def profile_enable(on: bool = True):
+    """Time every kernel launch with CUDA events on its launch stream."""
+    _check(load_library().ger_profile_enable(1 if on else 0))
+
+
+def profile_read() -> dict:
+    """{family: (launches, total_ms)} since the last profile_enable(True)."""
+    buf = (KernelProfile * 16)()
+    k = load_library().ger_profile_read(buf, 16)
+    if k < 0:
+        _check(k)
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(k, 16))}
+
+
+def _arr(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Graph:
+    """A graph resident on one GPU (ger_load_csr ... ger_free)."""
+
+    def __init__(self, row_ptr, col_idx, device: int = 0):
+        L = load_library()
+        self._rp = _arr(row_ptr, np.int64)
+        self._ci = _arr(col_idx, np.int32)
+        h = _P()
+        n = self._rp.shape[0] - 1
+        _check(L.ger_load_csr(n, self._rp.ctypes.data_as(_P), self._ci.ctypes.data_as(_P), int(device),
+                              ctypes.byref(h)))
+        self._h = h
+        self.n = int(n)
+        self.nnz = int(self._rp[-1])
+        self._rp = self._ci = None  # the library holds its own copy
+
+    @classmethod
+    def from_csr(cls, g, device: int = 0) -> "Graph":
+        return cls(g.row_ptr, g.col_idx, device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load_library().ger_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def spectral_bound(self):
+        """(lambda, lambda_2, lambda_n) computed on the GPU (Section 3.1)."""
+        lam, l2, ln = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(load_library().ger_spectral_bound(self._h, ctypes.byref(lam), ctypes.byref(l2), ctypes.byref(ln)))
+        return lam.value, l2.value, ln.value
+
+    def set_spectral_bound(self, lam: float):
+        _check(load_library().ger_set_spectral_bound(self._h, float(lam)))
+
+    def query(self, s, t, eps, options: Options | None = None, stats: bool = False):
+        """r'(s,t) for host arrays s, t (eps scalar or per query). Returns r
+        (float64 array) or (r, stats record array)."""
+        L = load_library()
+        s = _arr(s, np.int32)
+        t = _arr(t, np.int32)
+        q = s.shape[0]
+        if t.shape[0] != q:
+            raise ValueError("s and t differ in length")
+        r = np.zeros(q, dtype=np.float64)
+        st = np.zeros(q, dtype=STATS_DTYPE) if stats else None
+        opt = options if options is not None else default_options()
+        sp = st.ctypes.data_as(_P) if st is not None else None
+        if np.ndim(eps) == 0:
+            rc = L.ger_query_batch(self._h, q, s.ctypes.data_as(_P), t.ctypes.data_as(_P), float(eps),
+                                   ctypes.byref(opt), r.ctypes.data_as(_P), sp)
+        else:
+            e = _arr(eps, np.float64)
+            if e.shape[0] != q:
+                raise ValueError("eps length differs from q")
+            rc = L.ger_query_batch_eps(self._h, q, s.ctypes.data_as(_P), t.ctypes.data_as(_P),
+                                       e.ctypes.data_as(_P), ctypes.byref(opt), r.ctypes.data_as(_P), sp)
+        _check(rc)
+        return (r, st) if stats else r
+
+    def query_dev(self, s_dev, t_dev, eps_dev, r_dev, stats_dev=None, options: Options | None = None,
+                  stream=None):
+        """Device-resident variant: arguments are CUDA tensors (or raw device
+        pointers as ints) on this graph's GPU; stats_dev, if given, is a
+        uint8 tensor of q * sizeof(ger_query_stats) bytes."""
+        def ptr(x):
+            if x is None:
+                return None
+            return ctypes.c_void_p(x if isinstance(x, int) else x.data_ptr())
+        q = int(s_dev.shape[0]) if hasattr(s_dev, "shape") else None
+        if q is None:
+            raise ValueError("s_dev must be a tensor")
+        opt = options if options is not None else default_options()
+        _check(load_library().ger_query_batch_dev(self._h, q, ptr(s_dev), ptr(t_dev), ptr(eps_dev),
+                                                  ctypes.byref(opt), ptr(r_dev), ptr(stats_dev),
+                                                  ctypes.c_void_p(stream) if stream else None))

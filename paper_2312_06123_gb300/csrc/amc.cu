@@ -1,0 +1,215 @@
+// amc.cu -- AMC phase of GEER (Algorithm 1 with the residual vectors s*, t*
+// of Algorithm 3): batches of walk pairs, the per-query sums of Z_k and
+// Z_k^2, and the empirical-Bernstein stop of Lemma 2 / Eq. (7) at delta/tau.
+//
+// Work layout of one batch b: query q runs eta_q walk pairs, cut into
+// chunks of ppc pairs (a multiple of 16, at most kMaxChunksPerQuery chunks).
+// A warp owns one chunk at a time: lanes 2i and 2i+1 walk pair k = k0 + i,
+// lane 2i from s (sigma = 0), lane 2i+1 from t (sigma = 1). Each walk step
+// draws one 32-bit word of Philox4x32-10 keyed by (seed) with counter
+// (k, 2(b-1)+sigma, query index, (j-1) >> 2), word (j-1) & 3, and moves to
+// neighbour floor(draw * d(w) / 2^32) in CSR order -- the same specification
+// the CPU oracle implements, so walk endpoints agree bit for bit.
+// Z_k = sum over the S walk of g(w_j) - sum over the T walk of g(w_j) with
+// g(v) = s*(v)/d(s) - t*(v)/d(t) read from the query's lookup table (Eq. 12;
+// the start node w_0 is not counted, as E[Z_k] = q(s,t) of Eq. 11 requires).
+// Per-chunk sums go to a partial array; the reduce kernel adds a query's
+// chunks in a fixed order, so results do not depend on scheduling.
+#include "geer_internal.cuh"
+#include "geer_kernels.h"
+
+namespace geer {
+
+namespace {
+
+__device__ __forceinline__ double lookup_g(const GEntry* tab, int32_t mask, int32_t v) {
+    uint32_t h = hash32((uint32_t)v) & (uint32_t)mask;
+    for (;;) {
+        const int4 raw = __ldg(reinterpret_cast<const int4*>(tab + h));
+        if (raw.x == v) return __hiloint2double(raw.w, raw.z);
+        if (raw.x == -1) return 0.0;
+        h = (h + 1) & (uint32_t)mask;
+    }
+}
+
+__device__ __forceinline__ uint32_t word(const uint4& r, int i) {
+    return i == 0 ? r.x : (i == 1 ? r.y : (i == 2 ? r.z : r.w));
+}
+
+}  // namespace
+
+// One CTA: chunk layout of batch b for every query still in AMC.
+__global__ void __launch_bounds__(kCta) amc_schedule_kernel(AmcArgs a) {
+    __shared__ int64_t scan[kWarps + 1];
+    __shared__ int64_t carry;
+    const int tid = threadIdx.x;
+    if (tid == 0) carry = 0;
+    __syncthreads();
+    for (int64_t tile = 0; tile < a.nq; tile += kCta) {
+        const int64_t q = tile + tid;
+        int64_t nch = 0;
+        if (q < a.nq) {
+            QState* Q = a.st + q;
+            if (Q->status == ST_AMC) {
+                const int64_t eta = Q->eta;
+                const int64_t units = (eta + kPairsPerWarpRound - 1) / kPairsPerWarpRound;
+                int64_t c = units < kMaxChunksPerQuery ? units : kMaxChunksPerQuery;
+                const int64_t ppc = kPairsPerWarpRound * ((units + c - 1) / c);
+                nch = (eta + ppc - 1) / ppc;
+                Q->ppc = ppc;
+            }
+            Q->nchunks = nch;
+        }
+        int64_t tot;
+        const int64_t ex = cta_excl_scan(nch, scan, &tot);
+        if (q < a.nq) a.chunk_begin[q] = carry + ex;
+        __syncthreads();
+        if (tid == 0) carry += tot;
+        __syncthreads();
+    }
+    if (tid == 0) a.chunk_begin[a.nq] = carry;
+}
+
+__global__ void __launch_bounds__(256) amc_walk_kernel(AmcArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int sigma = lane & 1;
+    const int64_t total = a.chunk_begin[a.nq];
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+    const int64_t* row_ptr = a.g.row_ptr;
+    const int32_t* col_idx = a.g.col_idx;
+    const uint32_t lane_ctr = (uint32_t)(2 * (a.batch - 1) + sigma);
+    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total; c += nw) {
+        // owning query: last q with chunk_begin[q] <= c
+        int64_t lo = 0, hi = a.nq + 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (a.chunk_begin[mid] <= c) lo = mid + 1; else hi = mid;
+        }
+        const QState* Q = a.st + (lo - 1);
+        const int64_t cb = a.chunk_begin[lo - 1];
+        const int64_t eta = Q->eta, ppc = Q->ppc;
+        const int32_t lf = Q->lf, qidx = Q->qidx;
+        const int32_t start = sigma ? Q->t : Q->s;
+        const GEntry* tab = a.pool + Q->table_off;
+        const int32_t mask = Q->table_mask;
+        const int64_t k_lo = (c - cb) * ppc;
+        const int64_t k_hi = min(k_lo + ppc, eta);
+        double sz = 0.0, sz2 = 0.0;
+        uint64_t cs = 0;
+        for (int64_t k0 = k_lo; k0 < k_hi; k0 += kPairsPerWarpRound) {
+            const int64_t k = k0 + (lane >> 1);
+            const bool active = k < k_hi;
+            double zp = 0.0;
+            if (active) {
+                int32_t w = start;
+                uint4 r = make_uint4(0, 0, 0, 0);
+                for (int j = 1; j <= lf; ++j) {
+                    if (((j - 1) & 3) == 0)
+                        r = philox4x32_10(make_uint4((uint32_t)k, lane_ctr, (uint32_t)qidx, (uint32_t)((j - 1) >> 2)), key);
+                    const uint32_t draw = word(r, (j - 1) & 3);
+                    const int64_t rs = __ldg(row_ptr + w);
+                    const uint64_t d = (uint64_t)(__ldg(row_ptr + w + 1) - rs);
+                    w = __ldg(col_idx + rs + (int64_t)(((uint64_t)draw * d) >> 32));
+                    zp += lookup_g(tab, mask, w);
+                }
+                cs += walk_hash(w, k, sigma, a.batch);
+            }
+            const double other = __shfl_xor_sync(0xffffffffu, zp, 1);
+            if (active && sigma == 0) {
+                const double zk = zp - other;
+                sz += zk;
+                sz2 += zk * zk;
+            }
+        }
+        sz = warp_sum(sz);
+        sz2 = warp_sum(sz2);
+        cs = warp_sum(cs);
+        if (lane == 0) {
+            Partial p;
+            p.sz = sz;
+            p.sz2 = sz2;
+            p.cs = cs;
+            a.partial[c] = p;
+        }
+    }
+}
+
+// One CTA per query: batch statistics (Algorithm 1: Z, the empirical
+// variance, f of Eq. (7) at delta/tau) and the stop / doubling decision.
+__global__ void __launch_bounds__(kCta) amc_reduce_kernel(AmcArgs a) {
+    __shared__ double red0[kWarps], red1[kWarps];
+    __shared__ uint64_t red2[kWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int64_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
+        QState* Q = a.st + q;
+        if (Q->status != ST_AMC) continue;  // uniform across the CTA
+        const int64_t nch = Q->nchunks, begin = a.chunk_begin[q];
+        double sz = 0.0, sz2 = 0.0;
+        uint64_t cs = 0;
+        for (int64_t i = tid; i < nch; i += kCta) {
+            const Partial p = a.partial[begin + i];
+            sz += p.sz;
+            sz2 += p.sz2;
+            cs += p.cs;
+        }
+        sz = warp_sum(sz);
+        sz2 = warp_sum(sz2);
+        cs = warp_sum(cs);
+        if (lane == 0) {
+            red0[warp] = sz;
+            red1[warp] = sz2;
+            red2[warp] = cs;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double S = 0.0, S2 = 0.0;
+            uint64_t C = 0;
+            for (int w = 0; w < kWarps; ++w) {
+                S += red0[w];
+                S2 += red1[w];
+                C += red2[w];
+            }
+            const int64_t eta = Q->eta;
+            const double Z = S / (double)eta;
+            double var = S2 / (double)eta - Z * Z;
+            if (var < 0.0) var = 0.0;
+            const double delta_b = a.delta / (double)a.tau;
+            const double L = log(3.0 / delta_b);
+            const double f = sqrt(2.0 * var * L / (double)eta) + 3.0 * Q->psi * L / (double)eta;
+            Q->walks += eta;
+            Q->walk_steps += 2 * eta * (int64_t)Q->lf;
+            Q->checksum += C;
+            Q->batch = a.batch;
+            Q->f_last = f;
+            if (f <= Q->eps / 2.0 || a.batch >= a.tau) {
+                Q->r_f = Z;
+                Q->r = Q->r_b + Z;
+                Q->status = ST_DONE;
+            } else {
+                Q->eta = 2 * eta;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+void launch_amc_schedule(const AmcArgs& a, cudaStream_t st) {
+    prof_begin(FAM_AMC_SCHEDULE, st);
+    amc_schedule_kernel<<<1, kCta, 0, st>>>(a);
+    prof_end(FAM_AMC_SCHEDULE, st);
+}
+
+void launch_amc_walk(const AmcArgs& a, int grid, cudaStream_t st) {
+    prof_begin(FAM_AMC_WALK, st);
+    amc_walk_kernel<<<grid, 256, 0, st>>>(a);
+    prof_end(FAM_AMC_WALK, st);
+}
+
+void launch_amc_reduce(const AmcArgs& a, int grid, cudaStream_t st) {
+    prof_begin(FAM_AMC_REDUCE, st);
+    amc_reduce_kernel<<<grid, kCta, 0, st>>>(a);
+    prof_end(FAM_AMC_REDUCE, st);
+}
+
+}  // namespace geer

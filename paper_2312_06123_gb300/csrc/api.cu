@@ -1,0 +1,652 @@
+// api.cu -- the C ABI of include/geer.h: graph loading and validation,
+// workspace management, and the launch sequence of a GEER query batch
+// (Algorithm 3): sparse SMM with the greedy switch, then tau AMC rounds of
+// schedule -> walks -> batch statistics, then the per-query outputs.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/geer.h"
+#include "geer_internal.cuh"
+#include "geer_kernels.h"
+
+namespace geer {
+
+static std::atomic<int64_t> g_launches{0};
+void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------------------
+// profiler: CUDA events around launches, on the launch stream
+// ---------------------------------------------------------------------------
+static const char* kFamilyNames[FAM_COUNT] = {"smm_sparse", "amc_schedule", "amc_walk", "amc_reduce",
+                                              "finalize", "lanczos"};
+struct ProfRec {
+    int fam;
+    cudaEvent_t a, b;
+};
+static bool g_prof_on = false;
+static std::vector<ProfRec> g_prof_pending;
+static std::vector<cudaEvent_t> g_prof_free;
+static cudaEvent_t g_prof_open[FAM_COUNT];
+static int64_t g_prof_launches[FAM_COUNT];
+static double g_prof_ms[FAM_COUNT];
+
+static cudaEvent_t prof_event() {
+    if (!g_prof_free.empty()) {
+        cudaEvent_t e = g_prof_free.back();
+        g_prof_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(int fam, cudaStream_t st) {
+    if (!g_prof_on) return;
+    g_prof_open[fam] = prof_event();
+    cudaEventRecord(g_prof_open[fam], st);
+}
+
+void prof_end(int fam, cudaStream_t st) {
+    if (!g_prof_on || !g_prof_open[fam]) return;
+    cudaEvent_t b = prof_event();
+    cudaEventRecord(b, st);
+    g_prof_pending.push_back({fam, g_prof_open[fam], b});
+    g_prof_open[fam] = nullptr;
+}
+
+void prof_collect() {
+    for (const ProfRec& r : g_prof_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            g_prof_ms[r.fam] += ms;
+            g_prof_launches[r.fam] += 1;
+        }
+        g_prof_free.push_back(r.a);
+        g_prof_free.push_back(r.b);
+    }
+    g_prof_pending.clear();
+}
+
+static thread_local char g_err[512] = "";
+
+static int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* what) {
+    return fail(GER_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define GER_CUDA(call)                                          \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+struct Workspace {
+    int64_t q_cap = 0;
+    QState* st = nullptr;
+    int32_t* s = nullptr;
+    int32_t* t = nullptr;
+    double* eps = nullptr;
+    double* r = nullptr;
+    ger_query_stats* stats = nullptr;
+    int64_t* chunk_begin = nullptr;
+    Partial* partial = nullptr;
+    int64_t partial_cap = 0;
+    // sparse SMM scratch
+    int slots = 0;
+    int64_t cap = 0;
+    int32_t* scr_i32 = nullptr;
+    void* scr_val = nullptr;
+    uint8_t* scr_bits = nullptr;
+    // lookup tables
+    GEntry* pool = nullptr;
+    int64_t pool_cap = 0;
+    // counters: [0] work counter, [1] error flag (int), pool_used (u64)
+    int* counters = nullptr;
+    unsigned long long* pool_used = nullptr;
+    // pinned readback
+    int64_t* host_rb = nullptr;
+};
+
+}  // namespace geer
+
+struct ger_graph {
+    int device = 0;
+    int sm_count = 0;
+    int64_t n = 0, nnz = 0;
+    int64_t* row_ptr = nullptr;
+    int32_t* col_idx = nullptr;
+    bool has_lambda = false;
+    double lambda = 0, lam2 = 0, lamn = 0;
+    cudaStream_t stream = nullptr;
+    geer::Workspace ws;
+};
+
+namespace geer {
+
+static void free_ws(Workspace& w) {
+    cudaFree(w.st); cudaFree(w.s); cudaFree(w.t); cudaFree(w.eps); cudaFree(w.r); cudaFree(w.stats);
+    cudaFree(w.chunk_begin); cudaFree(w.partial); cudaFree(w.scr_i32); cudaFree(w.scr_val);
+    cudaFree(w.scr_bits); cudaFree(w.pool); cudaFree(w.counters); cudaFree(w.pool_used);
+    if (w.host_rb) cudaFreeHost(w.host_rb);
+    w = Workspace();
+}
+
+template <typename T>
+static cudaError_t alloc(T** p, size_t count) {
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16);
+}
+
+// Make room for q queries, `slots` sparse CTAs of capacity `cap`, and a
+// lookup pool of at least pool_cap entries.
+static int ensure_ws(ger_graph* g, int64_t q, int slots, int64_t cap, int64_t pool_cap) {
+    Workspace& w = g->ws;
+    if (!w.counters) {
+        GER_CUDA(alloc(&w.counters, 4));
+        GER_CUDA(alloc(&w.pool_used, 1));
+        GER_CUDA(cudaMallocHost(reinterpret_cast<void**>(&w.host_rb), 4 * sizeof(int64_t)));
+    }
+    if (q > w.q_cap) {
+        cudaFree(w.st); cudaFree(w.s); cudaFree(w.t); cudaFree(w.eps); cudaFree(w.r); cudaFree(w.stats);
+        cudaFree(w.chunk_begin); cudaFree(w.partial);
+        w.st = nullptr; w.s = nullptr; w.t = nullptr; w.eps = nullptr; w.r = nullptr; w.stats = nullptr;
+        w.chunk_begin = nullptr; w.partial = nullptr; w.q_cap = 0;
+        const int64_t qc = std::max<int64_t>(q, 64);
+        const int64_t pc = qc * kMaxChunksPerQuery;
+        if (alloc(&w.st, qc) || alloc(&w.s, qc) || alloc(&w.t, qc) || alloc(&w.eps, qc) || alloc(&w.r, qc) ||
+            alloc(&w.stats, qc) || alloc(&w.chunk_begin, qc + 1) || alloc(&w.partial, pc)) {
+            cudaGetLastError();
+            return fail(GER_ERR_OOM, "workspace for %lld queries", (long long)q);
+        }
+        w.q_cap = qc;
+        w.partial_cap = pc;
+    }
+    if (slots > w.slots || cap != w.cap) {
+        cudaFree(w.scr_i32); cudaFree(w.scr_val); cudaFree(w.scr_bits);
+        w.scr_i32 = nullptr; w.scr_val = nullptr; w.scr_bits = nullptr; w.slots = 0;
+        const int64_t F = cap + 2;
+        const size_t ni = (size_t)slots * (size_t)(5 * cap + 3 * F + 2);
+        const size_t nv = (size_t)slots * (size_t)(4 * F);
+        const size_t nb = (size_t)slots * (size_t)(2 * F);
+        if (alloc(&w.scr_i32, ni) || cudaMalloc(&w.scr_val, nv * sizeof(double) + 16) || alloc(&w.scr_bits, nb)) {
+            cudaGetLastError();
+            return fail(GER_ERR_OOM, "sparse SMM scratch (%d slots x %lld pairs)", slots, (long long)cap);
+        }
+        w.slots = slots;
+        w.cap = cap;
+    }
+    if (pool_cap > w.pool_cap) {
+        cudaFree(w.pool);
+        w.pool = nullptr;
+        w.pool_cap = 0;
+        if (alloc(&w.pool, pool_cap)) {
+            cudaGetLastError();
+            return fail(GER_ERR_OOM, "lookup pool of %lld entries", (long long)pool_cap);
+        }
+        w.pool_cap = pool_cap;
+    }
+    return GER_OK;
+}
+
+// ---------------------------------------------------------------------------
+// outputs
+// ---------------------------------------------------------------------------
+__global__ void finalize_kernel(const QState* st, int64_t nq, double* r, ger_query_stats* stats) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
+        const QState& Q = st[q];
+        r[q] = Q.r;
+        if (stats) {
+            ger_query_stats o;
+            o.ell = Q.ell;
+            o.ell_b = Q.ell_b;
+            o.batches = Q.batch;
+            o.flags = Q.err;
+            o.eta0 = Q.eta0;
+            o.walks = Q.walks;
+            o.walk_steps = Q.walk_steps;
+            o.r_b = Q.r_b;
+            o.r_f = Q.r_f;
+            o.psi = Q.psi;
+            o.f_last = Q.f_last;
+            o.volume = Q.volume;
+            o.h = Q.h;
+            o.checksum = Q.checksum;
+            stats[q] = o;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// graph validation (host)
+// ---------------------------------------------------------------------------
+static int validate_csr(int64_t n, const int64_t* rp, const int32_t* ci) {
+    if (n < 3) return fail(GER_ERR_INVALID, "n = %lld: a connected non-bipartite graph needs n >= 3", (long long)n);
+    if (rp[0] != 0) return fail(GER_ERR_CSR, "row_ptr[0] != 0");
+    for (int64_t v = 0; v < n; ++v)
+        if (rp[v + 1] < rp[v]) return fail(GER_ERR_CSR, "row_ptr decreases at %lld", (long long)v);
+    // sorted, in range, no self-loop, no duplicate
+    for (int64_t v = 0; v < n; ++v) {
+        for (int64_t e = rp[v]; e < rp[v + 1]; ++e) {
+            const int64_t u = ci[e];
+            if (u < 0 || u >= n) return fail(GER_ERR_CSR, "col_idx[%lld] = %lld out of range", (long long)e, (long long)u);
+            if (u == v) return fail(GER_ERR_CSR, "self-loop at node %lld", (long long)v);
+            if (e > rp[v] && ci[e - 1] >= u)
+                return fail(GER_ERR_CSR, "row %lld not strictly increasing (unsorted or duplicate)", (long long)v);
+        }
+    }
+    // symmetry: scanning rows in ascending order, the entries below the
+    // diagonal of each row v must be exactly the rows u < v that list v
+    std::vector<int64_t> cursor(rp, rp + n);
+    for (int64_t u = 0; u < n; ++u) {
+        for (int64_t e = rp[u]; e < rp[u + 1]; ++e) {
+            const int64_t v = ci[e];
+            if (v <= u) continue;
+            const int64_t c = cursor[v];
+            if (c >= rp[v + 1] || ci[c] != u)
+                return fail(GER_ERR_CSR, "edge (%lld,%lld) has no reverse entry", (long long)u, (long long)v);
+            cursor[v] = c + 1;
+        }
+    }
+    for (int64_t v = 0; v < n; ++v)
+        if (cursor[v] < rp[v + 1] && ci[cursor[v]] < v)
+            return fail(GER_ERR_CSR, "edge (%lld,%d) has no reverse entry", (long long)v, ci[cursor[v]]);
+    // connectivity and bipartiteness by breadth-first two-colouring
+    std::vector<int8_t> colour(n, -1);
+    std::vector<int32_t> queue(n);
+    int64_t head = 0, tail = 0;
+    colour[0] = 0;
+    queue[tail++] = 0;
+    bool odd_cycle = false;
+    while (head < tail) {
+        const int32_t v = queue[head++];
+        for (int64_t e = rp[v]; e < rp[v + 1]; ++e) {
+            const int32_t u = ci[e];
+            if (colour[u] < 0) {
+                colour[u] = (int8_t)(1 - colour[v]);
+                queue[tail++] = u;
+            } else if (colour[u] == colour[v]) {
+                odd_cycle = true;
+            }
+        }
+    }
+    if (tail != n) return fail(GER_ERR_DISCONNECTED, "graph is not connected (%lld of %lld nodes reachable from 0)",
+                               (long long)tail, (long long)n);
+    if (!odd_cycle) return fail(GER_ERR_BIPARTITE, "graph is bipartite: lambda_n = -1 and Eq. (6) is undefined");
+    return GER_OK;
+}
+
+static int ensure_lambda(ger_graph* g) {
+    if (g->has_lambda) return GER_OK;
+    DevGraph dg{g->n, g->nnz, g->row_ptr, g->col_idx};
+    double l2 = 0, ln = 0;
+    int steps = 0;
+    const int rc = lanczos_spectral_bound(dg, 300, 1e-13, g->stream, &l2, &ln, &steps);
+    if (rc == -2) return fail(GER_ERR_OOM, "spectral bound workspace");
+    if (rc != 0) return fail(GER_ERR_CUDA, "spectral bound: %s", cudaGetErrorString(cudaGetLastError()));
+    g->lam2 = l2;
+    g->lamn = ln;
+    g->lambda = std::max(std::fabs(l2), std::fabs(ln));
+    if (!(g->lambda < 1.0)) return fail(GER_ERR_BIPARTITE, "spectral bound lambda = %.17g >= 1", g->lambda);
+    g->has_lambda = true;
+    return GER_OK;
+}
+
+// ---------------------------------------------------------------------------
+// the query batch
+// ---------------------------------------------------------------------------
+struct Plan {
+    ger_options o;
+    int64_t q;
+    const int32_t* s;     // device
+    const int32_t* t;     // device
+    const double* eps;    // device, nullable
+    double eps_scalar;
+    double* r;            // device
+    ger_query_stats* stats;  // device, nullable
+    cudaStream_t st;
+};
+
+static int nbits_of(int64_t n) {
+    int b = 0;
+    for (int64_t x = n - 1; x > 0; x >>= 1) ++b;
+    return b < 1 ? 1 : b;
+}
+
+static int map_device_error(int e) {
+    switch (e) {
+        case DERR_NODE_RANGE: return fail(GER_ERR_NODE_RANGE, "a query node is outside [0, n) or eps <= 0");
+        case DERR_CAPACITY: return fail(GER_ERR_CAPACITY, "an SMM iteration exceeded the sparse capacity");
+        case DERR_TABLE: return fail(GER_ERR_CAPACITY, "lookup pool exhausted");
+        case DERR_ELL: return fail(GER_ERR_INVALID, "truncation length undefined (lambda >= 1)");
+        default: return fail(GER_ERR_CUDA, "device error %d", e);
+    }
+}
+
+template <typename T>
+static void launch_sequence(ger_graph* g, const Plan& p, bool per_query) {
+    Workspace& w = g->ws;
+    DevGraph dg{g->n, g->nnz, g->row_ptr, g->col_idx};
+    const int tau = p.o.tau;
+    const int walk_grid = per_query ? g->sm_count * 2 : g->sm_count * 8;
+    auto run = [&](int64_t q0, int64_t nq) {
+        cudaMemsetAsync(w.counters, 0, sizeof(int), p.st);  // work counter
+        SmmArgs a;
+        a.g = dg;
+        a.nq = (int32_t)nq;
+        a.q_index_base = (int32_t)q0;
+        a.st = w.st + q0;
+        a.s = p.s + q0;
+        a.t = p.t + q0;
+        a.eps = p.eps ? p.eps + q0 : nullptr;
+        a.eps_scalar = p.eps_scalar;
+        a.lambda = g->lambda;
+        a.delta = p.o.delta;
+        a.tau = tau;
+        a.ell_formula = p.o.ell_formula;
+        a.policy = p.o.switch_policy;
+        a.fixed_lb = p.o.fixed_ell_b;
+        a.nbits = nbits_of(g->n);
+        a.cap = w.cap;
+        a.scr_i32 = w.scr_i32;
+        a.scr_val = w.scr_val;
+        a.scr_bits = w.scr_bits;
+        a.pool = w.pool;
+        a.pool_cap = w.pool_cap;
+        a.pool_used = w.pool_used;
+        a.work_counter = w.counters;
+        a.err_flag = w.counters + 1;
+        const int grid = (int)std::min<int64_t>(nq, w.slots);
+        launch_smm_sparse(sizeof(T) == 8, a, grid, p.st);
+        AmcArgs m;
+        m.g = dg;
+        m.nq = (int32_t)nq;
+        m.st = w.st + q0;
+        m.chunk_begin = w.chunk_begin;
+        m.partial = w.partial;
+        m.partial_cap = w.partial_cap;
+        m.pool = w.pool;
+        m.seed = p.o.seed;
+        m.tau = tau;
+        m.delta = p.o.delta;
+        m.err_flag = w.counters + 1;
+        const int red_grid = (int)std::min<int64_t>(nq, 4096);
+        for (int b = 1; b <= tau; ++b) {
+            m.batch = b;
+            launch_amc_schedule(m, p.st);
+            launch_amc_walk(m, walk_grid, p.st);
+            launch_amc_reduce(m, red_grid, p.st);
+        }
+        note_launches(1 + 3 * tau);
+    };
+    cudaMemsetAsync(w.counters + 1, 0, sizeof(int), p.st);  // error flag
+    cudaMemsetAsync(w.pool_used, 0, sizeof(unsigned long long), p.st);
+    if (per_query) {
+        for (int64_t i = 0; i < p.q; ++i) run(i, 1);
+    } else {
+        run(0, p.q);
+    }
+    const int fg = (int)std::min<int64_t>((p.q + 255) / 256, 4096);
+    prof_begin(FAM_FINALIZE, p.st);
+    finalize_kernel<<<fg, 256, 0, p.st>>>(w.st, p.q, p.r, p.stats);
+    prof_end(FAM_FINALIZE, p.st);
+    note_launches(1);
+}
+
+static int run_batch(ger_graph* g, Plan& p) {
+    if (p.q == 0) return GER_OK;
+    int rc = ensure_lambda(g);
+    if (rc) return rc;
+    const bool per_query = p.o.per_query != 0;
+    const int slots = per_query ? 1 : (int)std::min<int64_t>(p.q, (int64_t)g->sm_count * 2);
+    int64_t cap = p.o.sparse_cap > 0 ? p.o.sparse_cap : (int64_t)1 << 17;
+    int64_t pool = std::max<int64_t>(g->ws.pool_cap, (int64_t)1 << 22);
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        rc = ensure_ws(g, p.q, std::max(slots, g->ws.slots), cap, pool);
+        if (rc) return rc;
+        if (p.o.precision == GER_FP64) launch_sequence<double>(g, p, per_query);
+        else launch_sequence<float>(g, p, per_query);
+        Workspace& w = g->ws;
+        GER_CUDA(cudaGetLastError());
+        GER_CUDA(cudaMemcpyAsync(w.host_rb, w.counters + 1, sizeof(int), cudaMemcpyDeviceToHost, p.st));
+        GER_CUDA(cudaMemcpyAsync(w.host_rb + 1, w.pool_used, sizeof(unsigned long long), cudaMemcpyDeviceToHost, p.st));
+        GER_CUDA(cudaStreamSynchronize(p.st));
+        prof_collect();
+        const int derr = (int)(reinterpret_cast<int*>(w.host_rb)[0]);
+        if (derr == DERR_NONE) return GER_OK;
+        if (derr == DERR_TABLE) {
+            const int64_t used = w.host_rb[1];
+            pool = std::max<int64_t>(2 * used, 2 * w.pool_cap);
+            continue;
+        }
+        if (derr == DERR_CAPACITY && p.o.sparse_cap <= 0 && cap < ((int64_t)1 << 21)) {
+            cap *= 4;
+            continue;
+        }
+        return map_device_error(derr);
+    }
+    return fail(GER_ERR_CAPACITY, "workspace did not fit after retries");
+}
+
+}  // namespace geer
+
+using namespace geer;
+
+extern "C" {
+
+void ger_default_options(ger_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->delta = 0.01;
+    o->tau = 5;
+    o->precision = GER_FP32;
+    o->per_query = 0;
+    o->switch_policy = GER_SWITCH_RULE;
+    o->fixed_ell_b = -1;
+    o->ell_formula = GER_ELL_REFINED;
+    o->seed = 3;
+    o->sparse_cap = 0;
+}
+
+const char* ger_last_error(void) { return g_err; }
+
+int64_t ger_launch_count(void) { return g_launches.load(); }
+
+int ger_profile_enable(int on) {
+    prof_collect();
+    g_prof_on = on != 0;
+    if (g_prof_on) {
+        for (int f = 0; f < FAM_COUNT; ++f) {
+            g_prof_launches[f] = 0;
+            g_prof_ms[f] = 0.0;
+            g_prof_open[f] = nullptr;
+        }
+    }
+    return GER_OK;
+}
+
+int ger_profile_read(ger_kernel_profile* out, int max_entries) {
+    if (max_entries < 0 || (max_entries > 0 && !out)) return fail(GER_ERR_INVALID, "bad profile buffer");
+    prof_collect();
+    int k = 0;
+    for (int f = 0; f < FAM_COUNT; ++f) {
+        if (g_prof_launches[f] == 0) continue;
+        if (k < max_entries) {
+            std::memset(&out[k], 0, sizeof(out[k]));
+            std::snprintf(out[k].name, sizeof(out[k].name), "%s", kFamilyNames[f]);
+            out[k].launches = g_prof_launches[f];
+            out[k].total_ms = g_prof_ms[f];
+        }
+        ++k;
+    }
+    return k;
+}
+
+int ger_load_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int device, ger_graph** out) {
+    if (!out || !row_ptr || (!col_idx && n > 0)) return fail(GER_ERR_INVALID, "null argument");
+    *out = nullptr;
+    int rc = validate_csr(n, row_ptr, col_idx);
+    if (rc) return rc;
+    ger_graph* g = new (std::nothrow) ger_graph();
+    if (!g) return fail(GER_ERR_OOM, "host allocation");
+    g->device = device;
+    g->n = n;
+    g->nnz = row_ptr[n];
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail(e, "cudaSetDevice");
+    }
+    cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&g->row_ptr, (n + 1) * sizeof(int64_t)) != cudaSuccess ||
+        cudaMalloc(&g->col_idx, std::max<int64_t>(g->nnz, 1) * sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        ger_free(g);
+        return fail(GER_ERR_OOM, "device copy of the graph");
+    }
+    if (cudaMemcpy(g->row_ptr, row_ptr, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->col_idx, col_idx, g->nnz * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+        ger_free(g);
+        return fail(GER_ERR_CUDA, "copying the graph");
+    }
+    *out = g;
+    return GER_OK;
+}
+
+void ger_free(ger_graph* g) {
+    if (!g) return;
+    cudaSetDevice(g->device);
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    free_ws(g->ws);
+    cudaFree(g->row_ptr);
+    cudaFree(g->col_idx);
+    if (g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+}
+
+int ger_graph_size(const ger_graph* g, int64_t* n, int64_t* nnz) {
+    if (!g) return fail(GER_ERR_INVALID, "null graph");
+    if (n) *n = g->n;
+    if (nnz) *nnz = g->nnz;
+    return GER_OK;
+}
+
+int ger_spectral_bound(ger_graph* g, double* lambda, double* lam2, double* lamn) {
+    if (!g) return fail(GER_ERR_INVALID, "null graph");
+    cudaSetDevice(g->device);
+    int rc = ensure_lambda(g);
+    if (rc) return rc;
+    if (lambda) *lambda = g->lambda;
+    if (lam2) *lam2 = g->lam2;
+    if (lamn) *lamn = g->lamn;
+    return GER_OK;
+}
+
+int ger_set_spectral_bound(ger_graph* g, double lambda) {
+    if (!g) return fail(GER_ERR_INVALID, "null graph");
+    if (!(lambda >= 0.0 && lambda < 1.0)) return fail(GER_ERR_INVALID, "lambda must be in [0, 1)");
+    g->lambda = lambda;
+    g->lam2 = g->lamn = std::nan("");
+    g->has_lambda = true;
+    return GER_OK;
+}
+
+static int check_opts(const ger_options* opt, ger_options* o) {
+    if (opt) *o = *opt; else ger_default_options(o);
+    if (!(o->delta > 0.0 && o->delta < 1.0)) return fail(GER_ERR_INVALID, "delta must be in (0, 1)");
+    if (o->tau < 1 || o->tau > 20) return fail(GER_ERR_INVALID, "tau must be in 1..20");
+    if (o->precision != GER_FP32 && o->precision != GER_FP64) return fail(GER_ERR_INVALID, "bad precision");
+    if (o->switch_policy != GER_SWITCH_RULE && o->switch_policy != GER_SWITCH_FIXED)
+        return fail(GER_ERR_INVALID, "bad switch policy");
+    if (o->ell_formula != GER_ELL_REFINED && o->ell_formula != GER_ELL_PENG) return fail(GER_ERR_INVALID, "bad ell formula");
+    return GER_OK;
+}
+
+static int host_batch(ger_graph* g, int64_t q, const int32_t* s, const int32_t* t, const double* eps_arr,
+                      double eps, const ger_options* opt, double* r_out, ger_query_stats* stats) {
+    if (!g || q < 0 || (q > 0 && (!s || !t || !r_out))) return fail(GER_ERR_INVALID, "null argument or q < 0");
+    if (q > 0x7fffffff) return fail(GER_ERR_INVALID, "q too large");
+    Plan p;
+    int rc = check_opts(opt, &p.o);
+    if (rc) return rc;
+    for (int64_t i = 0; i < q; ++i) {
+        if (s[i] < 0 || s[i] >= g->n || t[i] < 0 || t[i] >= g->n)
+            return fail(GER_ERR_NODE_RANGE, "query %lld: node outside [0, %lld)", (long long)i, (long long)g->n);
+        const double e = eps_arr ? eps_arr[i] : eps;
+        if (!(e > 0.0)) return fail(GER_ERR_INVALID, "query %lld: eps must be > 0", (long long)i);
+    }
+    cudaSetDevice(g->device);
+    if (q == 0) return GER_OK;
+    rc = ensure_ws(g, q, std::max(g->ws.slots, 1), g->ws.cap > 0 ? g->ws.cap : ((int64_t)1 << 17),
+                   std::max<int64_t>(g->ws.pool_cap, (int64_t)1 << 22));
+    if (rc) return rc;
+    Workspace& w = g->ws;
+    cudaStream_t st = g->stream;
+    GER_CUDA(cudaMemcpyAsync(w.s, s, q * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    GER_CUDA(cudaMemcpyAsync(w.t, t, q * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (eps_arr) GER_CUDA(cudaMemcpyAsync(w.eps, eps_arr, q * sizeof(double), cudaMemcpyHostToDevice, st));
+    p.q = q;
+    p.s = w.s;
+    p.t = w.t;
+    p.eps = eps_arr ? w.eps : nullptr;
+    p.eps_scalar = eps;
+    p.r = w.r;
+    p.stats = stats ? w.stats : nullptr;
+    p.st = st;
+    rc = run_batch(g, p);
+    if (rc) return rc;
+    GER_CUDA(cudaMemcpyAsync(r_out, w.r, q * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (stats) GER_CUDA(cudaMemcpyAsync(stats, w.stats, q * sizeof(ger_query_stats), cudaMemcpyDeviceToHost, st));
+    GER_CUDA(cudaStreamSynchronize(st));
+    return GER_OK;
+}
+
+int ger_query_batch(ger_graph* g, int64_t q, const int32_t* s, const int32_t* t, double eps,
+                    const ger_options* opt, double* r_out, ger_query_stats* stats) {
+    if (!(eps > 0.0)) return fail(GER_ERR_INVALID, "eps must be > 0");
+    return host_batch(g, q, s, t, nullptr, eps, opt, r_out, stats);
+}
+
+int ger_query_batch_eps(ger_graph* g, int64_t q, const int32_t* s, const int32_t* t, const double* eps,
+                        const ger_options* opt, double* r_out, ger_query_stats* stats) {
+    if (q > 0 && !eps) return fail(GER_ERR_INVALID, "null eps");
+    return host_batch(g, q, s, t, eps, 0.0, opt, r_out, stats);
+}
+
+int ger_query_batch_dev(ger_graph* g, int64_t q, const int32_t* s_dev, const int32_t* t_dev, const double* eps_dev,
+                        const ger_options* opt, double* r_dev, ger_query_stats* stats_dev, void* stream) {
+    if (!g || q < 0 || (q > 0 && (!s_dev || !t_dev || !eps_dev || !r_dev)))
+        return fail(GER_ERR_INVALID, "null argument or q < 0");
+    if (q > 0x7fffffff) return fail(GER_ERR_INVALID, "q too large");
+    Plan p;
+    int rc = check_opts(opt, &p.o);
+    if (rc) return rc;
+    cudaSetDevice(g->device);
+    p.q = q;
+    p.s = s_dev;
+    p.t = t_dev;
+    p.eps = eps_dev;
+    p.eps_scalar = 0.0;
+    p.r = r_dev;
+    p.stats = stats_dev;
+    p.st = stream ? reinterpret_cast<cudaStream_t>(stream) : (cudaStream_t)0;
+    return run_batch(g, p);
+}
+
+}  // extern "C"

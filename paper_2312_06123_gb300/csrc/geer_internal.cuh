@@ -1,0 +1,167 @@
+// geer_internal.cuh -- device-side building blocks and the state shared by
+// the GEER kernels (sparse SMM, AMC walks, spectral bound). Internal to the
+// CUDA library; nothing here is visible through include/geer.h.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace geer {
+
+constexpr int kCta = 256;          // threads per CTA of the SMM / reduction kernels
+constexpr int kWarps = kCta / 32;
+constexpr int kPairsPerWarpRound = 16;  // walk pairs per warp per round (2 lanes per pair)
+constexpr int kMaxChunksPerQuery = 4096;
+
+// query lifecycle
+enum : int32_t { ST_SMM = 0, ST_AMC = 1, ST_DONE = 2, ST_ERROR = 3 };
+
+// device error codes (mirrored into the host status codes)
+enum : int32_t { DERR_NONE = 0, DERR_NODE_RANGE = 1, DERR_CAPACITY = 2, DERR_TABLE = 3, DERR_ELL = 4 };
+
+// Per-query state, one record per query of a batch (device memory).
+struct QState {
+    int32_t s, t;
+    int32_t qidx, pad0;       // index in the caller's batch (walk RNG key)
+    double eps;
+    int32_t ds, dt;
+    int32_t ell, ell_b, lf, status;
+    int32_t batch, err;       // batches completed; device error code
+    double r_b, r_f, r;
+    double psi, volume, h, f_last;
+    int64_t eta0, eta;        // walk pairs: first batch, current batch
+    int64_t walks, walk_steps;
+    uint64_t checksum;
+    int64_t ppc;              // walk pairs per chunk in the current batch
+    int64_t nchunks;          // chunks in the current batch
+    int64_t table_off;        // entry offset of this query's lookup table
+    int32_t table_mask;       // capacity - 1 (power of two), -1: no table
+    int32_t front;            // |V_s u V_t| after the last SMM iteration
+};
+
+// One entry of a query's lookup table: node v and
+// g(v) = s*(v)/d(s) - t*(v)/d(t), the per-visit term of Z_k (Eq. 12).
+struct __align__(16) GEntry {
+    int32_t v;  // -1: empty
+    int32_t pad;
+    double g;
+};
+
+// Per-chunk partial sums of the walk kernel.
+struct Partial {
+    double sz, sz2;
+    uint64_t cs;
+};
+
+// Graph arrays on the device.
+struct DevGraph {
+    int64_t n, nnz;
+    const int64_t* row_ptr;
+    const int32_t* col_idx;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+    constexpr uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
+    constexpr uint32_t kWeyl0 = 0x9E3779B9u, kWeyl1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        uint32_t lo0 = kMul0 * c.x, hi0 = __umulhi(kMul0, c.x);
+        uint32_t lo1 = kMul1 * c.z, hi1 = __umulhi(kMul1, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += kWeyl0;
+        k.y += kWeyl1;
+    }
+    return c;
+}
+
+// splitmix64 finaliser (Steele, Lea, Flood, OOPSLA'14), for walk checksums
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t walk_hash(int32_t endpoint, int64_t k, int sigma, int b) {
+    uint64_t x = (uint64_t)(uint32_t)endpoint + 0x9E3779B97F4A7C15ull * (uint64_t)(2 * k + sigma + 1) +
+                 ((uint64_t)b << 58);
+    return mix64(x);
+}
+
+// murmur3 32-bit finaliser, for the lookup tables
+__device__ __forceinline__ uint32_t hash32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// CTA-wide helpers (blockDim.x == kCta)
+// ---------------------------------------------------------------------------
+
+// Inclusive warp scan of a 64-bit value.
+__device__ __forceinline__ int64_t warp_incl_scan(int64_t x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Exclusive CTA scan of one value per thread; returns the prefix and writes
+// the CTA total to *total (all threads). smem: kWarps + 1 int64.
+__device__ __forceinline__ int64_t cta_excl_scan(int64_t x, int64_t* smem, int64_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t inc = warp_incl_scan(x);
+    if (lane == 31) smem[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t w = lane < kWarps ? smem[lane] : 0;
+        int64_t wi = warp_incl_scan(w);
+        if (lane < kWarps) smem[lane] = wi - w;
+        if (lane == kWarps - 1) smem[kWarps] = wi;
+    }
+    __syncthreads();
+    int64_t r = smem[warp] + inc - x;
+    *total = smem[kWarps];
+    __syncthreads();
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// merge two (max1, max2) pairs of a multiset
+__device__ __forceinline__ void top2_merge(double& a, double& b, double a2, double b2) {
+    double hi = fmax(a, a2), lo = fmin(a, a2);
+    b = fmax(lo, fmax(b, b2));
+    a = hi;
+}
+
+__device__ __forceinline__ void warp_top2(double& a, double& b) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double a2 = __shfl_xor_sync(0xffffffffu, a, o);
+        double b2 = __shfl_xor_sync(0xffffffffu, b, o);
+        top2_merge(a, b, a2, b2);
+    }
+}
+
+}  // namespace geer
