@@ -6,7 +6,7 @@ INFRASTRUCTURE ONLY.
   * ``transition_dense``: P = D^-1 A (Section 2.1).
   * ``r_ell_dense``: Eq. (4), the series of Eq. (3) truncated at l, from dense
     powers of P.
-  * ``q_dense``: Eq. (11), the expectation of one AMC sample Z_k (Eq. (12)),
+  * ``q_dense``: Eq. (12), the expectation of one AMC sample Z_k (Eqs. (11), (13)),
     from dense powers of P.
   * ``spectrum_dense``: eigenvalues of P (via the similar symmetric matrix
     D^-1/2 A D^-1/2).
@@ -65,7 +65,7 @@ def r_ell_dense(g, s: int, t: int, L: int) -> float:
 
 
 def q_dense(g, s: int, t: int, xs: np.ndarray, xt: np.ndarray, lf: int) -> float:
-    """Eq. (11): sum_{i=1}^{lf} sum_v (p_i(s,v) - p_i(t,v)) (xs(v)/d(s) - xt(v)/d(t))."""
+    """Eq. (12): sum_{i=1}^{lf} sum_v (p_i(s,v) - p_i(t,v)) (xs(v)/d(s) - xt(v)/d(t))."""
     P = transition_dense(g)
     d = g.degrees().astype(float)
     w = xs / d[s] - xt / d[t]

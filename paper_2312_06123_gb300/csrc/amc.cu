@@ -11,8 +11,8 @@
 // neighbour floor(draw * d(w) / 2^32) in CSR order -- the same specification
 // the CPU oracle implements, so walk endpoints agree bit for bit.
 // Z_k = sum over the S walk of g(w_j) - sum over the T walk of g(w_j) with
-// g(v) = s*(v)/d(s) - t*(v)/d(t) read from the query's lookup table (Eq. 12;
-// the start node w_0 is not counted, as E[Z_k] = q(s,t) of Eq. 11 requires).
+// g(v) = s*(v)/d(s) - t*(v)/d(t) read from the query's lookup table (Eq. 11;
+// the start node w_0 is not counted, as E[Z_k] = q(s,t) of Eqs. 12-13 requires).
 // Per-chunk sums go to a partial array; the reduce kernel adds a query's
 // chunks in a fixed order, so results do not depend on scheduling.
 #include "geer_internal.cuh"

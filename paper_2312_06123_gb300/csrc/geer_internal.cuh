@@ -40,7 +40,7 @@ struct QState {
 };
 
 // One entry of a query's lookup table: node v and
-// g(v) = s*(v)/d(s) - t*(v)/d(t), the per-visit term of Z_k (Eq. 12).
+// g(v) = s*(v)/d(s) - t*(v)/d(t), the per-visit term of Z_k (Eq. 11).
 struct __align__(16) GEntry {
     int32_t v;  // -1: empty
     int32_t pad;

@@ -18,7 +18,7 @@
 // Algorithm 2 added to r_b in FP64, the support volume of Eq. (17), max_1 and
 // max_2 of s* and t*, psi (Eq. 9), eta* (Eq. 8), h(l - l_b) and the switch.
 // At the switch the query's lookup table g(v) = s*(v)/d(s) - t*(v)/d(t) is
-// built for the AMC walks (Algorithm 1, the Z_k of Eq. 12).
+// built for the AMC walks (Algorithm 1, the Z_k of Eq. 11).
 #include "geer_internal.cuh"
 #include "geer_kernels.h"
 

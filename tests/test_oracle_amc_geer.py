@@ -24,7 +24,7 @@ def _smm_vectors(g, s, t, lb):
 
 @pytest.mark.parametrize("lb,lf", [(0, 6), (2, 5), (4, 3)])
 def test_amc_sample_mean_is_q(lb, lf):
-    # E[Z_k] = q(s,t) of Eq. (11) for any non-negative vectors (Eq. 13);
+    # E[Z_k] = q(s,t) of Eq. (12) for any non-negative vectors (Eq. 13);
     # the empirical mean of eta samples lies within a CLT band around it.
     g = graphs.random_connected(50, 70, 11)
     s, t = 2, 40
