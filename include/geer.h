@@ -152,6 +152,29 @@ int ger_query_batch_dev(ger_graph *g, int64_t q, const int32_t *s_dev, const int
                         const double *eps_dev, const ger_options *opt, double *r_dev,
                         ger_query_stats *stats_dev, void *stream);
 
+/*
+ * ger_query_batch_dev with no allocation: the paper has no counterpart; this
+ * entry point exists for callers that cannot call cudaMalloc -- a serving
+ * loop that must never block on the device (cudaMalloc/cudaFree may
+ * synchronise it), or a process whose device memory is reserved up front or
+ * owned by another allocator. It allocates nothing (no cudaMalloc, cudaFree,
+ * pinned buffer or allocating library call): all scratch comes from one
+ * static 32 MiB device array that every GPU loading the library holds until
+ * the process exits. Arguments are those of ger_query_batch_dev, with these
+ * limits: q <= 64, at most 65536 SMM push pairs per query iteration
+ * (sparse_cap <= 65536), 524288 lookup entries per call; beyond them it
+ * returns GER_ERR_CAPACITY. The spectral bound must already be available
+ * (ger_spectral_bound or ger_set_spectral_bound), else GER_ERR_NO_LAMBDA.
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture. Every call shares the one array and
+ * resets what must start at zero; calls that overlap on the GPU (other
+ * streams, other threads) race on it and must be serialised by the caller.
+ * Returns once the work has completed.
+ */
+int ger_query_batch_dev_noalloc(ger_graph *g, int64_t q, const int32_t *s_dev, const int32_t *t_dev,
+                                const double *eps_dev, const ger_options *opt, double *r_dev,
+                                ger_query_stats *stats_dev, void *stream);
+
 /* Thread-local description of the last error of this thread. */
 const char *ger_last_error(void);
 

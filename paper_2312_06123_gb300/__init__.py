@@ -84,6 +84,7 @@ def load_library(build_if_missing: bool = True):
     L.ger_query_batch.argtypes = [_P, i64, _P, _P, f64, ctypes.POINTER(Options), _P, _P]
     L.ger_query_batch_eps.argtypes = [_P, i64, _P, _P, _P, ctypes.POINTER(Options), _P, _P]
     L.ger_query_batch_dev.argtypes = [_P, i64, _P, _P, _P, ctypes.POINTER(Options), _P, _P, _P]
+    L.ger_query_batch_dev_noalloc.argtypes = [_P, i64, _P, _P, _P, ctypes.POINTER(Options), _P, _P, _P]
     L.ger_last_error.argtypes = []
     L.ger_last_error.restype = ctypes.c_char_p
     L.ger_launch_count.argtypes = []
@@ -93,7 +94,8 @@ def load_library(build_if_missing: bool = True):
     L.ger_profile_read.argtypes = [ctypes.POINTER(KernelProfile), ctypes.c_int]
     L.ger_profile_read.restype = ctypes.c_int
     for name in ("ger_load_csr", "ger_graph_size", "ger_spectral_bound", "ger_set_spectral_bound",
-                 "ger_query_batch", "ger_query_batch_eps", "ger_query_batch_dev"):
+                 "ger_query_batch", "ger_query_batch_eps", "ger_query_batch_dev",
+                 "ger_query_batch_dev_noalloc"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -217,3 +219,20 @@ class Graph:
         _check(load_library().ger_query_batch_dev(self._h, q, ptr(s_dev), ptr(t_dev), ptr(eps_dev),
                                                   ctypes.byref(opt), ptr(r_dev), ptr(stats_dev),
                                                   ctypes.c_void_p(stream) if stream else None))
+
+    def query_dev_noalloc(self, s_dev, t_dev, eps_dev, r_dev, stats_dev=None, options: Options | None = None,
+                          stream=None):
+        """As query_dev, through ger_query_batch_dev_noalloc: for callers
+        that cannot allocate device memory. All scratch comes from a static
+        32 MiB device array; at most 64 queries per call; the spectral bound
+        must already be set or computed. Calls that overlap on the GPU race
+        on the shared array."""
+        def ptr(x):
+            if x is None:
+                return None
+            return ctypes.c_void_p(x if isinstance(x, int) else x.data_ptr())
+        q = int(s_dev.shape[0])
+        opt = options if options is not None else default_options()
+        _check(load_library().ger_query_batch_dev_noalloc(self._h, q, ptr(s_dev), ptr(t_dev), ptr(eps_dev),
+                                                          ctypes.byref(opt), ptr(r_dev), ptr(stats_dev),
+                                                          ctypes.c_void_p(stream) if stream else None))

@@ -443,6 +443,27 @@ static int run_batch(ger_graph* g, Plan& p) {
     return fail(GER_ERR_CAPACITY, "workspace did not fit after retries");
 }
 
+// Read-only view of a loaded graph, for entry points defined in other
+// translation units.
+int graph_view(const ger_graph* g, DevGraph* dg, double* lambda, bool* has_lambda, int* device, int* sm_count) {
+    if (!g) return fail(GER_ERR_INVALID, "null graph");
+    *dg = DevGraph{g->n, g->nnz, g->row_ptr, g->col_idx};
+    *lambda = g->lambda;
+    *has_lambda = g->has_lambda;
+    *device = g->device;
+    *sm_count = g->sm_count;
+    return GER_OK;
+}
+
+int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
+void launch_finalize(const QState* st, int64_t nq, double* r, ger_query_stats* stats, cudaStream_t s) {
+    const int fg = (int)std::min<int64_t>((nq + 255) / 256, 4096);
+    prof_begin(FAM_FINALIZE, s);
+    finalize_kernel<<<fg, 256, 0, s>>>(st, nq, r, stats);
+    prof_end(FAM_FINALIZE, s);
+}
+
 }  // namespace geer
 
 using namespace geer;

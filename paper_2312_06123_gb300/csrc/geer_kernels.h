@@ -71,3 +71,15 @@ int lanczos_spectral_bound(const DevGraph& g, int max_steps, double tol, cudaStr
                            double* lamn, int* steps);
 
 }  // namespace geer
+
+struct ger_graph;
+struct ger_query_stats;
+
+namespace geer {
+
+// accessors of api.cu for entry points in other translation units
+int graph_view(const ger_graph* g, DevGraph* dg, double* lambda, bool* has_lambda, int* device, int* sm_count);
+int set_error(int code, const char* msg);
+void launch_finalize(const QState* st, int64_t nq, double* r, ger_query_stats* stats, cudaStream_t s);
+
+}  // namespace geer
