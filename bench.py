@@ -159,6 +159,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=10.0, help="oracle seconds per reference step")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle seconds for cpu_baseline")
     ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 per-query path")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="profiling runs: skip the e2e, plain-FP64 and CPU-baseline legs (timed region unchanged)")
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.impl == "reference":
@@ -235,20 +237,21 @@ def main():
 
     # e2e: host buffers through ger_query_batch_eps, copies inside the timed region
     e2e_t = []
-    for _ in range(args.steps):
+    for _ in range(0 if args.no_extras else args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         G.query(w.s, w.t, w.eps, opts)
         e2e_t.append(time.perf_counter() - t1)
-    e2e_value = world * w.q * args.steps / sum(e2e_t)
+    e2e_value = world * w.q * len(e2e_t) / sum(e2e_t) if e2e_t else None
 
     # the plain FP64 per-query GPU path (one query at a time), same queries
     plain_opts = geer.default_options(precision=geer.GER_FP64, per_query=1)
-    G.query_dev(s_d, t_d, e_d, r_d, None, plain_opts, stream=stream.cuda_stream)
-    torch.cuda.synchronize()
+    if not args.no_extras:
+        G.query_dev(s_d, t_d, e_d, r_d, None, plain_opts, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
     pt = []
-    for _ in range(max(args.plain_steps, 1)):
+    for _ in range(0 if args.no_extras else max(args.plain_steps, 1)):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -256,7 +259,7 @@ def main():
         b.record(stream)
         b.synchronize()
         pt.append(a.elapsed_time(b))
-    plain_value = w.q * len(pt) / (sum(pt) / 1000.0)
+    plain_value = w.q * len(pt) / (sum(pt) / 1000.0) if pt else None
 
     if rank != 0:
         return 0
@@ -278,10 +281,12 @@ def main():
         roof = {"kernel": fam[0], "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s",
                 "frac": None, "peak_source": peak_kind, "traffic": None}
     # CPU baseline: the oracle as it stands, one host thread, bounded sample
-    import oracle
-    nq, el = oracle_sample(w, lam, args.cpu_seconds)
-    cpu = {"value": nq / el, "unit": "queries/s", "cores": 1, "kind": "oracle",
-           "sample": f"first {nq} queries of the workload, {el:.1f} s, same lambda and seed"}
+    cpu = None
+    if not args.no_extras:
+        import oracle
+        nq, el = oracle_sample(w, lam, args.cpu_seconds)
+        cpu = {"value": nq / el, "unit": "queries/s", "cores": 1, "kind": "oracle",
+               "sample": f"first {nq} queries of the workload, {el:.1f} s, same lambda and seed"}
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -293,8 +298,9 @@ def main():
                 "d2h_bytes_per_step": int(w.q * 8)},
         "gpu_launches": int(launches),
         "clocks": clk,
-        "plain_fp64_per_query": {"value": plain_value, "unit": "queries/s", "ms_per_step": float(np.mean(pt)),
-                                 "speedup_of_batched_fp32": value / world / plain_value},
+        "plain_fp64_per_query": None if plain_value is None else {
+            "value": plain_value, "unit": "queries/s", "ms_per_step": float(np.mean(pt)),
+            "speedup_of_batched_fp32": value / world / plain_value},
         "preprocess": {"spectral_bound_ms": pre_ms, "lambda": lam, "lambda_2": l2, "lambda_n": ln},
         "kernels": {k: {"launches": v[0], "total_ms": v[1]} for k, v in prof.items()},
         "work": {"walk_steps_per_step": walk_steps, "walk_pairs_per_step": int(stats["walks"].sum()),

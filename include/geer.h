@@ -67,7 +67,7 @@ typedef struct ger_options {
     int32_t  fixed_ell_b;   /* used by GER_SWITCH_FIXED */
     int32_t  ell_formula;   /* GER_ELL_REFINED (default) or GER_ELL_PENG */
     uint64_t seed;          /* walk RNG seed */
-    int64_t  sparse_cap;    /* max SMM push volume per query step on the sparse path (0: default) */
+    int64_t  sparse_cap;    /* max SMM push pairs of one query iteration (0: no limit beyond the pool) */
 } ger_options;
 
 /* Per-query statistics (all optional outputs). */
@@ -161,9 +161,10 @@ int ger_query_batch_dev(ger_graph *g, int64_t q, const int32_t *s_dev, const int
  * pinned buffer or allocating library call): all scratch comes from one
  * static 32 MiB device array that every GPU loading the library holds until
  * the process exits. Arguments are those of ger_query_batch_dev, with these
- * limits: q <= 64, at most 65536 SMM push pairs per query iteration
- * (sparse_cap <= 65536), 524288 lookup entries per call; beyond them it
- * returns GER_ERR_CAPACITY. The spectral bound must already be available
+ * limits: q <= 64, and 524288 frontier-table slots per call (the tables of
+ * every SMM iteration of every query, each a power of two at least twice the
+ * iteration's push volume); beyond them it returns GER_ERR_CAPACITY. The
+ * spectral bound must already be available
  * (ger_spectral_bound or ger_set_spectral_bound), else GER_ERR_NO_LAMBDA.
  * The first call on a device looks up the array's device address; make that
  * first call before any stream capture. Every call shares the one array and

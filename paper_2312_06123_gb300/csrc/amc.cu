@@ -3,9 +3,10 @@
 // Z_k^2, and the empirical-Bernstein stop of Lemma 2 / Eq. (7) at delta/tau.
 //
 // Work layout of one batch b: query q runs eta_q walk pairs, cut into
-// chunks of ppc pairs (a multiple of 16, at most kMaxChunksPerQuery chunks).
-// A warp owns one chunk at a time: lanes 2i and 2i+1 walk pair k = k0 + i,
-// lane 2i from s (sigma = 0), lane 2i+1 from t (sigma = 1). Each walk step
+// chunks of ppc pairs (a multiple of 16 W, at most kMaxChunksPerQuery
+// chunks). A warp owns one chunk at a time: lanes 2i and 2i+1 walk pairs
+// k0 + i + 16 w (w < W walks per lane), lane 2i from s (sigma = 0), lane
+// 2i+1 from t (sigma = 1). Each walk step
 // draws one 32-bit word of Philox4x32-10 keyed by (seed) with counter
 // (k, 2(b-1)+sigma, query index, (j-1) >> 2), word (j-1) & 3, and moves to
 // neighbour floor(draw * d(w) / 2^32) in CSR order -- the same specification
@@ -20,21 +21,12 @@
 
 namespace geer {
 
+#ifndef GEER_WALKS_PER_LANE
+#define GEER_WALKS_PER_LANE 1
+#endif
+constexpr int kWalksPerLane = GEER_WALKS_PER_LANE;
+
 namespace {
-
-__device__ __forceinline__ double lookup_g(const GEntry* tab, int32_t mask, int32_t v) {
-    uint32_t h = hash32((uint32_t)v) & (uint32_t)mask;
-    for (;;) {
-        const int4 raw = __ldg(reinterpret_cast<const int4*>(tab + h));
-        if (raw.x == v) return __hiloint2double(raw.w, raw.z);
-        if (raw.x == -1) return 0.0;
-        h = (h + 1) & (uint32_t)mask;
-    }
-}
-
-__device__ __forceinline__ uint32_t word(const uint4& r, int i) {
-    return i == 0 ? r.x : (i == 1 ? r.y : (i == 2 ? r.z : r.w));
-}
 
 }  // namespace
 
@@ -52,9 +44,11 @@ __global__ void __launch_bounds__(kCta) amc_schedule_kernel(AmcArgs a) {
             QState* Q = a.st + q;
             if (Q->status == ST_AMC) {
                 const int64_t eta = Q->eta;
-                const int64_t units = (eta + kPairsPerWarpRound - 1) / kPairsPerWarpRound;
+                // a warp round walks kWalksPerLane * kPairsPerWarpRound pairs
+                const int64_t unit = kWalksPerLane * kPairsPerWarpRound;
+                const int64_t units = (eta + unit - 1) / unit;
                 int64_t c = units < kMaxChunksPerQuery ? units : kMaxChunksPerQuery;
-                const int64_t ppc = kPairsPerWarpRound * ((units + c - 1) / c);
+                const int64_t ppc = unit * ((units + c - 1) / c);
                 nch = (eta + ppc - 1) / ppc;
                 Q->ppc = ppc;
             }
@@ -70,14 +64,41 @@ __global__ void __launch_bounds__(kCta) amc_schedule_kernel(AmcArgs a) {
     if (tid == 0) a.chunk_begin[a.nq] = carry;
 }
 
+// Row start and degree of node w.
+__device__ __forceinline__ uint2 node_row(const DevGraph& g, int32_t w) {
+    if (g.node_info) return __ldg(g.node_info + w);
+    const int64_t rs = __ldg(g.row_ptr + w);
+    return make_uint2((uint32_t)rs, (uint32_t)(__ldg(g.row_ptr + w + 1) - rs));
+}
+
+__device__ __forceinline__ const int32_t* row_base(const DevGraph& g, int32_t w, uint2 info) {
+    // node_info holds the low 32 bits of the row start (nnz < 2^32); otherwise
+    // re-read the full 64-bit start
+    return g.node_info ? g.col_idx + info.x : g.col_idx + __ldg(g.row_ptr + w);
+}
+
+// g of a node whose first probe `p` (slot h) is already loaded
+__device__ __forceinline__ double resolve_g(const GEntry* tab, int32_t mask, int32_t v, int4 p, uint32_t h) {
+    for (;;) {
+        if (p.x == v) return __hiloint2double(p.w, p.z);
+        if (p.x == -1) return 0.0;
+        h = (h + 1) & (uint32_t)mask;
+        p = __ldg(reinterpret_cast<const int4*>(tab + h));
+    }
+}
+
+// W walk pairs per lane pair and round: lanes 2i, 2i+1 walk pairs
+// k0 + i + 16 w (w < W), from s and from t. The W walks of a lane advance in
+// lockstep so that their loads overlap; each step issues the next node's
+// row record and its first lookup probe together.
+template <int W>
 __global__ void __launch_bounds__(256) amc_walk_kernel(AmcArgs a) {
     const int lane = threadIdx.x & 31;
     const int sigma = lane & 1;
     const int64_t total = a.chunk_begin[a.nq];
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
-    const int64_t* row_ptr = a.g.row_ptr;
-    const int32_t* col_idx = a.g.col_idx;
+    const DevGraph g = a.g;
     const uint32_t lane_ctr = (uint32_t)(2 * (a.batch - 1) + sigma);
     for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total; c += nw) {
         // owning query: last q with chunk_begin[q] <= c
@@ -93,33 +114,66 @@ __global__ void __launch_bounds__(256) amc_walk_kernel(AmcArgs a) {
         const int32_t start = sigma ? Q->t : Q->s;
         const GEntry* tab = a.pool + Q->table_off;
         const int32_t mask = Q->table_mask;
+        const uint2 start_info = node_row(g, start);
         const int64_t k_lo = (c - cb) * ppc;
         const int64_t k_hi = min(k_lo + ppc, eta);
         double sz = 0.0, sz2 = 0.0;
         uint64_t cs = 0;
-        for (int64_t k0 = k_lo; k0 < k_hi; k0 += kPairsPerWarpRound) {
-            const int64_t k = k0 + (lane >> 1);
-            const bool active = k < k_hi;
-            double zp = 0.0;
-            if (active) {
-                int32_t w = start;
-                uint4 r = make_uint4(0, 0, 0, 0);
-                for (int j = 1; j <= lf; ++j) {
-                    if (((j - 1) & 3) == 0)
-                        r = philox4x32_10(make_uint4((uint32_t)k, lane_ctr, (uint32_t)qidx, (uint32_t)((j - 1) >> 2)), key);
-                    const uint32_t draw = word(r, (j - 1) & 3);
-                    const int64_t rs = __ldg(row_ptr + w);
-                    const uint64_t d = (uint64_t)(__ldg(row_ptr + w + 1) - rs);
-                    w = __ldg(col_idx + rs + (int64_t)(((uint64_t)draw * d) >> 32));
-                    zp += lookup_g(tab, mask, w);
-                }
-                cs += walk_hash(w, k, sigma, a.batch);
+        for (int64_t k0 = k_lo; k0 < k_hi; k0 += W * kPairsPerWarpRound) {
+            int64_t k[W];
+            bool act[W];
+            double z[W];
+            int32_t w[W];
+            uint2 inf[W];
+            uint4 r[W];
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                k[i] = k0 + (lane >> 1) + i * kPairsPerWarpRound;
+                act[i] = k[i] < k_hi;
+                z[i] = 0.0;
+                w[i] = start;
+                inf[i] = start_info;
+                r[i] = make_uint4(0, 0, 0, 0);
             }
-            const double other = __shfl_xor_sync(0xffffffffu, zp, 1);
-            if (active && sigma == 0) {
-                const double zk = zp - other;
-                sz += zk;
-                sz2 += zk * zk;
+            if (act[0]) {
+                for (int j = 1; j <= lf; ++j) {
+                    const int sub = (j - 1) & 3;
+                    int32_t nx[W];
+                    uint32_t hh[W];
+                    int4 pr[W];
+#pragma unroll
+                    for (int i = 0; i < W; ++i) {
+                        if (sub == 0 && act[i])
+                            r[i] = philox4x32_10(
+                                make_uint4((uint32_t)k[i], lane_ctr, (uint32_t)qidx, (uint32_t)((j - 1) >> 2)), key);
+                        const uint32_t d = sub == 0 ? r[i].x : (sub == 1 ? r[i].y : (sub == 2 ? r[i].z : r[i].w));
+                        nx[i] = act[i] ? __ldg(row_base(g, w[i], inf[i]) + __umulhi(d, inf[i].y)) : start;
+                    }
+                    // next row records and first probes, all independent
+#pragma unroll
+                    for (int i = 0; i < W; ++i) {
+                        hh[i] = hash32((uint32_t)nx[i]) & (uint32_t)mask;
+                        pr[i] = __ldg(reinterpret_cast<const int4*>(tab + hh[i]));
+                        if (act[i]) inf[i] = node_row(g, nx[i]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < W; ++i) {
+                        if (act[i]) z[i] += resolve_g(tab, mask, nx[i], pr[i], hh[i]);
+                        w[i] = nx[i];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < W; ++i)
+                    if (act[i]) cs += walk_hash(w[i], k[i], sigma, a.batch);
+            }
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                const double o = __shfl_xor_sync(0xffffffffu, z[i], 1);
+                if (sigma == 0 && act[i]) {
+                    const double zk = z[i] - o;
+                    sz += zk;
+                    sz2 += zk * zk;
+                }
             }
         }
         sz = warp_sum(sz);
@@ -202,7 +256,7 @@ void launch_amc_schedule(const AmcArgs& a, cudaStream_t st) {
 
 void launch_amc_walk(const AmcArgs& a, int grid, cudaStream_t st) {
     prof_begin(FAM_AMC_WALK, st);
-    amc_walk_kernel<<<grid, 256, 0, st>>>(a);
+    amc_walk_kernel<kWalksPerLane><<<grid, 256, 0, st>>>(a);
     prof_end(FAM_AMC_WALK, st);
 }
 

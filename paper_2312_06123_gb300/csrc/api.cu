@@ -18,13 +18,15 @@
 namespace geer {
 
 static std::atomic<int64_t> g_launches{0};
+constexpr int64_t kHeavyCap = 1 << 16;
 void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------------------
 // profiler: CUDA events around launches, on the launch stream
 // ---------------------------------------------------------------------------
-static const char* kFamilyNames[FAM_COUNT] = {"smm_sparse", "amc_schedule", "amc_walk", "amc_reduce",
-                                              "finalize", "lanczos"};
+static const char* kFamilyNames[FAM_COUNT] = {"smm_setup", "smm_alloc", "smm_clear", "smm_push",
+                                              "smm_push_heavy", "smm_finish", "smm_top2", "smm_decide", "amc_schedule",
+                                              "amc_walk", "amc_reduce", "finalize", "lanczos"};
 struct ProfRec {
     int fam;
     cudaEvent_t a, b;
@@ -108,18 +110,19 @@ struct Workspace {
     int64_t* chunk_begin = nullptr;
     Partial* partial = nullptr;
     int64_t partial_cap = 0;
-    // sparse SMM scratch
-    int slots = 0;
-    int64_t cap = 0;
-    int32_t* scr_i32 = nullptr;
-    void* scr_val = nullptr;
-    uint8_t* scr_bits = nullptr;
-    // lookup tables
-    GEntry* pool = nullptr;
+    // SMM phase
+    QSmm* qsmm = nullptr;
+    int32_t* seg_q = nullptr;     // 2 (q_cap)
+    int64_t* seg_off = nullptr;   // 2 (q_cap + 1)
+    int64_t* heavy = nullptr;     // kHeavyCap slots
+    SmmCtl* ctl = nullptr;
+    // frontier-table pool (also the walk lookup tables)
+    GEntry* ent = nullptr;
+    unsigned long long* sums = nullptr;  // 2 pool_cap
+    double* yvals = nullptr;             // 2 pool_cap values (T = float or double)
     int64_t pool_cap = 0;
-    // counters: [0] work counter, [1] error flag (int), pool_used (u64)
+    // counters: [1] error flag (int)
     int* counters = nullptr;
-    unsigned long long* pool_used = nullptr;
     // pinned readback
     int64_t* host_rb = nullptr;
 };
@@ -132,6 +135,7 @@ struct ger_graph {
     int64_t n = 0, nnz = 0;
     int64_t* row_ptr = nullptr;
     int32_t* col_idx = nullptr;
+    uint2* node_info = nullptr;  // {first edge, degree} per node when nnz < 2^32
     bool has_lambda = false;
     double lambda = 0, lam2 = 0, lamn = 0;
     cudaStream_t stream = nullptr;
@@ -142,8 +146,9 @@ namespace geer {
 
 static void free_ws(Workspace& w) {
     cudaFree(w.st); cudaFree(w.s); cudaFree(w.t); cudaFree(w.eps); cudaFree(w.r); cudaFree(w.stats);
-    cudaFree(w.chunk_begin); cudaFree(w.partial); cudaFree(w.scr_i32); cudaFree(w.scr_val);
-    cudaFree(w.scr_bits); cudaFree(w.pool); cudaFree(w.counters); cudaFree(w.pool_used);
+    cudaFree(w.chunk_begin); cudaFree(w.partial); cudaFree(w.qsmm); cudaFree(w.seg_q); cudaFree(w.seg_off);
+    cudaFree(w.ctl); cudaFree(w.ent); cudaFree(w.sums); cudaFree(w.yvals); cudaFree(w.counters);
+    cudaFree(w.heavy);
     if (w.host_rb) cudaFreeHost(w.host_rb);
     w = Workspace();
 }
@@ -153,51 +158,38 @@ static cudaError_t alloc(T** p, size_t count) {
     return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16);
 }
 
-// Make room for q queries, `slots` sparse CTAs of capacity `cap`, and a
-// lookup pool of at least pool_cap entries.
-static int ensure_ws(ger_graph* g, int64_t q, int slots, int64_t cap, int64_t pool_cap) {
+// Make room for q queries and a frontier-table pool of at least pool_cap slots.
+static int ensure_ws(ger_graph* g, int64_t q, int64_t pool_cap) {
     Workspace& w = g->ws;
     if (!w.counters) {
         GER_CUDA(alloc(&w.counters, 4));
-        GER_CUDA(alloc(&w.pool_used, 1));
+        GER_CUDA(alloc(&w.ctl, 1));
+        GER_CUDA(alloc(&w.heavy, kHeavyCap));
         GER_CUDA(cudaMallocHost(reinterpret_cast<void**>(&w.host_rb), 4 * sizeof(int64_t)));
     }
     if (q > w.q_cap) {
         cudaFree(w.st); cudaFree(w.s); cudaFree(w.t); cudaFree(w.eps); cudaFree(w.r); cudaFree(w.stats);
-        cudaFree(w.chunk_begin); cudaFree(w.partial);
+        cudaFree(w.chunk_begin); cudaFree(w.partial); cudaFree(w.qsmm); cudaFree(w.seg_q); cudaFree(w.seg_off);
         w.st = nullptr; w.s = nullptr; w.t = nullptr; w.eps = nullptr; w.r = nullptr; w.stats = nullptr;
-        w.chunk_begin = nullptr; w.partial = nullptr; w.q_cap = 0;
+        w.chunk_begin = nullptr; w.partial = nullptr; w.qsmm = nullptr; w.seg_q = nullptr; w.seg_off = nullptr;
+        w.q_cap = 0;
         const int64_t qc = std::max<int64_t>(q, 64);
         const int64_t pc = qc * kMaxChunksPerQuery;
         if (alloc(&w.st, qc) || alloc(&w.s, qc) || alloc(&w.t, qc) || alloc(&w.eps, qc) || alloc(&w.r, qc) ||
-            alloc(&w.stats, qc) || alloc(&w.chunk_begin, qc + 1) || alloc(&w.partial, pc)) {
+            alloc(&w.stats, qc) || alloc(&w.chunk_begin, qc + 1) || alloc(&w.partial, pc) ||
+            alloc(&w.qsmm, qc) || alloc(&w.seg_q, 2 * qc) || alloc(&w.seg_off, 2 * (qc + 1))) {
             cudaGetLastError();
             return fail(GER_ERR_OOM, "workspace for %lld queries", (long long)q);
         }
         w.q_cap = qc;
         w.partial_cap = pc;
     }
-    if (slots > w.slots || cap != w.cap) {
-        cudaFree(w.scr_i32); cudaFree(w.scr_val); cudaFree(w.scr_bits);
-        w.scr_i32 = nullptr; w.scr_val = nullptr; w.scr_bits = nullptr; w.slots = 0;
-        const int64_t F = cap + 2;
-        const size_t ni = (size_t)slots * (size_t)(5 * cap + 3 * F + 2);
-        const size_t nv = (size_t)slots * (size_t)(4 * F);
-        const size_t nb = (size_t)slots * (size_t)(2 * F);
-        if (alloc(&w.scr_i32, ni) || cudaMalloc(&w.scr_val, nv * sizeof(double) + 16) || alloc(&w.scr_bits, nb)) {
-            cudaGetLastError();
-            return fail(GER_ERR_OOM, "sparse SMM scratch (%d slots x %lld pairs)", slots, (long long)cap);
-        }
-        w.slots = slots;
-        w.cap = cap;
-    }
     if (pool_cap > w.pool_cap) {
-        cudaFree(w.pool);
-        w.pool = nullptr;
-        w.pool_cap = 0;
-        if (alloc(&w.pool, pool_cap)) {
+        cudaFree(w.ent); cudaFree(w.sums); cudaFree(w.yvals);
+        w.ent = nullptr; w.sums = nullptr; w.yvals = nullptr; w.pool_cap = 0;
+        if (alloc(&w.ent, pool_cap) || alloc(&w.sums, 2 * pool_cap) || alloc(&w.yvals, 2 * pool_cap)) {
             cudaGetLastError();
-            return fail(GER_ERR_OOM, "lookup pool of %lld entries", (long long)pool_cap);
+            return fail(GER_ERR_OOM, "frontier-table pool of %lld slots", (long long)pool_cap);
         }
         w.pool_cap = pool_cap;
     }
@@ -293,7 +285,7 @@ static int validate_csr(int64_t n, const int64_t* rp, const int32_t* ci) {
 
 static int ensure_lambda(ger_graph* g) {
     if (g->has_lambda) return GER_OK;
-    DevGraph dg{g->n, g->nnz, g->row_ptr, g->col_idx};
+    DevGraph dg{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info};
     double l2 = 0, ln = 0;
     int steps = 0;
     const int rc = lanczos_spectral_bound(dg, 300, 1e-13, g->stream, &l2, &ln, &steps);
@@ -322,90 +314,106 @@ struct Plan {
     cudaStream_t st;
 };
 
-static int nbits_of(int64_t n) {
-    int b = 0;
-    for (int64_t x = n - 1; x > 0; x >>= 1) ++b;
-    return b < 1 ? 1 : b;
-}
 
 static int map_device_error(int e) {
     switch (e) {
         case DERR_NODE_RANGE: return fail(GER_ERR_NODE_RANGE, "a query node is outside [0, n) or eps <= 0");
-        case DERR_CAPACITY: return fail(GER_ERR_CAPACITY, "an SMM iteration exceeded the sparse capacity");
-        case DERR_TABLE: return fail(GER_ERR_CAPACITY, "lookup pool exhausted");
+        case DERR_CAPACITY: return fail(GER_ERR_CAPACITY, "an SMM iteration needs a frontier table beyond the limit");
+        case DERR_TABLE: return fail(GER_ERR_CAPACITY, "frontier-table pool exhausted");
         case DERR_ELL: return fail(GER_ERR_INVALID, "truncation length undefined (lambda >= 1)");
         default: return fail(GER_ERR_CUDA, "device error %d", e);
     }
 }
 
-template <typename T>
-static void launch_sequence(ger_graph* g, const Plan& p, bool per_query) {
+// The GEER launch sequence for queries [q0, q0 + nq) of the plan: the SMM
+// iterations (one host round trip per iteration to learn whether any query
+// continues), then tau AMC rounds. Returns a GER_* status.
+static int run_queries(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool fp64) {
     Workspace& w = g->ws;
-    DevGraph dg{g->n, g->nnz, g->row_ptr, g->col_idx};
+    DevGraph dg{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info};
     const int tau = p.o.tau;
-    const int walk_grid = per_query ? g->sm_count * 2 : g->sm_count * 8;
-    auto run = [&](int64_t q0, int64_t nq) {
-        cudaMemsetAsync(w.counters, 0, sizeof(int), p.st);  // work counter
-        SmmArgs a;
-        a.g = dg;
-        a.nq = (int32_t)nq;
-        a.q_index_base = (int32_t)q0;
-        a.st = w.st + q0;
-        a.s = p.s + q0;
-        a.t = p.t + q0;
-        a.eps = p.eps ? p.eps + q0 : nullptr;
-        a.eps_scalar = p.eps_scalar;
-        a.lambda = g->lambda;
-        a.delta = p.o.delta;
-        a.tau = tau;
-        a.ell_formula = p.o.ell_formula;
-        a.policy = p.o.switch_policy;
-        a.fixed_lb = p.o.fixed_ell_b;
-        a.nbits = nbits_of(g->n);
-        a.cap = w.cap;
-        a.scr_i32 = w.scr_i32;
-        a.scr_val = w.scr_val;
-        a.scr_bits = w.scr_bits;
-        a.pool = w.pool;
-        a.pool_cap = w.pool_cap;
-        a.pool_used = w.pool_used;
-        a.work_counter = w.counters;
-        a.err_flag = w.counters + 1;
-        const int grid = (int)std::min<int64_t>(nq, w.slots);
-        launch_smm_sparse(sizeof(T) == 8, a, grid, p.st);
-        AmcArgs m;
-        m.g = dg;
-        m.nq = (int32_t)nq;
-        m.st = w.st + q0;
-        m.chunk_begin = w.chunk_begin;
-        m.partial = w.partial;
-        m.partial_cap = w.partial_cap;
-        m.pool = w.pool;
-        m.seed = p.o.seed;
-        m.tau = tau;
-        m.delta = p.o.delta;
-        m.err_flag = w.counters + 1;
-        const int red_grid = (int)std::min<int64_t>(nq, 4096);
-        for (int b = 1; b <= tau; ++b) {
-            m.batch = b;
-            launch_amc_schedule(m, p.st);
-            launch_amc_walk(m, walk_grid, p.st);
-            launch_amc_reduce(m, red_grid, p.st);
-        }
-        note_launches(1 + 3 * tau);
-    };
-    cudaMemsetAsync(w.counters + 1, 0, sizeof(int), p.st);  // error flag
-    cudaMemsetAsync(w.pool_used, 0, sizeof(unsigned long long), p.st);
-    if (per_query) {
-        for (int64_t i = 0; i < p.q; ++i) run(i, 1);
+    SmmArgs a;
+    a.g = dg;
+    a.nq = (int32_t)nq;
+    a.q_index_base = (int32_t)q0;
+    a.st = w.st + q0;
+    a.sm = w.qsmm + q0;
+    a.s = p.s + q0;
+    a.t = p.t + q0;
+    a.eps = p.eps ? p.eps + q0 : nullptr;
+    a.eps_scalar = p.eps_scalar;
+    a.lambda = g->lambda;
+    a.delta = p.o.delta;
+    a.tau = tau;
+    a.ell_formula = p.o.ell_formula;
+    a.policy = p.o.switch_policy;
+    a.fixed_lb = p.o.fixed_ell_b;
+    if (p.o.sparse_cap > 0) {
+        int64_t cap = 16;
+        while (cap < 2 * p.o.sparse_cap) cap <<= 1;
+        a.max_table = cap;
     } else {
-        run(0, p.q);
+        a.max_table = std::min<int64_t>(w.pool_cap, (int64_t)1 << 26);
     }
-    const int fg = (int)std::min<int64_t>((p.q + 255) / 256, 4096);
-    prof_begin(FAM_FINALIZE, p.st);
-    finalize_kernel<<<fg, 256, 0, p.st>>>(w.st, p.q, p.r, p.stats);
-    prof_end(FAM_FINALIZE, p.st);
-    note_launches(1);
+    a.ent = w.ent;
+    a.sum_s = w.sums;
+    a.sum_t = w.sums + w.pool_cap;
+    a.ys = w.yvals;
+    a.yt = fp64 ? (void*)(w.yvals + w.pool_cap) : (void*)(reinterpret_cast<float*>(w.yvals) + w.pool_cap);
+    a.pool_cap = w.pool_cap;
+    a.seg_q[0] = w.seg_q;
+    a.seg_q[1] = w.seg_q + w.q_cap;
+    a.seg_off[0] = w.seg_off;
+    a.seg_off[1] = w.seg_off + (w.q_cap + 1);
+    a.heavy = w.heavy;
+    a.heavy_cap = kHeavyCap;
+    a.ctl = w.ctl;
+    a.err_flag = w.counters + 1;
+    const int grid = g->sm_count * 8;
+    launch_smm_setup(a, p.st);
+    launch_smm_alloc(a, 0, p.st);
+    launch_smm_clear(a, 0, grid, p.st);
+    launch_smm_seed(a, p.st);
+    launch_smm_finish(fp64, a, 0, grid, p.st);
+    launch_smm_top2(fp64, a, 0, grid, p.st);
+    launch_smm_decide(a, 0, 0, p.st);
+    note_launches(7);
+    int32_t* n_want = reinterpret_cast<int32_t*>(w.host_rb + 2);
+    for (int iter = 1; iter < 100000; ++iter) {
+        GER_CUDA(cudaMemcpyAsync(n_want, &w.ctl->n_want, sizeof(int32_t), cudaMemcpyDeviceToHost, p.st));
+        GER_CUDA(cudaStreamSynchronize(p.st));
+        if (*n_want == 0) break;
+        const int par = iter & 1;
+        launch_smm_alloc(a, par, p.st);
+        launch_smm_clear(a, par, grid, p.st);
+        launch_smm_push(fp64, a, par ^ 1, grid, p.st);
+        launch_smm_finish(fp64, a, par, grid, p.st);
+        launch_smm_top2(fp64, a, par, grid, p.st);
+        launch_smm_decide(a, par, iter, p.st);
+        note_launches(7);
+    }
+    AmcArgs m;
+    m.g = dg;
+    m.nq = (int32_t)nq;
+    m.st = w.st + q0;
+    m.chunk_begin = w.chunk_begin;
+    m.partial = w.partial;
+    m.partial_cap = w.partial_cap;
+    m.pool = w.ent;
+    m.seed = p.o.seed;
+    m.tau = tau;
+    m.delta = p.o.delta;
+    m.err_flag = w.counters + 1;
+    const int red_grid = (int)std::min<int64_t>(nq, 4096);
+    const int walk_grid = nq == 1 ? g->sm_count * 2 : g->sm_count * 8;
+    for (int b = 1; b <= tau; ++b) {
+        m.batch = b;
+        launch_amc_schedule(m, p.st);
+        launch_amc_walk(m, walk_grid, p.st);
+        launch_amc_reduce(m, red_grid, p.st);
+    }
+    note_launches(3 * tau);
+    return GER_OK;
 }
 
 static int run_batch(ger_graph* g, Plan& p) {
@@ -413,18 +421,32 @@ static int run_batch(ger_graph* g, Plan& p) {
     int rc = ensure_lambda(g);
     if (rc) return rc;
     const bool per_query = p.o.per_query != 0;
-    const int slots = per_query ? 1 : (int)std::min<int64_t>(p.q, (int64_t)g->sm_count * 2);
-    int64_t cap = p.o.sparse_cap > 0 ? p.o.sparse_cap : (int64_t)1 << 17;
+    const bool fp64 = p.o.precision == GER_FP64;
     int64_t pool = std::max<int64_t>(g->ws.pool_cap, (int64_t)1 << 22);
-    for (int attempt = 0; attempt < 4; ++attempt) {
-        rc = ensure_ws(g, p.q, std::max(slots, g->ws.slots), cap, pool);
+    for (int attempt = 0; attempt < 6; ++attempt) {
+        rc = ensure_ws(g, p.q, pool);
         if (rc) return rc;
-        if (p.o.precision == GER_FP64) launch_sequence<double>(g, p, per_query);
-        else launch_sequence<float>(g, p, per_query);
         Workspace& w = g->ws;
+        GER_CUDA(cudaMemsetAsync(w.counters, 0, 4 * sizeof(int), p.st));
+        GER_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(SmmCtl), p.st));
+        if (per_query) {
+            for (int64_t i = 0; i < p.q; ++i) {
+                rc = run_queries(g, p, i, 1, fp64);
+                if (rc) return rc;
+            }
+        } else {
+            rc = run_queries(g, p, 0, p.q, fp64);
+            if (rc) return rc;
+        }
+        const int fg = (int)std::min<int64_t>((p.q + 255) / 256, 4096);
+        prof_begin(FAM_FINALIZE, p.st);
+        finalize_kernel<<<fg, 256, 0, p.st>>>(w.st, p.q, p.r, p.stats);
+        prof_end(FAM_FINALIZE, p.st);
+        note_launches(1);
         GER_CUDA(cudaGetLastError());
         GER_CUDA(cudaMemcpyAsync(w.host_rb, w.counters + 1, sizeof(int), cudaMemcpyDeviceToHost, p.st));
-        GER_CUDA(cudaMemcpyAsync(w.host_rb + 1, w.pool_used, sizeof(unsigned long long), cudaMemcpyDeviceToHost, p.st));
+        GER_CUDA(cudaMemcpyAsync(w.host_rb + 1, &w.ctl->cursor, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                 p.st));
         GER_CUDA(cudaStreamSynchronize(p.st));
         prof_collect();
         const int derr = (int)(reinterpret_cast<int*>(w.host_rb)[0]);
@@ -434,20 +456,16 @@ static int run_batch(ger_graph* g, Plan& p) {
             pool = std::max<int64_t>(2 * used, 2 * w.pool_cap);
             continue;
         }
-        if (derr == DERR_CAPACITY && p.o.sparse_cap <= 0 && cap < ((int64_t)1 << 21)) {
-            cap *= 4;
-            continue;
-        }
         return map_device_error(derr);
     }
-    return fail(GER_ERR_CAPACITY, "workspace did not fit after retries");
+    return fail(GER_ERR_CAPACITY, "frontier-table pool did not fit after retries");
 }
 
 // Read-only view of a loaded graph, for entry points defined in other
 // translation units.
 int graph_view(const ger_graph* g, DevGraph* dg, double* lambda, bool* has_lambda, int* device, int* sm_count) {
     if (!g) return fail(GER_ERR_INVALID, "null graph");
-    *dg = DevGraph{g->n, g->nnz, g->row_ptr, g->col_idx};
+    *dg = DevGraph{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info};
     *lambda = g->lambda;
     *has_lambda = g->has_lambda;
     *device = g->device;
@@ -546,6 +564,18 @@ int ger_load_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int 
         ger_free(g);
         return fail(GER_ERR_CUDA, "copying the graph");
     }
+    if (g->nnz < ((int64_t)1 << 32)) {
+        // one 8-byte record per node for the walks: {first edge, degree}
+        std::vector<uint2> info(n);
+        for (int64_t v = 0; v < n; ++v)
+            info[v] = make_uint2((uint32_t)row_ptr[v], (uint32_t)(row_ptr[v + 1] - row_ptr[v]));
+        if (cudaMalloc(&g->node_info, n * sizeof(uint2)) != cudaSuccess ||
+            cudaMemcpy(g->node_info, info.data(), n * sizeof(uint2), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            ger_free(g);
+            return fail(GER_ERR_OOM, "device copy of the node records");
+        }
+    }
     *out = g;
     return GER_OK;
 }
@@ -557,6 +587,7 @@ void ger_free(ger_graph* g) {
     free_ws(g->ws);
     cudaFree(g->row_ptr);
     cudaFree(g->col_idx);
+    cudaFree(g->node_info);
     if (g->stream) cudaStreamDestroy(g->stream);
     delete g;
 }
@@ -614,8 +645,7 @@ static int host_batch(ger_graph* g, int64_t q, const int32_t* s, const int32_t* 
     }
     cudaSetDevice(g->device);
     if (q == 0) return GER_OK;
-    rc = ensure_ws(g, q, std::max(g->ws.slots, 1), g->ws.cap > 0 ? g->ws.cap : ((int64_t)1 << 17),
-                   std::max<int64_t>(g->ws.pool_cap, (int64_t)1 << 22));
+    rc = ensure_ws(g, q, std::max<int64_t>(g->ws.pool_cap, (int64_t)1 << 22));
     if (rc) return rc;
     Workspace& w = g->ws;
     cudaStream_t st = g->stream;

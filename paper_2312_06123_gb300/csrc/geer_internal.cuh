@@ -39,12 +39,41 @@ struct QState {
     int32_t front;            // |V_s u V_t| after the last SMM iteration
 };
 
-// One entry of a query's lookup table: node v and
-// g(v) = s*(v)/d(s) - t*(v)/d(t), the per-visit term of Z_k (Eq. 11).
+// One slot of a query's frontier table (open addressing, linear probing):
+// node v, its support bits (1: in V_s, 2: in V_t) and
+// g(v) = s*(v)/d(s) - t*(v)/d(t), the per-visit term of Z_k (Eq. 11). The
+// table of a query's last SMM iteration is the lookup table of its walks.
 struct __align__(16) GEntry {
-    int32_t v;  // -1: empty
-    int32_t pad;
+    int32_t v;      // -1: empty
+    uint32_t bits;  // support bits (low 2) | owning query index << 2
     double g;
+};
+
+// Per-query scratch of the SMM phase (device memory), reset by each decision.
+struct QSmm {
+    int32_t run;                 // 1 while SMM iterations continue
+    int32_t shift_s, shift_t;    // fixed-point scales 2^shift of s*, t*
+    int32_t lb_target;           // iterations wanted by a fixed policy, -1: rule
+    int32_t want;                // slots requested for the next table, 0: none
+    int32_t pad;
+    int64_t tab_off, tab_cap;    // table of the current frontier
+    int64_t ntab_off, ntab_cap;  // table being filled
+    unsigned long long vol_paper;  // sum_{V_s} d + sum_{V_t} d (Eq. 17)
+    unsigned long long vol_union;  // sum_{V_s u V_t} d: push pairs of the next iteration
+    unsigned long long count;      // |V_s u V_t|
+    unsigned long long max1s, max1t, max2s, max2t;  // bit patterns of non-negative doubles
+    unsigned long long cnt1s, cnt1t;                // entries equal to max1
+    double sval[4];              // s*(s), t*(s), s*(t), t*(t)
+    double inv_ds, inv_dt;       // 1/d(s), 1/d(t)
+};
+
+// Control block of the SMM phase (device memory).
+struct SmmCtl {
+    unsigned long long cursor;   // next free slot of the table pool
+    int32_t nseg[2];             // tables allocated per parity
+    int64_t lo[2], hi[2];        // slot range per parity
+    int32_t n_want;              // queries asking for another iteration
+    int32_t n_heavy;             // chunks of high-degree frontier nodes left to the heavy push
 };
 
 // Per-chunk partial sums of the walk kernel.
@@ -58,6 +87,7 @@ struct DevGraph {
     int64_t n, nnz;
     const int64_t* row_ptr;
     const int32_t* col_idx;
+    const uint2* node_info;  // per node {first edge, degree} when nnz < 2^32, else null
 };
 
 // ---------------------------------------------------------------------------

@@ -11,21 +11,27 @@ struct SmmArgs {
     int32_t nq;            // queries handled by this launch
     int32_t q_index_base;  // batch index of query 0 of this launch
     QState* st;            // nq records
+    QSmm* sm;              // nq records
     const int32_t* s;
     const int32_t* t;
     const double* eps;     // nullable: eps_scalar for every query
     double eps_scalar;
     double lambda, delta;
     int32_t tau, ell_formula, policy, fixed_lb;
-    int32_t nbits;         // bits of the largest node id (radix passes)
-    int64_t cap;           // push pairs per query iteration (sparse capacity)
-    int32_t* scr_i32;      // per CTA: 5 cap + 3 (cap + 2) + 2 int32
-    void* scr_val;         // per CTA: 4 (cap + 2) values
-    uint8_t* scr_bits;     // per CTA: 2 (cap + 2) bytes
-    GEntry* pool;          // lookup tables
+    int64_t max_table;     // largest table a query may request (slots)
+    // table pool: slots of every query-iteration table of the batch
+    GEntry* ent;
+    unsigned long long* sum_s;
+    unsigned long long* sum_t;
+    void* ys;              // T per slot
+    void* yt;              // T per slot
     int64_t pool_cap;
-    unsigned long long* pool_used;
-    int* work_counter;
+    // per-parity lists of the tables allocated in one iteration
+    int32_t* seg_q[2];     // nq entries: owning query
+    int64_t* seg_off[2];   // nq + 1 entries: first slot (last entry: end)
+    int64_t* heavy;        // per chunk of a high-degree frontier node: slot << 20 | chunk index
+    int64_t heavy_cap;
+    SmmCtl* ctl;
     int* err_flag;
 };
 
@@ -45,7 +51,16 @@ struct AmcArgs {
 };
 
 // host launchers (one per kernel)
-void launch_smm_sparse(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
+// SMM phase, level-synchronous over the batch: set-up, then per iteration
+// alloc -> clear -> (seed | push) -> finish -> top2 -> decide.
+void launch_smm_setup(const SmmArgs& a, cudaStream_t st);
+void launch_smm_alloc(const SmmArgs& a, int parity, cudaStream_t st);
+void launch_smm_clear(const SmmArgs& a, int parity, int grid, cudaStream_t st);
+void launch_smm_seed(const SmmArgs& a, cudaStream_t st);
+void launch_smm_push(bool fp64, const SmmArgs& a, int parity_cur, int grid, cudaStream_t st);
+void launch_smm_finish(bool fp64, const SmmArgs& a, int parity, int grid, cudaStream_t st);
+void launch_smm_top2(bool fp64, const SmmArgs& a, int parity, int grid, cudaStream_t st);
+void launch_smm_decide(const SmmArgs& a, int parity, int iter, cudaStream_t st);
 void launch_amc_schedule(const AmcArgs& a, cudaStream_t st);
 void launch_amc_walk(const AmcArgs& a, int grid, cudaStream_t st);
 void launch_amc_reduce(const AmcArgs& a, int grid, cudaStream_t st);
@@ -58,8 +73,9 @@ namespace geer {
 void note_launches(int k);
 
 // kernel families timed by the profiler
-enum Family : int { FAM_SMM_SPARSE = 0, FAM_AMC_SCHEDULE, FAM_AMC_WALK, FAM_AMC_REDUCE, FAM_FINALIZE,
-                    FAM_LANCZOS, FAM_COUNT };
+enum Family : int { FAM_SMM_SETUP = 0, FAM_SMM_ALLOC, FAM_SMM_CLEAR, FAM_SMM_PUSH, FAM_SMM_PUSH_HEAVY, FAM_SMM_FINISH,
+                    FAM_SMM_TOP2, FAM_SMM_DECIDE, FAM_AMC_SCHEDULE, FAM_AMC_WALK, FAM_AMC_REDUCE,
+                    FAM_FINALIZE, FAM_LANCZOS, FAM_COUNT };
 // bracket one launch on stream st with profiler events (no-op when off)
 void prof_begin(int fam, cudaStream_t st);
 void prof_end(int fam, cudaStream_t st);

@@ -10,10 +10,11 @@
 // nothing: no cudaMalloc, no cudaFree, no pinned host buffer, no library
 // routine that allocates. The caller passes the inputs and outputs.
 //
-// Limits: at most kNoAllocMaxQueries queries per call, at most kNoAllocCap
-// push pairs per SMM iteration of a query, kNoAllocPool lookup entries per
-// call; beyond them the call fails with GER_ERR_CAPACITY. The array lives
-// in every GPU that loads this module, until the process exits.
+// Limits: at most kNoAllocMaxQueries queries per call and kNoAllocPool
+// frontier-table slots per call (the tables of every SMM iteration of every
+// query, each a power of two at least twice the iteration's push volume);
+// beyond them the call fails with GER_ERR_CAPACITY. The array lives in every
+// GPU that loads this module, until the process exits.
 #include <mutex>
 
 #include "../../include/geer.h"
@@ -25,24 +26,26 @@ namespace geer {
 namespace {
 
 constexpr int64_t kNoAllocMaxQueries = 64;
-constexpr int kNoAllocSlots = 4;            // CTAs of the SMM kernel
-constexpr int64_t kNoAllocCap = 1 << 16;    // push pairs per SMM iteration
-constexpr int64_t kNoAllocPool = 1 << 19;   // lookup-table entries per call
-constexpr size_t kNoAllocBytes = 32u << 20; // 32 MiB per GPU
+constexpr int64_t kNoAllocPool = 1 << 19;    // frontier-table slots per call
+constexpr size_t kNoAllocBytes = 32u << 20;  // 32 MiB per GPU
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // byte offsets of the regions inside the array
-constexpr size_t kOffCounters = 0;  // work counter, error flag (int), pool cursor (u64)
-constexpr size_t kOffState = align256(kOffCounters + 64);
-constexpr size_t kOffChunk = align256(kOffState + sizeof(QState) * kNoAllocMaxQueries);
+constexpr size_t kOffCounters = 0;  // error flag (int) and spare words
+constexpr size_t kOffCtl = align256(kOffCounters + 64);
+constexpr size_t kOffState = align256(kOffCtl + sizeof(SmmCtl));
+constexpr size_t kOffQSmm = align256(kOffState + sizeof(QState) * kNoAllocMaxQueries);
+constexpr size_t kOffSegQ = align256(kOffQSmm + sizeof(QSmm) * kNoAllocMaxQueries);
+constexpr size_t kOffSegOff = align256(kOffSegQ + sizeof(int32_t) * 2 * kNoAllocMaxQueries);
+constexpr int64_t kNoAllocHeavy = 4096;
+constexpr size_t kOffHeavy = align256(kOffSegOff + sizeof(int64_t) * 2 * (kNoAllocMaxQueries + 1));
+constexpr size_t kOffChunk = align256(kOffHeavy + sizeof(int64_t) * kNoAllocHeavy);
 constexpr size_t kOffPartial = align256(kOffChunk + sizeof(int64_t) * (kNoAllocMaxQueries + 1));
-constexpr size_t kOffI32 = align256(kOffPartial + sizeof(Partial) * kNoAllocMaxQueries * kMaxChunksPerQuery);
-constexpr size_t kF = kNoAllocCap + 2;
-constexpr size_t kOffVal = align256(kOffI32 + sizeof(int32_t) * kNoAllocSlots * (5 * kNoAllocCap + 3 * kF + 2));
-constexpr size_t kOffBits = align256(kOffVal + sizeof(double) * kNoAllocSlots * 4 * kF);
-constexpr size_t kOffPool = align256(kOffBits + kNoAllocSlots * 2 * kF);
-constexpr size_t kEnd = kOffPool + sizeof(GEntry) * kNoAllocPool;
+constexpr size_t kOffEnt = align256(kOffPartial + sizeof(Partial) * kNoAllocMaxQueries * kMaxChunksPerQuery);
+constexpr size_t kOffSums = align256(kOffEnt + sizeof(GEntry) * kNoAllocPool);
+constexpr size_t kOffY = align256(kOffSums + sizeof(uint64_t) * 2 * kNoAllocPool);
+constexpr size_t kEnd = kOffY + sizeof(double) * 2 * kNoAllocPool;
 static_assert(kEnd <= kNoAllocBytes, "no-alloc layout exceeds its array");
 
 // The scratch array. In host code this name is only a stand-in for the
@@ -72,6 +75,13 @@ int scratch_address(int device, unsigned char** out) {
     return GER_OK;
 }
 
+int sync_read_int(const void* dev, int* out, cudaStream_t st) {
+    if (cudaMemcpyAsync(out, dev, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return set_error(GER_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
+    return GER_OK;
+}
+
 }  // namespace
 
 }  // namespace geer
@@ -92,8 +102,6 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
         (o.switch_policy != GER_SWITCH_RULE && o.switch_policy != GER_SWITCH_FIXED) ||
         (o.ell_formula != GER_ELL_REFINED && o.ell_formula != GER_ELL_PENG))
         return set_error(GER_ERR_INVALID, "invalid options");
-    if (o.sparse_cap > kNoAllocCap)
-        return set_error(GER_ERR_CAPACITY, "sparse_cap above the no-alloc limit of 65536 pairs");
     DevGraph dg;
     double lambda;
     bool has_lambda;
@@ -104,26 +112,27 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
         return set_error(GER_ERR_NO_LAMBDA,
                          "spectral bound not available: call ger_spectral_bound or ger_set_spectral_bound first");
     if (q == 0) return GER_OK;
-    cudaError_t e = cudaSetDevice(device);
-    if (e != cudaSuccess) return set_error(GER_ERR_CUDA, "cudaSetDevice failed");
+    if (cudaSetDevice(device) != cudaSuccess) return set_error(GER_ERR_CUDA, "cudaSetDevice failed");
     unsigned char* base = nullptr;
     rc = scratch_address(device, &base);
     if (rc) return rc;
     cudaStream_t st = stream ? reinterpret_cast<cudaStream_t>(stream) : (cudaStream_t)0;
+    const bool fp64 = o.precision == GER_FP64;
 
     int* counters = reinterpret_cast<int*>(base + kOffCounters);
-    unsigned long long* pool_used = reinterpret_cast<unsigned long long*>(base + kOffCounters + 16);
+    SmmCtl* ctl = reinterpret_cast<SmmCtl*>(base + kOffCtl);
     QState* qs = reinterpret_cast<QState*>(base + kOffState);
-    // the array keeps the previous call's contents: reset the counters
-    if (cudaMemsetAsync(base + kOffCounters, 0, 64, st) != cudaSuccess) {
+    // the array keeps the previous call's contents: reset what must start at zero
+    if (cudaMemsetAsync(base + kOffCounters, 0, kOffState - kOffCounters, st) != cudaSuccess) {
         cudaGetLastError();
-        return set_error(GER_ERR_CUDA, "cudaMemsetAsync of the no-alloc counters failed");
+        return set_error(GER_ERR_CUDA, "cudaMemsetAsync of the no-alloc control words failed");
     }
     SmmArgs a;
     a.g = dg;
     a.nq = (int32_t)q;
     a.q_index_base = 0;
     a.st = qs;
+    a.sm = reinterpret_cast<QSmm*>(base + kOffQSmm);
     a.s = s_dev;
     a.t = t_dev;
     a.eps = eps_dev;
@@ -134,20 +143,51 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     a.ell_formula = o.ell_formula;
     a.policy = o.switch_policy;
     a.fixed_lb = o.fixed_ell_b;
-    int nbits = 0;
-    for (int64_t x = dg.n - 1; x > 0; x >>= 1) ++nbits;
-    a.nbits = nbits < 1 ? 1 : nbits;
-    a.cap = o.sparse_cap > 0 ? o.sparse_cap : kNoAllocCap;
-    a.scr_i32 = reinterpret_cast<int32_t*>(base + kOffI32);
-    a.scr_val = base + kOffVal;
-    a.scr_bits = base + kOffBits;
-    a.pool = reinterpret_cast<GEntry*>(base + kOffPool);
+    int64_t max_table = kNoAllocPool;
+    if (o.sparse_cap > 0) {
+        int64_t cap = 16;
+        while (cap < 2 * o.sparse_cap) cap <<= 1;
+        max_table = cap < kNoAllocPool ? cap : kNoAllocPool;
+    }
+    a.max_table = max_table;
+    a.ent = reinterpret_cast<GEntry*>(base + kOffEnt);
+    a.sum_s = reinterpret_cast<unsigned long long*>(base + kOffSums);
+    a.sum_t = a.sum_s + kNoAllocPool;
+    a.ys = base + kOffY;
+    a.yt = fp64 ? (void*)(reinterpret_cast<double*>(base + kOffY) + kNoAllocPool)
+                : (void*)(reinterpret_cast<float*>(base + kOffY) + kNoAllocPool);
     a.pool_cap = kNoAllocPool;
-    a.pool_used = pool_used;
-    a.work_counter = counters;
+    a.seg_q[0] = reinterpret_cast<int32_t*>(base + kOffSegQ);
+    a.seg_q[1] = a.seg_q[0] + kNoAllocMaxQueries;
+    a.seg_off[0] = reinterpret_cast<int64_t*>(base + kOffSegOff);
+    a.seg_off[1] = a.seg_off[0] + (kNoAllocMaxQueries + 1);
+    a.heavy = reinterpret_cast<int64_t*>(base + kOffHeavy);
+    a.heavy_cap = kNoAllocHeavy;
+    a.ctl = ctl;
     a.err_flag = counters + 1;
-    const int grid = (int)(q < kNoAllocSlots ? q : kNoAllocSlots);
-    launch_smm_sparse(o.precision == GER_FP64, a, grid, st);
+    const int grid = sm_count * 8;
+    launch_smm_setup(a, st);
+    launch_smm_alloc(a, 0, st);
+    launch_smm_clear(a, 0, grid, st);
+    launch_smm_seed(a, st);
+    launch_smm_finish(fp64, a, 0, grid, st);
+    launch_smm_top2(fp64, a, 0, grid, st);
+    launch_smm_decide(a, 0, 0, st);
+    note_launches(7);
+    for (int iter = 1; iter < 100000; ++iter) {
+        int n_want = 0;
+        rc = sync_read_int(&ctl->n_want, &n_want, st);
+        if (rc) return rc;
+        if (n_want == 0) break;
+        const int par = iter & 1;
+        launch_smm_alloc(a, par, st);
+        launch_smm_clear(a, par, grid, st);
+        launch_smm_push(fp64, a, par ^ 1, grid, st);
+        launch_smm_finish(fp64, a, par, grid, st);
+        launch_smm_top2(fp64, a, par, grid, st);
+        launch_smm_decide(a, par, iter, st);
+        note_launches(7);
+    }
     AmcArgs m;
     m.g = dg;
     m.nq = (int32_t)q;
@@ -155,7 +195,7 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     m.chunk_begin = reinterpret_cast<int64_t*>(base + kOffChunk);
     m.partial = reinterpret_cast<Partial*>(base + kOffPartial);
     m.partial_cap = kNoAllocMaxQueries * kMaxChunksPerQuery;
-    m.pool = a.pool;
+    m.pool = a.ent;
     m.seed = o.seed;
     m.tau = o.tau;
     m.delta = o.delta;
@@ -167,19 +207,16 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
         launch_amc_reduce(m, (int)q, st);
     }
     launch_finalize(qs, q, r_dev, stats_dev, st);
-    note_launches(2 + 3 * o.tau);
+    note_launches(1 + 3 * o.tau);
     int derr = 0;
-    if (cudaMemcpyAsync(&derr, counters + 1, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
-        return set_error(GER_ERR_CUDA, cudaGetErrorString(cudaGetLastError()));
-    }
+    rc = sync_read_int(counters + 1, &derr, st);
+    if (rc) return rc;
     switch (derr) {
         case DERR_NONE: return GER_OK;
         case DERR_NODE_RANGE: return set_error(GER_ERR_NODE_RANGE, "a query node is outside [0, n) or eps <= 0");
         case DERR_CAPACITY:
-            return set_error(GER_ERR_CAPACITY, "an SMM iteration exceeded the no-alloc limit of 65536 push pairs");
         case DERR_TABLE:
-            return set_error(GER_ERR_CAPACITY, "lookup tables exceeded the no-alloc limit of 524288 entries");
+            return set_error(GER_ERR_CAPACITY, "the frontier tables exceeded the no-alloc limit of 524288 slots");
         default: return set_error(GER_ERR_INVALID, "truncation length undefined (lambda >= 1)");
     }
 }

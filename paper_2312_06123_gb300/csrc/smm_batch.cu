@@ -1,0 +1,622 @@
+// smm_batch.cu -- SMM phase of GEER (Algorithm 3 with the iteration of
+// Algorithm 2), level-synchronous over a whole batch of queries.
+//
+// A query keeps s* and t* (Eq. 15: s*(v) = p_i(v,s), t*(v) = p_i(v,t)) in a
+// frontier table: an open-addressing hash table, in a pool shared by the
+// batch, whose occupied slots are the nodes of V_s u V_t with both values
+// and two support bits. One SMM iteration builds the query's next table by
+// push: every node u of the current table sends x(u) to each v in N(u) --
+// exactly the cost sum_{u in V} d(u) that Eq. (17) charges -- and then
+// y(v) = (sum received) / d(v), the support bits OR-ed (V' = N(V),
+// structurally). Contributions are added as 64-bit fixed-point integers
+// with atomics at scale 2^S_s for s* (S_s = 61 - ceil(log2(d(s)+1))) and
+// 2^S_t for t*: integer addition is associative, so the sums do not depend
+// on thread scheduling, and the scale has headroom since
+// sum_{u in N(v)} p_i(u,s) = d(s) p_{i+1}(s,v) <= d(s) (reversibility). A
+// contribution carries at most 2^-(S+1) absolute rounding.
+//
+// Every kernel covers every query of the batch; one iteration is
+//   alloc  (1 CTA)  : tables for the queries that continue, from the pool;
+//   clear           : empty those tables;
+//   seed | push     : F_0 = {s, t} with s* = e_s, t* = e_t | the push above;
+//   finish          : y values, g(v) = s*(v)/d(s) - t*(v)/d(t), and the
+//                     per-query sums of Eq. (17)'s volume, |V|, max_1;
+//   top2            : max_2 (second element of the descending multiset);
+//   decide          : the four series terms of Algorithm 2 added to r_b in
+//                     FP64, psi (Eq. 9), eta* (Eq. 8), h(l - l_b) and the
+//                     switch (Eq. 17, or a fixed policy).
+// The last table of a query is its walk lookup table (Algorithm 1).
+#include "geer_internal.cuh"
+#include "geer_kernels.h"
+
+namespace geer {
+
+namespace {
+
+// x * 2^S rounded to nearest (ties to even), for 0 <= x, from the bits of x
+// (integer operations only).
+__device__ __forceinline__ unsigned long long to_fixed(float x, int S) {
+    const uint32_t b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xff);
+    uint64_t mant = b & 0x7fffffu;
+    int ex;
+    if (e == 0) {
+        ex = -149;
+    } else {
+        mant |= 0x800000u;
+        ex = e - 150;
+    }
+    const int sh = ex + S;
+    if (sh >= 0) return mant << sh;
+    const int r = -sh;
+    if (r >= 64) return 0ull;
+    const uint64_t q = mant >> r;
+    const uint64_t rem = mant & ((1ull << r) - 1);
+    const uint64_t half = 1ull << (r - 1);
+    return q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+}
+
+__device__ __forceinline__ unsigned long long to_fixed(double x, int S) {
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    uint64_t mant = b & 0xfffffffffffffull;
+    int ex;
+    if (e == 0) {
+        ex = -1074;
+    } else {
+        mant |= 1ull << 52;
+        ex = e - 1075;
+    }
+    const int sh = ex + S;
+    if (sh >= 0) return sh >= 11 ? ~0ull : (mant << sh);  // x <= 1 never reaches sh >= 11
+    const int r = -sh;
+    if (r >= 64) return 0ull;
+    const uint64_t q = mant >> r;
+    const uint64_t rem = mant & ((1ull << r) - 1);
+    const uint64_t half = 1ull << (r - 1);
+    return q + ((rem > half || (rem == half && (q & 1))) ? 1 : 0);
+}
+
+// y = sum * 2^-S / d in T. FP32: the 64-bit integer is rounded to float
+// through its two 32-bit halves (FP32 pipe only); FP64: one conversion.
+template <typename T>
+__device__ __forceinline__ T from_fixed(unsigned long long sum, int S, int64_t d);
+
+template <>
+__device__ __forceinline__ float from_fixed<float>(unsigned long long sum, int S, int64_t d) {
+    const float hi = __uint2float_rn((uint32_t)(sum >> 32));
+    const float lo = __uint2float_rn((uint32_t)sum);
+    const float x = __fmaf_rn(hi, 4294967296.0f, lo);
+    return ldexpf(x, -S) / (float)d;
+}
+
+template <>
+__device__ __forceinline__ double from_fixed<double>(unsigned long long sum, int S, int64_t d) {
+    return ldexp((double)sum, -S) / (double)d;
+}
+
+__device__ __forceinline__ int fixed_shift(int64_t d) {
+    int b = 0;
+    for (uint64_t x = (uint64_t)d; x > 0; x >>= 1) ++b;  // ceil(log2(d + 1))
+    return 61 - b;
+}
+
+// insert v into a table (capacity mask+1); returns its slot
+__device__ __forceinline__ uint32_t table_insert(GEntry* tab, uint32_t mask, int32_t v) {
+    uint32_t h = hash32((uint32_t)v) & mask;
+    for (;;) {
+        const int32_t prev = atomicCAS(&tab[h].v, -1, v);
+        if (prev == -1 || prev == v) return h;
+        h = (h + 1) & mask;
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// set-up: validation, l (Eq. 6 or Eq. 5), first table request
+// ---------------------------------------------------------------------------
+__global__ void smm_setup_kernel(SmmArgs a) {
+    const int64_t* row_ptr = a.g.row_ptr;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < a.nq; q += (int64_t)gridDim.x * blockDim.x) {
+        QState* Q = a.st + q;
+        QSmm* M = a.sm + q;
+        const int32_t s = a.s[q], t = a.t[q];
+        const double eps = a.eps ? a.eps[q] : a.eps_scalar;
+        Q->s = s; Q->t = t; Q->eps = eps; Q->qidx = a.q_index_base + (int32_t)q;
+        Q->batch = 0; Q->err = 0; Q->r_b = 0; Q->r_f = 0; Q->r = 0; Q->psi = 0;
+        Q->volume = 0; Q->h = 0; Q->f_last = 0; Q->eta0 = 0; Q->eta = 0; Q->walks = 0;
+        Q->walk_steps = 0; Q->checksum = 0; Q->ppc = 0; Q->nchunks = 0; Q->table_off = 0;
+        Q->table_mask = -1; Q->front = 0; Q->ell = 0; Q->ell_b = 0; Q->lf = 0; Q->ds = 0; Q->dt = 0;
+        M->run = 0; M->want = 0; M->tab_off = M->tab_cap = M->ntab_off = M->ntab_cap = 0;
+        M->vol_paper = M->vol_union = M->count = 0;
+        M->max1s = M->max1t = M->max2s = M->max2t = M->cnt1s = M->cnt1t = 0;
+        M->sval[0] = M->sval[1] = M->sval[2] = M->sval[3] = 0.0;
+        if (s < 0 || s >= a.g.n || t < 0 || t >= a.g.n || !(eps > 0.0)) {
+            Q->status = ST_ERROR;
+            Q->err = DERR_NODE_RANGE;
+            atomicCAS(a.err_flag, 0, DERR_NODE_RANGE);
+            continue;
+        }
+        if (s == t) {  // r(s,s) = 0 (Definition 1)
+            Q->status = ST_DONE;
+            continue;
+        }
+        const int64_t dsi = row_ptr[s + 1] - row_ptr[s], dti = row_ptr[t + 1] - row_ptr[t];
+        const double ds = (double)dsi, dt = (double)dti;
+        int64_t ell;
+        const double lam = a.lambda;
+        if (!(lam < 1.0)) {
+            ell = -1;
+        } else if (lam <= 0.0) {
+            ell = 0;
+        } else {
+            const double v = a.ell_formula == 1
+                                 ? ceil(log(4.0 / (eps - eps * lam)) / log(1.0 / lam) - 1.0)
+                                 : ceil(log((2.0 / ds + 2.0 / dt) / (eps * (1.0 - lam))) / log(1.0 / lam) - 1.0);
+            ell = v < 0.0 ? 0 : (int64_t)v;
+        }
+        if (ell < 0) {
+            Q->status = ST_ERROR;
+            Q->err = DERR_ELL;
+            atomicCAS(a.err_flag, 0, DERR_ELL);
+            continue;
+        }
+        Q->status = ST_SMM;
+        Q->ds = (int32_t)dsi;
+        Q->dt = (int32_t)dti;
+        Q->ell = (int32_t)ell;
+        M->shift_s = fixed_shift(dsi);
+        M->shift_t = fixed_shift(dti);
+        M->inv_ds = 1.0 / ds;
+        M->inv_dt = 1.0 / dt;
+        M->lb_target = a.policy == 2 ? (a.fixed_lb < 0 ? (int32_t)ell : min(a.fixed_lb, (int32_t)ell)) : -1;
+        M->want = 8;  // F_0 = {s, t}
+    }
+}
+
+// ---------------------------------------------------------------------------
+// alloc (one CTA): tables for the queries that asked for one, in query order
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kCta) smm_alloc_kernel(SmmArgs a, int parity) {
+    __shared__ int64_t scan[kWarps + 1];
+    __shared__ int64_t carry, seg_carry;
+    const int tid = threadIdx.x;
+    SmmCtl* C = a.ctl;
+    const unsigned long long base = C->cursor;
+    if (tid == 0) {
+        carry = 0;
+        seg_carry = 0;
+    }
+    __syncthreads();
+    int32_t* seg_q = a.seg_q[parity];
+    int64_t* seg_off = a.seg_off[parity];
+    for (int64_t tile = 0; tile < a.nq; tile += kCta) {
+        const int64_t q = tile + tid;
+        int64_t want = 0;
+        if (q < a.nq) {
+            QSmm* M = a.sm + q;
+            want = M->want;
+            M->want = 0;
+            M->run = want > 0;
+        }
+        int64_t tot, ntot;
+        const int64_t ex = cta_excl_scan(want, scan, &tot);
+        const int64_t sx = cta_excl_scan(want > 0 ? 1 : 0, scan, &ntot);
+        if (want > 0) {
+            const int64_t off = (int64_t)base + carry + ex;
+            QSmm* M = a.sm + q;
+            M->ntab_off = off;
+            M->ntab_cap = want;
+            seg_q[seg_carry + sx] = (int32_t)q;
+            seg_off[seg_carry + sx] = off;
+            if (off + want > a.pool_cap) {  // the pool is too small for this batch
+                a.st[q].status = ST_ERROR;
+                a.st[q].err = DERR_TABLE;
+                M->run = 0;
+                atomicCAS(a.err_flag, 0, DERR_TABLE);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            carry += tot;
+            seg_carry += ntot;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        int64_t hi = (int64_t)base + carry;
+        if (hi > a.pool_cap) hi = a.pool_cap;
+        seg_off[seg_carry] = hi;
+        C->nseg[parity] = (int32_t)seg_carry;
+        C->lo[parity] = (int64_t)base;
+        C->hi[parity] = hi;
+        C->cursor = base + (unsigned long long)carry;
+        C->n_want = 0;
+        C->n_heavy = 0;
+    }
+}
+
+// clear the tables allocated for `parity`
+__global__ void smm_clear_kernel(SmmArgs a, int parity) {
+    const int64_t lo = a.ctl->lo[parity], hi = a.ctl->hi[parity];
+    for (int64_t j = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < hi;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        GEntry e;
+        e.v = -1;
+        e.bits = 0;
+        e.g = 0.0;
+        a.ent[j] = e;
+        a.sum_s[j] = 0ull;
+        a.sum_t[j] = 0ull;
+    }
+}
+
+// F_0 = {s, t} with s* = e_s, t* = e_t: sums d(s) 2^S_s and d(t) 2^S_t make
+// y = sum / d = 1 exactly in the finish kernel
+__global__ void smm_seed_kernel(SmmArgs a) {
+    const int nseg = a.ctl->nseg[0];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nseg; k += gridDim.x * blockDim.x) {
+        const int q = a.seg_q[0][k];
+        const QSmm* M = a.sm + q;
+        if (!M->run) continue;
+        const QState* Q = a.st + q;
+        GEntry* tab = a.ent + M->ntab_off;
+        const uint32_t mask = (uint32_t)(M->ntab_cap - 1);
+        uint32_t hs = table_insert(tab, mask, Q->s);
+        tab[hs].bits = 1u | ((uint32_t)q << 2);
+        a.sum_s[M->ntab_off + hs] = (unsigned long long)Q->ds << M->shift_s;
+        uint32_t ht = table_insert(tab, mask, Q->t);
+        tab[ht].bits = 2u | ((uint32_t)q << 2);
+        a.sum_t[M->ntab_off + ht] = (unsigned long long)Q->dt << M->shift_t;
+    }
+}
+
+constexpr int64_t kLightMax = 1024;  // neighbours a single warp pushes
+constexpr int64_t kHeavyChunk = 1024;
+
+// push the values of table slot j (node u of query q) to neighbours
+// [pb, pe) of u; called by `nthreads` cooperating threads with rank `rank`
+template <typename T>
+__device__ __forceinline__ void push_range(const SmmArgs& a, int64_t j, int q, int64_t pb, int64_t pe, int rank,
+                                           int nthreads) {
+    const T* ys = reinterpret_cast<const T*>(a.ys);
+    const T* yt = reinterpret_cast<const T*>(a.yt);
+    const QSmm* M = a.sm + q;
+    GEntry* ntab = a.ent + M->ntab_off;
+    const uint32_t nmask = (uint32_t)(M->ntab_cap - 1);
+    const T xs = ys[j], xt = yt[j];
+    const unsigned long long fs = xs != T(0) ? to_fixed(xs, M->shift_s) : 0ull;
+    const unsigned long long ft = xt != T(0) ? to_fixed(xt, M->shift_t) : 0ull;
+    const uint32_t bits = a.ent[j].bits;  // support bits and the owner, unchanged
+    unsigned long long* ss = a.sum_s + M->ntab_off;
+    unsigned long long* tt = a.sum_t + M->ntab_off;
+    const int32_t* col_idx = a.g.col_idx;
+    for (int64_t p = pb + rank; p < pe; p += nthreads) {
+        const int32_t v = col_idx[p];
+        const uint32_t h = table_insert(ntab, nmask, v);
+        if (fs) atomicAdd(&ss[h], fs);
+        if (ft) atomicAdd(&tt[h], ft);
+        atomicOr(&ntab[h].bits, bits);
+    }
+}
+
+// push: every node of a continuing query's current table sends its values
+// to its neighbours in the query's next table. One warp per table slot; a
+// node with more than kLightMax neighbours goes to the heavy list instead.
+template <typename T>
+__global__ void __launch_bounds__(256) smm_push_kernel(SmmArgs a, int parity_cur) {
+    const int lane = threadIdx.x & 31;
+    const int64_t lo = a.ctl->lo[parity_cur], hi = a.ctl->hi[parity_cur];
+    const int64_t* row_ptr = a.g.row_ptr;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = lo + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); j < hi; j += nwarps) {
+        const GEntry e = a.ent[j];
+        if (e.v < 0) continue;
+        const int q = (int)(e.bits >> 2);
+        if (!a.sm[q].run) continue;
+        const int64_t rb = row_ptr[e.v], re = row_ptr[e.v + 1];
+        if (re - rb > kLightMax) {
+            // hand the node's neighbour list, in chunks, to the heavy push
+            const int nch = (int)((re - rb + kHeavyChunk - 1) / kHeavyChunk);
+            int first = 0;
+            if (lane == 0) first = atomicAdd(&a.ctl->n_heavy, nch);
+            first = __shfl_sync(0xffffffffu, first, 0);
+            if ((int64_t)first + nch <= a.heavy_cap) {
+                for (int c = lane; c < nch; c += 32) a.heavy[first + c] = (j << 20) | (int64_t)c;
+                continue;
+            }
+        }
+        push_range<T>(a, j, q, rb, re, lane, 32);
+    }
+}
+
+// heavy push: one CTA per chunk of kHeavyChunk neighbours of a
+// high-degree node
+template <typename T>
+__global__ void __launch_bounds__(256) smm_push_heavy_kernel(SmmArgs a) {
+    const int64_t nc = min((int64_t)a.ctl->n_heavy, a.heavy_cap);
+    const int64_t* row_ptr = a.g.row_ptr;
+    for (int64_t c = blockIdx.x; c < nc; c += gridDim.x) {
+        const int64_t rec = a.heavy[c];
+        const int64_t j = rec >> 20, part = rec & 0xfffff;
+        const GEntry e = a.ent[j];
+        const int q = (int)(e.bits >> 2);
+        const int64_t rb = row_ptr[e.v], re = row_ptr[e.v + 1];
+        const int64_t pb = rb + part * kHeavyChunk;
+        push_range<T>(a, j, q, pb, min(pb + kHeavyChunk, re), threadIdx.x, blockDim.x);
+    }
+}
+
+// finish: y(v) = sum / d(v) in T, g(v), and the per-query sums (vol of
+// Eq. 17, the next push volume, |V|, max_1), aggregated per warp
+template <typename T>
+__global__ void __launch_bounds__(256) smm_finish_kernel(SmmArgs a, int parity) {
+    const int64_t lo = a.ctl->lo[parity], hi = a.ctl->hi[parity];
+    T* ys = reinterpret_cast<T*>(a.ys);
+    T* yt = reinterpret_cast<T*>(a.yt);
+    const int64_t* row_ptr = a.g.row_ptr;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // warp-uniform trip count so that every lane reaches the warp reductions
+    for (int64_t base = lo + (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < hi; base += stride) {
+        const int64_t j = base + (threadIdx.x & 31);
+        int q = -1;
+        unsigned long long vp = 0, vu = 0, cnt = 0, m1s = 0, m1t = 0;
+        if (j < hi) {
+            const GEntry e = a.ent[j];
+            const int32_t v = e.v;
+            if (v >= 0) {
+                q = (int)(e.bits >> 2);
+                QSmm* M = a.sm + q;
+                if (M->run) {
+                    const QState* Q = a.st + q;
+                    const int64_t dv = row_ptr[v + 1] - row_ptr[v];
+                    const T s_v = from_fixed<T>(a.sum_s[j], M->shift_s, dv);
+                    const T t_v = from_fixed<T>(a.sum_t[j], M->shift_t, dv);
+                    ys[j] = s_v;
+                    yt[j] = t_v;
+                    a.ent[j].g = (double)s_v * M->inv_ds - (double)t_v * M->inv_dt;
+                    const uint32_t bits = e.bits & 3u;
+                    vp = (unsigned long long)(dv * (int64_t)((bits & 1u) + ((bits >> 1) & 1u)));
+                    vu = (unsigned long long)dv;
+                    cnt = 1;
+                    m1s = (unsigned long long)__double_as_longlong((double)s_v);
+                    m1t = (unsigned long long)__double_as_longlong((double)t_v);
+                    if (v == Q->s) {
+                        M->sval[0] = (double)s_v;
+                        M->sval[1] = (double)t_v;
+                    }
+                    if (v == Q->t) {
+                        M->sval[2] = (double)s_v;
+                        M->sval[3] = (double)t_v;
+                    }
+                } else {
+                    q = -1;
+                }
+            }
+        }
+        const int q0 = __shfl_sync(0xffffffffu, q, 0);
+        const bool uniform = __all_sync(0xffffffffu, q == q0 || q < 0);
+        int qa = q;
+        if (uniform) {
+            // q0 may be -1 when lane 0's slot is empty: take any valid lane's query
+            const unsigned has = __ballot_sync(0xffffffffu, q >= 0);
+            qa = has ? __shfl_sync(0xffffffffu, q, __ffs(has) - 1) : -1;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                vp += __shfl_xor_sync(0xffffffffu, vp, o);
+                vu += __shfl_xor_sync(0xffffffffu, vu, o);
+                cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+                m1s = max(m1s, __shfl_xor_sync(0xffffffffu, m1s, o));
+                m1t = max(m1t, __shfl_xor_sync(0xffffffffu, m1t, o));
+            }
+            if ((threadIdx.x & 31) != 0) qa = -1;
+        }
+        if (qa >= 0 && cnt > 0) {
+            QSmm* M = a.sm + qa;
+            atomicAdd(&M->vol_paper, vp);
+            atomicAdd(&M->vol_union, vu);
+            atomicAdd(&M->count, cnt);
+            atomicMax(&M->max1s, m1s);
+            atomicMax(&M->max1t, m1t);
+        }
+    }
+}
+
+// top2: max_2 of each vector = the largest value below max_1, or max_1 itself
+// when it occurs twice (the multiset's second element); aggregated per warp
+template <typename T>
+__global__ void __launch_bounds__(256) smm_top2_kernel(SmmArgs a, int parity) {
+    const int64_t lo = a.ctl->lo[parity], hi = a.ctl->hi[parity];
+    const T* ys = reinterpret_cast<const T*>(a.ys);
+    const T* yt = reinterpret_cast<const T*>(a.yt);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = lo + (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < hi; base += stride) {
+        const int64_t j = base + (threadIdx.x & 31);
+        int q = -1;
+        unsigned long long m2s = 0, m2t = 0, c1s = 0, c1t = 0;
+        const GEntry e = j < hi ? a.ent[j] : GEntry{-1, 0u, 0.0};
+        if (e.v >= 0) {
+            q = (int)(e.bits >> 2);
+            const QSmm* M = a.sm + q;
+            if (M->run) {
+                const unsigned long long bs = (unsigned long long)__double_as_longlong((double)ys[j]);
+                const unsigned long long bt = (unsigned long long)__double_as_longlong((double)yt[j]);
+                if (bs < M->max1s) m2s = bs; else c1s = 1;
+                if (bt < M->max1t) m2t = bt; else c1t = 1;
+            } else {
+                q = -1;
+            }
+        }
+        const int q0 = __shfl_sync(0xffffffffu, q, 0);
+        const bool uniform = __all_sync(0xffffffffu, q == q0 || q < 0);
+        int qa = q;
+        if (uniform) {
+            const unsigned has = __ballot_sync(0xffffffffu, q >= 0);
+            qa = has ? __shfl_sync(0xffffffffu, q, __ffs(has) - 1) : -1;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                m2s = max(m2s, __shfl_xor_sync(0xffffffffu, m2s, o));
+                m2t = max(m2t, __shfl_xor_sync(0xffffffffu, m2t, o));
+                c1s += __shfl_xor_sync(0xffffffffu, c1s, o);
+                c1t += __shfl_xor_sync(0xffffffffu, c1t, o);
+            }
+            if ((threadIdx.x & 31) != 0) qa = -1;
+        }
+        if (qa >= 0) {
+            QSmm* M = a.sm + qa;
+            if (m2s) atomicMax(&M->max2s, m2s);
+            if (m2t) atomicMax(&M->max2t, m2t);
+            if (c1s) atomicAdd(&M->cnt1s, c1s);
+            if (c1t) atomicAdd(&M->cnt1t, c1t);
+        }
+    }
+}
+
+// psi (Eq. 9), eta0 = max(1, ceil(eta*/2^(tau-1))) with eta* from Eq. (8),
+// h = (2^tau - 1) eta0
+__device__ void switch_quantities(int64_t lf, double s1, double s2, double t1, double t2, double ds, double dt,
+                                  double eps, double delta, int tau, double* psi, int64_t* eta0, double* h) {
+    const double up = (double)((lf + 1) / 2), dn = (double)(lf / 2);
+    const double p = 2.0 * up * (s1 / ds + t1 / dt) + 2.0 * dn * (s2 / ds + t2 / dt);
+    const double es = 2.0 * p * p * log(2.0 * (double)tau / delta) / (eps * eps);
+    int64_t e0 = (int64_t)ceil(es / ldexp(1.0, tau - 1));
+    if (e0 < 1) e0 = 1;
+    *psi = p;
+    *eta0 = e0;
+    *h = (double)((((int64_t)1 << tau) - 1) * e0);
+}
+
+// decide: one thread per query whose table was just finished
+__global__ void smm_decide_kernel(SmmArgs a, int parity, int iter) {
+    const int nseg = a.ctl->nseg[parity];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nseg; k += gridDim.x * blockDim.x) {
+        const int q = a.seg_q[parity][k];
+        QSmm* M = a.sm + q;
+        QState* Q = a.st + q;
+        if (!M->run || Q->status != ST_SMM) continue;
+        const double ds = (double)Q->ds, dt = (double)Q->dt;
+        // Algorithm 2: r_b += s*(s)/d(s) + t*(t)/d(t) - s*(t)/d(s) - t*(s)/d(t)
+        Q->r_b += M->sval[0] / ds + M->sval[3] / dt - M->sval[2] / ds - M->sval[1] / dt;
+        const int64_t lb = iter;
+        const int64_t ell = Q->ell;
+        // max_1, max_2 of the full vectors: entries outside the table are zero,
+        // so the accumulators starting at 0.0 already include them
+        const double s1 = __longlong_as_double((long long)M->max1s);
+        const double t1 = __longlong_as_double((long long)M->max1t);
+        const double s2 = M->cnt1s >= 2 ? s1 : __longlong_as_double((long long)M->max2s);
+        const double t2 = M->cnt1t >= 2 ? t1 : __longlong_as_double((long long)M->max2t);
+        const double vol = (double)M->vol_paper;
+        const int64_t lf = ell - lb;
+        double psi = 0.0, h = 0.0;
+        int64_t eta0 = 0;
+        if (lf > 0) switch_quantities(lf, s1, s2, t1, t2, ds, dt, Q->eps, a.delta, a.tau, &psi, &eta0, &h);
+        bool go;
+        if (iter == 0) {
+            go = M->lb_target >= 0 ? (M->lb_target > 0) : (ell >= 1);  // the loop runs once when l >= 1
+        } else {
+            const bool free_stop = (vol > h) || (lb >= ell);  // Eq. (17)
+            go = M->lb_target >= 0 ? (lb < M->lb_target) : !free_stop;
+        }
+        // the table just finished holds the current frontier
+        M->tab_off = M->ntab_off;
+        M->tab_cap = M->ntab_cap;
+        if (go) {
+            int64_t cap = 16;
+            while (cap < 2 * (int64_t)M->vol_union) cap <<= 1;
+            if (cap > a.max_table) {
+                Q->status = ST_ERROR;
+                Q->err = DERR_CAPACITY;
+                Q->ell_b = (int32_t)lb;
+                M->run = 0;
+                atomicCAS(a.err_flag, 0, DERR_CAPACITY);
+                continue;
+            }
+            M->want = (int32_t)cap;
+            atomicAdd(&a.ctl->n_want, 1);
+        } else {
+            Q->ell_b = (int32_t)lb;
+            Q->lf = (int32_t)lf;
+            Q->psi = psi;
+            Q->volume = vol;
+            Q->h = h;
+            Q->eta0 = eta0;
+            Q->eta = eta0;
+            Q->front = (int32_t)M->count;
+            Q->table_off = M->tab_off;
+            Q->table_mask = (int32_t)(M->tab_cap - 1);
+            if (lf > 0) {
+                Q->status = ST_AMC;
+            } else {
+                Q->status = ST_DONE;
+                Q->r = Q->r_b;
+            }
+        }
+        M->vol_paper = M->vol_union = M->count = 0;
+        M->max1s = M->max1t = M->max2s = M->max2t = M->cnt1s = M->cnt1t = 0;
+        M->sval[0] = M->sval[1] = M->sval[2] = M->sval[3] = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+void launch_smm_setup(const SmmArgs& a, cudaStream_t st) {
+    const int grid = (int)std::min<int64_t>((a.nq + 255) / 256, 1024);
+    prof_begin(FAM_SMM_SETUP, st);
+    smm_setup_kernel<<<grid, 256, 0, st>>>(a);
+    prof_end(FAM_SMM_SETUP, st);
+}
+
+void launch_smm_alloc(const SmmArgs& a, int parity, cudaStream_t st) {
+    prof_begin(FAM_SMM_ALLOC, st);
+    smm_alloc_kernel<<<1, kCta, 0, st>>>(a, parity);
+    prof_end(FAM_SMM_ALLOC, st);
+}
+
+void launch_smm_clear(const SmmArgs& a, int parity, int grid, cudaStream_t st) {
+    prof_begin(FAM_SMM_CLEAR, st);
+    smm_clear_kernel<<<grid, 256, 0, st>>>(a, parity);
+    prof_end(FAM_SMM_CLEAR, st);
+}
+
+void launch_smm_seed(const SmmArgs& a, cudaStream_t st) {
+    const int grid = (int)std::min<int64_t>((a.nq + 255) / 256, 1024);
+    prof_begin(FAM_SMM_PUSH, st);
+    smm_seed_kernel<<<grid, 256, 0, st>>>(a);
+    prof_end(FAM_SMM_PUSH, st);
+}
+
+void launch_smm_push(bool fp64, const SmmArgs& a, int parity_cur, int grid, cudaStream_t st) {
+    prof_begin(FAM_SMM_PUSH, st);
+    if (fp64) smm_push_kernel<double><<<grid, 256, 0, st>>>(a, parity_cur);
+    else smm_push_kernel<float><<<grid, 256, 0, st>>>(a, parity_cur);
+    prof_end(FAM_SMM_PUSH, st);
+    prof_begin(FAM_SMM_PUSH_HEAVY, st);
+    if (fp64) smm_push_heavy_kernel<double><<<grid, 256, 0, st>>>(a);
+    else smm_push_heavy_kernel<float><<<grid, 256, 0, st>>>(a);
+    prof_end(FAM_SMM_PUSH_HEAVY, st);
+}
+
+void launch_smm_finish(bool fp64, const SmmArgs& a, int parity, int grid, cudaStream_t st) {
+    prof_begin(FAM_SMM_FINISH, st);
+    if (fp64) smm_finish_kernel<double><<<grid, 256, 0, st>>>(a, parity);
+    else smm_finish_kernel<float><<<grid, 256, 0, st>>>(a, parity);
+    prof_end(FAM_SMM_FINISH, st);
+}
+
+void launch_smm_top2(bool fp64, const SmmArgs& a, int parity, int grid, cudaStream_t st) {
+    prof_begin(FAM_SMM_TOP2, st);
+    if (fp64) smm_top2_kernel<double><<<grid, 256, 0, st>>>(a, parity);
+    else smm_top2_kernel<float><<<grid, 256, 0, st>>>(a, parity);
+    prof_end(FAM_SMM_TOP2, st);
+}
+
+void launch_smm_decide(const SmmArgs& a, int parity, int iter, cudaStream_t st) {
+    const int grid = (int)std::min<int64_t>((a.nq + 255) / 256, 1024);
+    prof_begin(FAM_SMM_DECIDE, st);
+    smm_decide_kernel<<<grid, 256, 0, st>>>(a, parity, iter);
+    prof_end(FAM_SMM_DECIDE, st);
+}
+
+}  // namespace geer
