@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -18,8 +19,11 @@
 namespace geer {
 
 static std::atomic<int64_t> g_launches{0};
+static bool g_capturing = false;  // graph capture: launches are counted per replay instead
 constexpr int64_t kHeavyCap = 1 << 16;
-void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+void note_launches(int k) {
+    if (!g_capturing) g_launches.fetch_add(k, std::memory_order_relaxed);
+}
 
 // ---------------------------------------------------------------------------
 // profiler: CUDA events around launches, on the launch stream
@@ -32,6 +36,8 @@ struct ProfRec {
     cudaEvent_t a, b;
 };
 static bool g_prof_on = false;
+static bool g_prof_suspend = false;             // inside a graph's while body: no event records
+static std::vector<ProfRec>* g_prof_sink = nullptr;  // graph capture: keep the records with the graph
 static std::vector<ProfRec> g_prof_pending;
 static std::vector<cudaEvent_t> g_prof_free;
 static cudaEvent_t g_prof_open[FAM_COUNT];
@@ -49,18 +55,39 @@ static cudaEvent_t prof_event() {
     return e;
 }
 
+// Inside a graph capture the record must be an external event-record node,
+// so that the event is really recorded each time the graph runs.
+static void prof_record(cudaEvent_t e, cudaStream_t st) {
+    if (g_prof_sink) cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else cudaEventRecord(e, st);
+}
+
 void prof_begin(int fam, cudaStream_t st) {
-    if (!g_prof_on) return;
+    if (!g_prof_on || g_prof_suspend) return;
     g_prof_open[fam] = prof_event();
-    cudaEventRecord(g_prof_open[fam], st);
+    prof_record(g_prof_open[fam], st);
 }
 
 void prof_end(int fam, cudaStream_t st) {
-    if (!g_prof_on || !g_prof_open[fam]) return;
+    if (!g_prof_on || g_prof_suspend || !g_prof_open[fam]) return;
     cudaEvent_t b = prof_event();
-    cudaEventRecord(b, st);
-    g_prof_pending.push_back({fam, g_prof_open[fam], b});
+    prof_record(b, st);
+    (g_prof_sink ? *g_prof_sink : g_prof_pending).push_back({fam, g_prof_open[fam], b});
     g_prof_open[fam] = nullptr;
+}
+
+// fold the records kept by a replayed graph (after it has completed)
+static void prof_collect_graph(const std::vector<ProfRec>& recs) {
+    if (!g_prof_on) return;
+    for (const ProfRec& r : recs) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            g_prof_ms[r.fam] += ms;
+            g_prof_launches[r.fam] += 1;
+        } else {
+            cudaGetLastError();
+        }
+    }
 }
 
 void prof_collect() {
@@ -129,6 +156,24 @@ struct Workspace {
 
 }  // namespace geer
 
+namespace geer {
+// The captured launch sequence of one batch shape (see run_batch).
+struct BatchGraph {
+    bool valid = false;
+    int64_t nq = 0;
+    bool fp64 = false;
+    ger_options o{};
+    double lambda = 0;
+    const void* pool = nullptr;
+    const void* state = nullptr;
+    bool prof = false;
+    int64_t launches = 0;  // kernels outside the while body
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<ProfRec> prof_recs;
+};
+}  // namespace geer
+
 struct ger_graph {
     int device = 0;
     int sm_count = 0;
@@ -139,7 +184,9 @@ struct ger_graph {
     bool has_lambda = false;
     double lambda = 0, lam2 = 0, lamn = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t stream2 = nullptr;  // captures the SMM while body
     geer::Workspace ws;
+    geer::BatchGraph bg;
 };
 
 namespace geer {
@@ -325,14 +372,11 @@ static int map_device_error(int e) {
     }
 }
 
-// The GEER launch sequence for queries [q0, q0 + nq) of the plan: the SMM
-// iterations (one host round trip per iteration to learn whether any query
-// continues), then tau AMC rounds. Returns a GER_* status.
-static int run_queries(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool fp64) {
+// Launch arguments of the SMM and AMC phases for queries [q0, q0 + nq).
+static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool fp64, SmmArgs* pa, AmcArgs* pm) {
     Workspace& w = g->ws;
     DevGraph dg{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info};
-    const int tau = p.o.tau;
-    SmmArgs a;
+    SmmArgs& a = *pa;
     a.g = dg;
     a.nq = (int32_t)nq;
     a.q_index_base = (int32_t)q0;
@@ -344,7 +388,7 @@ static int run_queries(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool
     a.eps_scalar = p.eps_scalar;
     a.lambda = g->lambda;
     a.delta = p.o.delta;
-    a.tau = tau;
+    a.tau = p.o.tau;
     a.ell_formula = p.o.ell_formula;
     a.policy = p.o.switch_policy;
     a.fixed_lb = p.o.fixed_ell_b;
@@ -369,30 +413,7 @@ static int run_queries(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool
     a.heavy_cap = kHeavyCap;
     a.ctl = w.ctl;
     a.err_flag = w.counters + 1;
-    const int grid = g->sm_count * 8;
-    launch_smm_setup(a, p.st);
-    launch_smm_alloc(a, 0, p.st);
-    launch_smm_clear(a, 0, grid, p.st);
-    launch_smm_seed(a, p.st);
-    launch_smm_finish(fp64, a, 0, grid, p.st);
-    launch_smm_top2(fp64, a, 0, grid, p.st);
-    launch_smm_decide(a, 0, 0, p.st);
-    note_launches(7);
-    int32_t* n_want = reinterpret_cast<int32_t*>(w.host_rb + 2);
-    for (int iter = 1; iter < 100000; ++iter) {
-        GER_CUDA(cudaMemcpyAsync(n_want, &w.ctl->n_want, sizeof(int32_t), cudaMemcpyDeviceToHost, p.st));
-        GER_CUDA(cudaStreamSynchronize(p.st));
-        if (*n_want == 0) break;
-        const int par = iter & 1;
-        launch_smm_alloc(a, par, p.st);
-        launch_smm_clear(a, par, grid, p.st);
-        launch_smm_push(fp64, a, par ^ 1, grid, p.st);
-        launch_smm_finish(fp64, a, par, grid, p.st);
-        launch_smm_top2(fp64, a, par, grid, p.st);
-        launch_smm_decide(a, par, iter, p.st);
-        note_launches(7);
-    }
-    AmcArgs m;
+    AmcArgs& m = *pm;
     m.g = dg;
     m.nq = (int32_t)nq;
     m.st = w.st + q0;
@@ -401,53 +422,212 @@ static int run_queries(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool
     m.partial_cap = w.partial_cap;
     m.pool = w.ent;
     m.seed = p.o.seed;
-    m.tau = tau;
+    m.tau = p.o.tau;
     m.delta = p.o.delta;
     m.err_flag = w.counters + 1;
+}
+
+// The tau AMC rounds (schedule -> walks -> batch statistics).
+static void issue_amc(ger_graph* g, AmcArgs m, int64_t nq, cudaStream_t st) {
     const int red_grid = (int)std::min<int64_t>(nq, 4096);
     const int walk_grid = nq == 1 ? g->sm_count * 2 : g->sm_count * 8;
-    for (int b = 1; b <= tau; ++b) {
+    for (int b = 1; b <= m.tau; ++b) {
         m.batch = b;
-        launch_amc_schedule(m, p.st);
-        launch_amc_walk(m, walk_grid, p.st);
-        launch_amc_reduce(m, red_grid, p.st);
+        launch_amc_schedule(m, st);
+        launch_amc_walk(m, walk_grid, st);
+        launch_amc_reduce(m, red_grid, st);
     }
-    note_launches(3 * tau);
+    note_launches(3 * m.tau);
+}
+
+// The GEER launch sequence for queries [q0, q0 + nq), stream-ordered, with
+// one host round trip per SMM iteration to learn whether any query
+// continues.
+static int run_queries(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool fp64) {
+    Workspace& w = g->ws;
+    SmmArgs a;
+    AmcArgs m;
+    make_args(g, p, q0, nq, fp64, &a, &m);
+    const int grid = g->sm_count * 8;
+    launch_smm_start(fp64, a, grid, p.st);
+    launch_smm_advance(a, 0, false, p.st);
+    note_launches(8);
+    int32_t* n_want = reinterpret_cast<int32_t*>(w.host_rb + 2);
+    for (int iter = 1; iter < 100000; ++iter) {
+        GER_CUDA(cudaMemcpyAsync(n_want, &w.ctl->n_want, sizeof(int32_t), cudaMemcpyDeviceToHost, p.st));
+        GER_CUDA(cudaStreamSynchronize(p.st));
+        if (*n_want == 0) break;
+        launch_smm_iteration(fp64, a, grid, p.st);
+        launch_smm_advance(a, 0, false, p.st);
+        note_launches(8);
+    }
+    issue_amc(g, m, nq, p.st);
     return GER_OK;
 }
 
+static void destroy_graph(BatchGraph& bg) {
+    if (bg.exec) cudaGraphExecDestroy(bg.exec);
+    if (bg.graph) cudaGraphDestroy(bg.graph);
+    for (const ProfRec& r : bg.prof_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    bg = BatchGraph();
+}
+
+static bool same_key(const BatchGraph& bg, const Plan& p, bool fp64, const ger_graph* g) {
+    return bg.valid && bg.nq == p.q && bg.fp64 == fp64 && std::memcmp(&bg.o, &p.o, sizeof(ger_options)) == 0 &&
+           bg.lambda == g->lambda && bg.pool == g->ws.ent && bg.state == g->ws.st && bg.prof == g_prof_on;
+}
+
+// Capture the whole batch as one graph: the initial SMM iteration, a
+// conditional while node over the further SMM iterations (its condition
+// set on the device by the advance kernel), the tau AMC rounds and the
+// outputs. The plan must read its inputs from, and write its outputs to,
+// the workspace buffers, so that one capture serves every batch of the
+// same shape.
+static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
+    BatchGraph& bg = g->bg;
+    destroy_graph(bg);
+    Workspace& w = g->ws;
+    cudaStream_t st = g->stream, st2 = g->stream2;
+    SmmArgs a;
+    AmcArgs m;
+    make_args(g, p, 0, p.q, fp64, &a, &m);
+    const int grid = g->sm_count * 8;
+    cudaGraph_t graph = nullptr;
+    GER_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle handle;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 0, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return cuda_fail(e, "cudaGraphConditionalHandleCreate");
+    }
+    g_prof_sink = &bg.prof_recs;
+    g_capturing = true;
+    e = cudaStreamBeginCaptureToGraph(st, graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(w.counters, 0, 4 * sizeof(int), st);
+        cudaMemsetAsync(w.ctl, 0, sizeof(SmmCtl), st);
+        launch_smm_start(fp64, a, grid, st);
+        launch_smm_advance(a, handle, true, st);
+        cudaStreamCaptureStatus cs;
+        const cudaGraphNode_t* deps = nullptr;
+        size_t ndeps = 0;
+        cudaGraph_t cap = nullptr;
+        e = cudaStreamGetCaptureInfo(st, &cs, nullptr, &cap, &deps, nullptr, &ndeps);
+        cudaGraphNode_t cnode = nullptr;
+        cudaGraphNodeParams cp = {};
+        if (e == cudaSuccess) {
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = handle;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            e = cudaGraphAddNode(&cnode, cap, deps, nullptr, ndeps, &cp);
+        }
+        if (e == cudaSuccess)
+            e = cudaStreamUpdateCaptureDependencies(st, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (e == cudaSuccess) {
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            e = cudaStreamBeginCaptureToGraph(st2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+            if (e == cudaSuccess) {
+                g_prof_suspend = true;  // no event records inside a conditional body
+                launch_smm_iteration(fp64, a, grid, st2);
+                launch_smm_advance(a, handle, true, st2);
+                g_prof_suspend = false;
+                e = cudaStreamEndCapture(st2, &body);
+            }
+        }
+        if (e == cudaSuccess) {
+            issue_amc(g, m, p.q, st);
+            const int fg = (int)std::min<int64_t>((p.q + 255) / 256, 4096);
+            prof_begin(FAM_FINALIZE, st);
+            finalize_kernel<<<fg, 256, 0, st>>>(w.st, p.q, p.r, p.stats);
+            prof_end(FAM_FINALIZE, st);
+        }
+        cudaGraph_t done = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(st, &done);
+        if (e == cudaSuccess) e = e2;
+    }
+    g_prof_sink = nullptr;
+    g_capturing = false;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&bg.exec, graph, 0);
+    bg.graph = graph;
+    if (e != cudaSuccess) {
+        destroy_graph(bg);
+        cudaGetLastError();
+        return cuda_fail(e, "capturing the batch graph");
+    }
+    bg.valid = true;
+    bg.nq = p.q;
+    bg.fp64 = fp64;
+    bg.o = p.o;
+    bg.lambda = g->lambda;
+    bg.pool = w.ent;
+    bg.state = w.st;
+    bg.prof = g_prof_on;
+    bg.launches = 8 + 3 * p.o.tau + 1;
+    return GER_OK;
+}
+
+static bool graphs_enabled() {
+    const char* v = std::getenv("GEER_NO_GRAPH");
+    return !(v && v[0] && v[0] != '0');
+}
+
+// One batch. Batched plans run as a captured graph (built on first use for
+// each batch shape, replayed after) and must use the workspace buffers for
+// s, t, eps, r and stats; one-query-at-a-time plans run stream-ordered. A
+// frontier-table pool overflow grows the pool and reruns the batch.
 static int run_batch(ger_graph* g, Plan& p) {
     if (p.q == 0) return GER_OK;
     int rc = ensure_lambda(g);
     if (rc) return rc;
     const bool per_query = p.o.per_query != 0;
     const bool fp64 = p.o.precision == GER_FP64;
+    const bool use_graph = !per_query && graphs_enabled();
     int64_t pool = std::max<int64_t>(g->ws.pool_cap, (int64_t)1 << 22);
     for (int attempt = 0; attempt < 6; ++attempt) {
         rc = ensure_ws(g, p.q, pool);
         if (rc) return rc;
         Workspace& w = g->ws;
-        GER_CUDA(cudaMemsetAsync(w.counters, 0, 4 * sizeof(int), p.st));
-        GER_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(SmmCtl), p.st));
-        if (per_query) {
-            for (int64_t i = 0; i < p.q; ++i) {
-                rc = run_queries(g, p, i, 1, fp64);
+        if (use_graph) {
+            if (!same_key(g->bg, p, fp64, g)) {
+                rc = build_graph(g, p, fp64);
                 if (rc) return rc;
             }
+            GER_CUDA(cudaGraphLaunch(g->bg.exec, p.st));
+            note_launches((int)g->bg.launches);
         } else {
-            rc = run_queries(g, p, 0, p.q, fp64);
-            if (rc) return rc;
+            GER_CUDA(cudaMemsetAsync(w.counters, 0, 4 * sizeof(int), p.st));
+            GER_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(SmmCtl), p.st));
+            if (per_query) {
+                for (int64_t i = 0; i < p.q; ++i) {
+                    rc = run_queries(g, p, i, 1, fp64);
+                    if (rc) return rc;
+                }
+            } else {
+                rc = run_queries(g, p, 0, p.q, fp64);
+                if (rc) return rc;
+            }
+            const int fg = (int)std::min<int64_t>((p.q + 255) / 256, 4096);
+            prof_begin(FAM_FINALIZE, p.st);
+            finalize_kernel<<<fg, 256, 0, p.st>>>(w.st, p.q, p.r, p.stats);
+            prof_end(FAM_FINALIZE, p.st);
+            note_launches(1);
         }
-        const int fg = (int)std::min<int64_t>((p.q + 255) / 256, 4096);
-        prof_begin(FAM_FINALIZE, p.st);
-        finalize_kernel<<<fg, 256, 0, p.st>>>(w.st, p.q, p.r, p.stats);
-        prof_end(FAM_FINALIZE, p.st);
-        note_launches(1);
         GER_CUDA(cudaGetLastError());
         GER_CUDA(cudaMemcpyAsync(w.host_rb, w.counters + 1, sizeof(int), cudaMemcpyDeviceToHost, p.st));
         GER_CUDA(cudaMemcpyAsync(w.host_rb + 1, &w.ctl->cursor, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                  p.st));
+        GER_CUDA(cudaMemcpyAsync(w.host_rb + 3, &w.ctl->iter, sizeof(int32_t), cudaMemcpyDeviceToHost, p.st));
         GER_CUDA(cudaStreamSynchronize(p.st));
+        if (use_graph) {
+            prof_collect_graph(g->bg.prof_recs);
+            // the while body ran iter - 1 times, 8 kernels each
+            const int32_t iters = *reinterpret_cast<int32_t*>(w.host_rb + 3);
+            if (iters > 1) note_launches(8 * (iters - 1));
+        }
         prof_collect();
         const int derr = (int)(reinterpret_cast<int*>(w.host_rb)[0]);
         if (derr == DERR_NONE) return GER_OK;
@@ -553,6 +733,7 @@ int ger_load_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int 
     }
     cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&g->stream2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaMalloc(&g->row_ptr, (n + 1) * sizeof(int64_t)) != cudaSuccess ||
         cudaMalloc(&g->col_idx, std::max<int64_t>(g->nnz, 1) * sizeof(int32_t)) != cudaSuccess) {
         cudaGetLastError();
@@ -584,11 +765,13 @@ void ger_free(ger_graph* g) {
     if (!g) return;
     cudaSetDevice(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
+    destroy_graph(g->bg);
     free_ws(g->ws);
     cudaFree(g->row_ptr);
     cudaFree(g->col_idx);
     cudaFree(g->node_info);
     if (g->stream) cudaStreamDestroy(g->stream);
+    if (g->stream2) cudaStreamDestroy(g->stream2);
     delete g;
 }
 
@@ -651,14 +834,20 @@ static int host_batch(ger_graph* g, int64_t q, const int32_t* s, const int32_t* 
     cudaStream_t st = g->stream;
     GER_CUDA(cudaMemcpyAsync(w.s, s, q * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     GER_CUDA(cudaMemcpyAsync(w.t, t, q * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    if (eps_arr) GER_CUDA(cudaMemcpyAsync(w.eps, eps_arr, q * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (eps_arr) {
+        GER_CUDA(cudaMemcpyAsync(w.eps, eps_arr, q * sizeof(double), cudaMemcpyHostToDevice, st));
+    } else {
+        std::vector<double> ev((size_t)q, eps);
+        GER_CUDA(cudaMemcpyAsync(w.eps, ev.data(), q * sizeof(double), cudaMemcpyHostToDevice, st));
+        GER_CUDA(cudaStreamSynchronize(st));
+    }
     p.q = q;
     p.s = w.s;
     p.t = w.t;
-    p.eps = eps_arr ? w.eps : nullptr;
-    p.eps_scalar = eps;
+    p.eps = w.eps;
+    p.eps_scalar = 0.0;
     p.r = w.r;
-    p.stats = stats ? w.stats : nullptr;
+    p.stats = w.stats;
     p.st = st;
     rc = run_batch(g, p);
     if (rc) return rc;
@@ -689,15 +878,28 @@ int ger_query_batch_dev(ger_graph* g, int64_t q, const int32_t* s_dev, const int
     int rc = check_opts(opt, &p.o);
     if (rc) return rc;
     cudaSetDevice(g->device);
+    if (q == 0) return GER_OK;
+    rc = ensure_ws(g, q, std::max<int64_t>(g->ws.pool_cap, (int64_t)1 << 22));
+    if (rc) return rc;
+    Workspace& w = g->ws;
+    cudaStream_t st = stream ? reinterpret_cast<cudaStream_t>(stream) : (cudaStream_t)0;
+    GER_CUDA(cudaMemcpyAsync(w.s, s_dev, q * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    GER_CUDA(cudaMemcpyAsync(w.t, t_dev, q * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    GER_CUDA(cudaMemcpyAsync(w.eps, eps_dev, q * sizeof(double), cudaMemcpyDeviceToDevice, st));
     p.q = q;
-    p.s = s_dev;
-    p.t = t_dev;
-    p.eps = eps_dev;
+    p.s = w.s;
+    p.t = w.t;
+    p.eps = w.eps;
     p.eps_scalar = 0.0;
-    p.r = r_dev;
-    p.stats = stats_dev;
-    p.st = stream ? reinterpret_cast<cudaStream_t>(stream) : (cudaStream_t)0;
-    return run_batch(g, p);
+    p.r = w.r;
+    p.stats = w.stats;
+    p.st = st;
+    rc = run_batch(g, p);
+    if (rc) return rc;
+    GER_CUDA(cudaMemcpyAsync(r_dev, w.r, q * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (stats_dev) GER_CUDA(cudaMemcpyAsync(stats_dev, w.stats, q * sizeof(ger_query_stats), cudaMemcpyDeviceToDevice, st));
+    GER_CUDA(cudaStreamSynchronize(st));
+    return GER_OK;
 }
 
 }  // extern "C"

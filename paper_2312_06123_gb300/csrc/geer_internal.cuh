@@ -74,6 +74,8 @@ struct SmmCtl {
     int64_t lo[2], hi[2];        // slot range per parity
     int32_t n_want;              // queries asking for another iteration
     int32_t n_heavy;             // chunks of high-degree frontier nodes left to the heavy push
+    int32_t iter;                // current SMM iteration (0: the initial frontier)
+    int32_t pad;
 };
 
 // Per-chunk partial sums of the walk kernel.

@@ -51,16 +51,23 @@ struct AmcArgs {
 };
 
 // host launchers (one per kernel)
-// SMM phase, level-synchronous over the batch: set-up, then per iteration
-// alloc -> clear -> (seed | push) -> finish -> top2 -> decide.
+// SMM phase, level-synchronous over the batch. The iteration number lives
+// in the control block (device memory), so the launches of an iteration are
+// the same every time and can sit in a graph's while loop.
+//   start     : setup, alloc, clear, seed, finish, top2, decide (iteration 0)
+//   iteration : alloc, clear, push (+ heavy push), finish, top2, decide
+//   advance   : iteration += 1; optionally sets the graph's while condition
 void launch_smm_setup(const SmmArgs& a, cudaStream_t st);
-void launch_smm_alloc(const SmmArgs& a, int parity, cudaStream_t st);
-void launch_smm_clear(const SmmArgs& a, int parity, int grid, cudaStream_t st);
+void launch_smm_alloc(const SmmArgs& a, cudaStream_t st);
+void launch_smm_clear(const SmmArgs& a, int grid, cudaStream_t st);
 void launch_smm_seed(const SmmArgs& a, cudaStream_t st);
-void launch_smm_push(bool fp64, const SmmArgs& a, int parity_cur, int grid, cudaStream_t st);
-void launch_smm_finish(bool fp64, const SmmArgs& a, int parity, int grid, cudaStream_t st);
-void launch_smm_top2(bool fp64, const SmmArgs& a, int parity, int grid, cudaStream_t st);
-void launch_smm_decide(const SmmArgs& a, int parity, int iter, cudaStream_t st);
+void launch_smm_push(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
+void launch_smm_finish(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
+void launch_smm_top2(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
+void launch_smm_decide(const SmmArgs& a, cudaStream_t st);
+void launch_smm_advance(const SmmArgs& a, cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st);
+void launch_smm_start(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
+void launch_smm_iteration(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 void launch_amc_schedule(const AmcArgs& a, cudaStream_t st);
 void launch_amc_walk(const AmcArgs& a, int grid, cudaStream_t st);
 void launch_amc_reduce(const AmcArgs& a, int grid, cudaStream_t st);

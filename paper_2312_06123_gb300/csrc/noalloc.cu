@@ -166,27 +166,17 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     a.ctl = ctl;
     a.err_flag = counters + 1;
     const int grid = sm_count * 8;
-    launch_smm_setup(a, st);
-    launch_smm_alloc(a, 0, st);
-    launch_smm_clear(a, 0, grid, st);
-    launch_smm_seed(a, st);
-    launch_smm_finish(fp64, a, 0, grid, st);
-    launch_smm_top2(fp64, a, 0, grid, st);
-    launch_smm_decide(a, 0, 0, st);
-    note_launches(7);
+    launch_smm_start(fp64, a, grid, st);
+    launch_smm_advance(a, 0, false, st);
+    note_launches(8);
     for (int iter = 1; iter < 100000; ++iter) {
         int n_want = 0;
         rc = sync_read_int(&ctl->n_want, &n_want, st);
         if (rc) return rc;
         if (n_want == 0) break;
-        const int par = iter & 1;
-        launch_smm_alloc(a, par, st);
-        launch_smm_clear(a, par, grid, st);
-        launch_smm_push(fp64, a, par ^ 1, grid, st);
-        launch_smm_finish(fp64, a, par, grid, st);
-        launch_smm_top2(fp64, a, par, grid, st);
-        launch_smm_decide(a, par, iter, st);
-        note_launches(7);
+        launch_smm_iteration(fp64, a, grid, st);
+        launch_smm_advance(a, 0, false, st);
+        note_launches(8);
     }
     AmcArgs m;
     m.g = dg;

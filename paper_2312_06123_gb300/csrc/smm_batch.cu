@@ -118,6 +118,7 @@ __device__ __forceinline__ uint32_t table_insert(GEntry* tab, uint32_t mask, int
 // ---------------------------------------------------------------------------
 __global__ void smm_setup_kernel(SmmArgs a) {
     const int64_t* row_ptr = a.g.row_ptr;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->iter = 0;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < a.nq; q += (int64_t)gridDim.x * blockDim.x) {
         QState* Q = a.st + q;
         QSmm* M = a.sm + q;
@@ -178,11 +179,12 @@ __global__ void smm_setup_kernel(SmmArgs a) {
 // ---------------------------------------------------------------------------
 // alloc (one CTA): tables for the queries that asked for one, in query order
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kCta) smm_alloc_kernel(SmmArgs a, int parity) {
+__global__ void __launch_bounds__(kCta) smm_alloc_kernel(SmmArgs a) {
     __shared__ int64_t scan[kWarps + 1];
     __shared__ int64_t carry, seg_carry;
     const int tid = threadIdx.x;
     SmmCtl* C = a.ctl;
+    const int parity = C->iter & 1;
     const unsigned long long base = C->cursor;
     if (tid == 0) {
         carry = 0;
@@ -238,7 +240,8 @@ __global__ void __launch_bounds__(kCta) smm_alloc_kernel(SmmArgs a, int parity) 
 }
 
 // clear the tables allocated for `parity`
-__global__ void smm_clear_kernel(SmmArgs a, int parity) {
+__global__ void smm_clear_kernel(SmmArgs a) {
+    const int parity = a.ctl->iter & 1;
     const int64_t lo = a.ctl->lo[parity], hi = a.ctl->hi[parity];
     for (int64_t j = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < hi;
          j += (int64_t)gridDim.x * blockDim.x) {
@@ -305,7 +308,8 @@ __device__ __forceinline__ void push_range(const SmmArgs& a, int64_t j, int q, i
 // to its neighbours in the query's next table. One warp per table slot; a
 // node with more than kLightMax neighbours goes to the heavy list instead.
 template <typename T>
-__global__ void __launch_bounds__(256) smm_push_kernel(SmmArgs a, int parity_cur) {
+__global__ void __launch_bounds__(256) smm_push_kernel(SmmArgs a) {
+    const int parity_cur = (a.ctl->iter & 1) ^ 1;
     const int lane = threadIdx.x & 31;
     const int64_t lo = a.ctl->lo[parity_cur], hi = a.ctl->hi[parity_cur];
     const int64_t* row_ptr = a.g.row_ptr;
@@ -351,7 +355,8 @@ __global__ void __launch_bounds__(256) smm_push_heavy_kernel(SmmArgs a) {
 // finish: y(v) = sum / d(v) in T, g(v), and the per-query sums (vol of
 // Eq. 17, the next push volume, |V|, max_1), aggregated per warp
 template <typename T>
-__global__ void __launch_bounds__(256) smm_finish_kernel(SmmArgs a, int parity) {
+__global__ void __launch_bounds__(256) smm_finish_kernel(SmmArgs a) {
+    const int parity = a.ctl->iter & 1;
     const int64_t lo = a.ctl->lo[parity], hi = a.ctl->hi[parity];
     T* ys = reinterpret_cast<T*>(a.ys);
     T* yt = reinterpret_cast<T*>(a.yt);
@@ -426,7 +431,8 @@ __global__ void __launch_bounds__(256) smm_finish_kernel(SmmArgs a, int parity) 
 // top2: max_2 of each vector = the largest value below max_1, or max_1 itself
 // when it occurs twice (the multiset's second element); aggregated per warp
 template <typename T>
-__global__ void __launch_bounds__(256) smm_top2_kernel(SmmArgs a, int parity) {
+__global__ void __launch_bounds__(256) smm_top2_kernel(SmmArgs a) {
+    const int parity = a.ctl->iter & 1;
     const int64_t lo = a.ctl->lo[parity], hi = a.ctl->hi[parity];
     const T* ys = reinterpret_cast<const T*>(a.ys);
     const T* yt = reinterpret_cast<const T*>(a.yt);
@@ -488,7 +494,9 @@ __device__ void switch_quantities(int64_t lf, double s1, double s2, double t1, d
 }
 
 // decide: one thread per query whose table was just finished
-__global__ void smm_decide_kernel(SmmArgs a, int parity, int iter) {
+__global__ void smm_decide_kernel(SmmArgs a) {
+    const int iter = a.ctl->iter;
+    const int parity = iter & 1;
     const int nseg = a.ctl->nseg[parity];
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nseg; k += gridDim.x * blockDim.x) {
         const int q = a.seg_q[parity][k];
@@ -558,6 +566,14 @@ __global__ void smm_decide_kernel(SmmArgs a, int parity, int iter) {
     }
 }
 
+// advance: next iteration; in a captured graph, also the while condition
+// (another iteration while some query asked for one)
+__global__ void smm_advance_kernel(SmmArgs a, cudaGraphConditionalHandle h, int use_handle) {
+    SmmCtl* C = a.ctl;
+    C->iter += 1;
+    if (use_handle) cudaGraphSetConditional(h, C->n_want > 0 ? 1u : 0u);
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -568,15 +584,15 @@ void launch_smm_setup(const SmmArgs& a, cudaStream_t st) {
     prof_end(FAM_SMM_SETUP, st);
 }
 
-void launch_smm_alloc(const SmmArgs& a, int parity, cudaStream_t st) {
+void launch_smm_alloc(const SmmArgs& a, cudaStream_t st) {
     prof_begin(FAM_SMM_ALLOC, st);
-    smm_alloc_kernel<<<1, kCta, 0, st>>>(a, parity);
+    smm_alloc_kernel<<<1, kCta, 0, st>>>(a);
     prof_end(FAM_SMM_ALLOC, st);
 }
 
-void launch_smm_clear(const SmmArgs& a, int parity, int grid, cudaStream_t st) {
+void launch_smm_clear(const SmmArgs& a, int grid, cudaStream_t st) {
     prof_begin(FAM_SMM_CLEAR, st);
-    smm_clear_kernel<<<grid, 256, 0, st>>>(a, parity);
+    smm_clear_kernel<<<grid, 256, 0, st>>>(a);
     prof_end(FAM_SMM_CLEAR, st);
 }
 
@@ -587,10 +603,10 @@ void launch_smm_seed(const SmmArgs& a, cudaStream_t st) {
     prof_end(FAM_SMM_PUSH, st);
 }
 
-void launch_smm_push(bool fp64, const SmmArgs& a, int parity_cur, int grid, cudaStream_t st) {
+void launch_smm_push(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
     prof_begin(FAM_SMM_PUSH, st);
-    if (fp64) smm_push_kernel<double><<<grid, 256, 0, st>>>(a, parity_cur);
-    else smm_push_kernel<float><<<grid, 256, 0, st>>>(a, parity_cur);
+    if (fp64) smm_push_kernel<double><<<grid, 256, 0, st>>>(a);
+    else smm_push_kernel<float><<<grid, 256, 0, st>>>(a);
     prof_end(FAM_SMM_PUSH, st);
     prof_begin(FAM_SMM_PUSH_HEAVY, st);
     if (fp64) smm_push_heavy_kernel<double><<<grid, 256, 0, st>>>(a);
@@ -598,25 +614,48 @@ void launch_smm_push(bool fp64, const SmmArgs& a, int parity_cur, int grid, cuda
     prof_end(FAM_SMM_PUSH_HEAVY, st);
 }
 
-void launch_smm_finish(bool fp64, const SmmArgs& a, int parity, int grid, cudaStream_t st) {
+void launch_smm_finish(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
     prof_begin(FAM_SMM_FINISH, st);
-    if (fp64) smm_finish_kernel<double><<<grid, 256, 0, st>>>(a, parity);
-    else smm_finish_kernel<float><<<grid, 256, 0, st>>>(a, parity);
+    if (fp64) smm_finish_kernel<double><<<grid, 256, 0, st>>>(a);
+    else smm_finish_kernel<float><<<grid, 256, 0, st>>>(a);
     prof_end(FAM_SMM_FINISH, st);
 }
 
-void launch_smm_top2(bool fp64, const SmmArgs& a, int parity, int grid, cudaStream_t st) {
+void launch_smm_top2(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
     prof_begin(FAM_SMM_TOP2, st);
-    if (fp64) smm_top2_kernel<double><<<grid, 256, 0, st>>>(a, parity);
-    else smm_top2_kernel<float><<<grid, 256, 0, st>>>(a, parity);
+    if (fp64) smm_top2_kernel<double><<<grid, 256, 0, st>>>(a);
+    else smm_top2_kernel<float><<<grid, 256, 0, st>>>(a);
     prof_end(FAM_SMM_TOP2, st);
 }
 
-void launch_smm_decide(const SmmArgs& a, int parity, int iter, cudaStream_t st) {
+void launch_smm_decide(const SmmArgs& a, cudaStream_t st) {
     const int grid = (int)std::min<int64_t>((a.nq + 255) / 256, 1024);
     prof_begin(FAM_SMM_DECIDE, st);
-    smm_decide_kernel<<<grid, 256, 0, st>>>(a, parity, iter);
+    smm_decide_kernel<<<grid, 256, 0, st>>>(a);
     prof_end(FAM_SMM_DECIDE, st);
+}
+
+void launch_smm_advance(const SmmArgs& a, cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st) {
+    smm_advance_kernel<<<1, 1, 0, st>>>(a, h, use_handle ? 1 : 0);
+}
+
+void launch_smm_iteration(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
+    launch_smm_alloc(a, st);
+    launch_smm_clear(a, grid, st);
+    launch_smm_push(fp64, a, grid, st);
+    launch_smm_finish(fp64, a, grid, st);
+    launch_smm_top2(fp64, a, grid, st);
+    launch_smm_decide(a, st);
+}
+
+void launch_smm_start(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
+    launch_smm_setup(a, st);
+    launch_smm_alloc(a, st);
+    launch_smm_clear(a, grid, st);
+    launch_smm_seed(a, st);
+    launch_smm_finish(fp64, a, grid, st);
+    launch_smm_top2(fp64, a, grid, st);
+    launch_smm_decide(a, st);
 }
 
 }  // namespace geer
