@@ -30,8 +30,11 @@ namespace {
 
 }  // namespace
 
-// One CTA: chunk layout of batch b for every query still in AMC.
-__global__ void __launch_bounds__(kCta) amc_schedule_kernel(AmcArgs a) {
+// Chunk layout of the next batch for every query still in AMC, by one CTA:
+// per query ppc (walk pairs per chunk) and its chunk count, and their prefix
+// in chunk_begin. Reads the query
+// state through the L2 (it was written by other CTAs of the same kernel).
+__device__ void schedule_cta(const AmcArgs& a) {
     __shared__ int64_t scan[kWarps + 1];
     __shared__ int64_t carry;
     const int tid = threadIdx.x;
@@ -42,8 +45,8 @@ __global__ void __launch_bounds__(kCta) amc_schedule_kernel(AmcArgs a) {
         int64_t nch = 0;
         if (q < a.nq) {
             QState* Q = a.st + q;
-            if (Q->status == ST_AMC) {
-                const int64_t eta = Q->eta;
+            if (__ldcg(&Q->status) == ST_AMC) {
+                const int64_t eta = __ldcg(&Q->eta);
                 // a warp round walks kWalksPerLane * kPairsPerWarpRound pairs
                 const int64_t unit = kWalksPerLane * kPairsPerWarpRound;
                 const int64_t units = (eta + unit - 1) / unit;
@@ -63,6 +66,8 @@ __global__ void __launch_bounds__(kCta) amc_schedule_kernel(AmcArgs a) {
     }
     if (tid == 0) a.chunk_begin[a.nq] = carry;
 }
+
+__global__ void __launch_bounds__(kCta) amc_schedule_kernel(AmcArgs a) { schedule_cta(a); }
 
 // Row start and degree of node w.
 __device__ __forceinline__ uint2 node_row(const DevGraph& g, int32_t w) {
@@ -91,8 +96,19 @@ __device__ __forceinline__ double resolve_g(const GEntry* tab, int32_t mask, int
 // k0 + i + 16 w (w < W), from s and from t. The W walks of a lane advance in
 // lockstep so that their loads overlap; each step issues the next node's
 // row record and its first lookup probe together.
+constexpr int kSmemChunkBegin = 2048;  // chunk_begin entries staged in shared memory
+#ifndef GEER_WALK_MINB
+#define GEER_WALK_MINB 5
+#endif
+
 template <int W>
-__global__ void __launch_bounds__(256) amc_walk_kernel(AmcArgs a) {
+__global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a) {
+    __shared__ int64_t cbeg[kSmemChunkBegin];
+    const bool staged = a.nq + 1 <= kSmemChunkBegin;
+    if (staged)
+        for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) cbeg[i] = a.chunk_begin[i];
+    __syncthreads();
+    const int64_t* cb_arr = staged ? cbeg : a.chunk_begin;
     const int lane = threadIdx.x & 31;
     const int sigma = lane & 1;
     const int64_t total = a.chunk_begin[a.nq];
@@ -102,13 +118,13 @@ __global__ void __launch_bounds__(256) amc_walk_kernel(AmcArgs a) {
     const uint32_t lane_ctr = (uint32_t)(2 * (a.batch - 1) + sigma);
     for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total; c += nw) {
         // owning query: last q with chunk_begin[q] <= c
-        int64_t lo = 0, hi = a.nq + 1;
+        int lo = 0, hi = a.nq + 1;
         while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (a.chunk_begin[mid] <= c) lo = mid + 1; else hi = mid;
+            const int mid = (lo + hi) >> 1;
+            if (cb_arr[mid] <= c) lo = mid + 1; else hi = mid;
         }
         const QState* Q = a.st + (lo - 1);
-        const int64_t cb = a.chunk_begin[lo - 1];
+        const int64_t cb = cb_arr[lo - 1];
         const int64_t eta = Q->eta, ppc = Q->ppc;
         const int32_t lf = Q->lf, qidx = Q->qidx;
         const int32_t start = sigma ? Q->t : Q->s;
@@ -189,63 +205,60 @@ __global__ void __launch_bounds__(256) amc_walk_kernel(AmcArgs a) {
     }
 }
 
-// One CTA per query: batch statistics (Algorithm 1: Z, the empirical
+// One warp per query: batch statistics (Algorithm 1: Z, the empirical
 // variance, f of Eq. (7) at delta/tau) and the stop / doubling decision.
+// The last CTA to finish lays out the next batch (schedule_cta).
 __global__ void __launch_bounds__(kCta) amc_reduce_kernel(AmcArgs a) {
-    __shared__ double red0[kWarps], red1[kWarps];
-    __shared__ uint64_t red2[kWarps];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int64_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t q = (int64_t)blockIdx.x * kWarps + warp;
+    if (q < a.nq) {
         QState* Q = a.st + q;
-        if (Q->status != ST_AMC) continue;  // uniform across the CTA
-        const int64_t nch = Q->nchunks, begin = a.chunk_begin[q];
-        double sz = 0.0, sz2 = 0.0;
-        uint64_t cs = 0;
-        for (int64_t i = tid; i < nch; i += kCta) {
-            const Partial p = a.partial[begin + i];
-            sz += p.sz;
-            sz2 += p.sz2;
-            cs += p.cs;
-        }
-        sz = warp_sum(sz);
-        sz2 = warp_sum(sz2);
-        cs = warp_sum(cs);
-        if (lane == 0) {
-            red0[warp] = sz;
-            red1[warp] = sz2;
-            red2[warp] = cs;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double S = 0.0, S2 = 0.0;
-            uint64_t C = 0;
-            for (int w = 0; w < kWarps; ++w) {
-                S += red0[w];
-                S2 += red1[w];
-                C += red2[w];
+        if (Q->status == ST_AMC) {  // uniform across the warp
+            const int64_t nch = Q->nchunks, begin = a.chunk_begin[q];
+            double sz = 0.0, sz2 = 0.0;
+            uint64_t cs = 0;
+            for (int64_t i = lane; i < nch; i += 32) {
+                const Partial p = a.partial[begin + i];
+                sz += p.sz;
+                sz2 += p.sz2;
+                cs += p.cs;
             }
-            const int64_t eta = Q->eta;
-            const double Z = S / (double)eta;
-            double var = S2 / (double)eta - Z * Z;
-            if (var < 0.0) var = 0.0;
-            const double delta_b = a.delta / (double)a.tau;
-            const double L = log(3.0 / delta_b);
-            const double f = sqrt(2.0 * var * L / (double)eta) + 3.0 * Q->psi * L / (double)eta;
-            Q->walks += eta;
-            Q->walk_steps += 2 * eta * (int64_t)Q->lf;
-            Q->checksum += C;
-            Q->batch = a.batch;
-            Q->f_last = f;
-            if (f <= Q->eps / 2.0 || a.batch >= a.tau) {
-                Q->r_f = Z;
-                Q->r = Q->r_b + Z;
-                Q->status = ST_DONE;
-            } else {
-                Q->eta = 2 * eta;
+            sz = warp_sum(sz);
+            sz2 = warp_sum(sz2);
+            cs = warp_sum(cs);
+            if (lane == 0) {
+                const int64_t eta = Q->eta;
+                const double Z = sz / (double)eta;
+                double var = sz2 / (double)eta - Z * Z;
+                if (var < 0.0) var = 0.0;
+                const double delta_b = a.delta / (double)a.tau;
+                const double L = log(3.0 / delta_b);
+                const double f = sqrt(2.0 * var * L / (double)eta) + 3.0 * Q->psi * L / (double)eta;
+                Q->walks += eta;
+                Q->walk_steps += 2 * eta * (int64_t)Q->lf;
+                Q->checksum += cs;
+                Q->batch = a.batch;
+                Q->f_last = f;
+                if (f <= Q->eps / 2.0 || a.batch >= a.tau) {
+                    Q->r_f = Z;
+                    Q->r = Q->r_b + Z;
+                    Q->status = ST_DONE;
+                } else {
+                    Q->eta = 2 * eta;
+                }
             }
         }
-        __syncthreads();
     }
+    if (a.batch >= a.tau) return;  // no next batch to lay out
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(a.done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    schedule_cta(a);
+    if (threadIdx.x == 0) *a.done = 0u;
 }
 
 void launch_amc_schedule(const AmcArgs& a, cudaStream_t st) {
@@ -260,7 +273,8 @@ void launch_amc_walk(const AmcArgs& a, int grid, cudaStream_t st) {
     prof_end(FAM_AMC_WALK, st);
 }
 
-void launch_amc_reduce(const AmcArgs& a, int grid, cudaStream_t st) {
+void launch_amc_reduce(const AmcArgs& a, cudaStream_t st) {
+    const int grid = (int)((a.nq + kWarps - 1) / kWarps);
     prof_begin(FAM_AMC_REDUCE, st);
     amc_reduce_kernel<<<grid, kCta, 0, st>>>(a);
     prof_end(FAM_AMC_REDUCE, st);

@@ -418,6 +418,7 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
     m.nq = (int32_t)nq;
     m.st = w.st + q0;
     m.chunk_begin = w.chunk_begin;
+    m.done = reinterpret_cast<unsigned int*>(w.counters + 2);
     m.partial = w.partial;
     m.partial_cap = w.partial_cap;
     m.pool = w.ent;
@@ -429,15 +430,15 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
 
 // The tau AMC rounds (schedule -> walks -> batch statistics).
 static void issue_amc(ger_graph* g, AmcArgs m, int64_t nq, cudaStream_t st) {
-    const int red_grid = (int)std::min<int64_t>(nq, 4096);
     const int walk_grid = nq == 1 ? g->sm_count * 2 : g->sm_count * 8;
+    m.batch = 1;
+    launch_amc_schedule(m, st);
     for (int b = 1; b <= m.tau; ++b) {
         m.batch = b;
-        launch_amc_schedule(m, st);
         launch_amc_walk(m, walk_grid, st);
-        launch_amc_reduce(m, red_grid, st);
+        launch_amc_reduce(m, st);  // its last CTA lays out batch b + 1
     }
-    note_launches(3 * m.tau);
+    note_launches(1 + 2 * m.tau);
 }
 
 // The GEER launch sequence for queries [q0, q0 + nq), stream-ordered, with
@@ -566,7 +567,7 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
     bg.pool = w.ent;
     bg.state = w.st;
     bg.prof = g_prof_on;
-    bg.launches = 8 + 3 * p.o.tau + 1;
+    bg.launches = 8 + 1 + 2 * p.o.tau + 1;
     return GER_OK;
 }
 

@@ -40,6 +40,7 @@ struct AmcArgs {
     int32_t nq;
     QState* st;
     int64_t* chunk_begin;  // nq + 1
+    unsigned int* done;    // CTA counter of the fused reduce (last CTA schedules)
     Partial* partial;
     int64_t partial_cap;
     const GEntry* pool;
@@ -70,7 +71,8 @@ void launch_smm_start(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 void launch_smm_iteration(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 void launch_amc_schedule(const AmcArgs& a, cudaStream_t st);
 void launch_amc_walk(const AmcArgs& a, int grid, cudaStream_t st);
-void launch_amc_reduce(const AmcArgs& a, int grid, cudaStream_t st);
+// batch statistics of batch a.batch; the last CTA schedules batch a.batch + 1
+void launch_amc_reduce(const AmcArgs& a, cudaStream_t st);
 
 }  // namespace geer
 

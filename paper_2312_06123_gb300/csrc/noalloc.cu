@@ -183,6 +183,7 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     m.nq = (int32_t)q;
     m.st = qs;
     m.chunk_begin = reinterpret_cast<int64_t*>(base + kOffChunk);
+    m.done = reinterpret_cast<unsigned int*>(counters + 2);
     m.partial = reinterpret_cast<Partial*>(base + kOffPartial);
     m.partial_cap = kNoAllocMaxQueries * kMaxChunksPerQuery;
     m.pool = a.ent;
@@ -190,14 +191,15 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     m.tau = o.tau;
     m.delta = o.delta;
     m.err_flag = counters + 1;
+    m.batch = 1;
+    launch_amc_schedule(m, st);
     for (int b = 1; b <= o.tau; ++b) {
         m.batch = b;
-        launch_amc_schedule(m, st);
         launch_amc_walk(m, sm_count * 8, st);
-        launch_amc_reduce(m, (int)q, st);
+        launch_amc_reduce(m, st);  // its last CTA lays out batch b + 1
     }
     launch_finalize(qs, q, r_dev, stats_dev, st);
-    note_launches(1 + 3 * o.tau);
+    note_launches(2 + 2 * o.tau);
     int derr = 0;
     rc = sync_read_int(counters + 1, &derr, st);
     if (rc) return rc;

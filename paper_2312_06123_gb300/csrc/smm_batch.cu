@@ -275,8 +275,8 @@ __global__ void smm_seed_kernel(SmmArgs a) {
     }
 }
 
-constexpr int64_t kLightMax = 1024;  // neighbours a single warp pushes
-constexpr int64_t kHeavyChunk = 1024;
+constexpr int64_t kLightMax = 128;  // neighbours a single warp pushes
+constexpr int64_t kHeavyChunk = 512;
 
 // push the values of table slot j (node u of query q) to neighbours
 // [pb, pe) of u; called by `nthreads` cooperating threads with rank `rank`
@@ -335,8 +335,8 @@ __global__ void __launch_bounds__(256) smm_push_kernel(SmmArgs a) {
     }
 }
 
-// heavy push: one CTA per chunk of kHeavyChunk neighbours of a
-// high-degree node
+// heavy push: one CTA per chunk of kHeavyChunk neighbours of a node with
+// more than kLightMax neighbours
 template <typename T>
 __global__ void __launch_bounds__(256) smm_push_heavy_kernel(SmmArgs a) {
     const int64_t nc = min((int64_t)a.ctl->n_heavy, a.heavy_cap);
