@@ -52,6 +52,10 @@ extern "C" {
 #define GER_SWITCH_RULE  0  /* Eq. (17): stop SMM once the support volume exceeds h(l - l_b) */
 #define GER_SWITCH_FIXED 2  /* run exactly min(fixed_ell_b, l) SMM iterations; fixed_ell_b < 0 means l */
 
+/* engine of the SMM iterations */
+#define GER_ENGINE_SPARSE 0 /* per-query frontier tables, push (fits the small frontiers of Eq. (17)'s switch) */
+#define GER_ENGINE_DENSE  1 /* blocks of query vectors, pull SpMM over all rows (deep SMM) */
+
 /* truncation length formula */
 #define GER_ELL_REFINED 0   /* Eq. (6), Theorem 1 */
 #define GER_ELL_PENG    1   /* Eq. (5), Peng et al. */
@@ -68,6 +72,8 @@ typedef struct ger_options {
     int32_t  ell_formula;   /* GER_ELL_REFINED (default) or GER_ELL_PENG */
     uint64_t seed;          /* walk RNG seed */
     int64_t  sparse_cap;    /* max SMM push pairs of one query iteration (0: no limit beyond the pool) */
+    int32_t  smm_engine;    /* GER_ENGINE_SPARSE (default) or GER_ENGINE_DENSE */
+    int32_t  dense_width;   /* dense engine: columns per block (2 per query); 0: autotuned per graph */
 } ger_options;
 
 /* Per-query statistics (all optional outputs). */

@@ -24,6 +24,7 @@ GER_ERR = {
 GER_FP64, GER_FP32 = 0, 1
 GER_SWITCH_RULE, GER_SWITCH_FIXED = 0, 2
 GER_ELL_REFINED, GER_ELL_PENG = 0, 1
+GER_ENGINE_SPARSE, GER_ENGINE_DENSE = 0, 1
 
 
 class GeerError(RuntimeError):
@@ -36,7 +37,8 @@ class Options(ctypes.Structure):
     _fields_ = [("delta", ctypes.c_double), ("tau", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("per_query", ctypes.c_int32), ("switch_policy", ctypes.c_int32),
                 ("fixed_ell_b", ctypes.c_int32), ("ell_formula", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("sparse_cap", ctypes.c_int64)]
+                ("seed", ctypes.c_uint64), ("sparse_cap", ctypes.c_int64), ("smm_engine", ctypes.c_int32),
+                ("dense_width", ctypes.c_int32)]
 
 
 class QueryStats(ctypes.Structure):

@@ -130,6 +130,10 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
         const int32_t start = sigma ? Q->t : Q->s;
         const GEntry* tab = a.pool + Q->table_off;
         const int32_t mask = Q->table_mask;
+        // dense-engine queries: (s*, t*) read directly from their block column
+        const char* dvals = reinterpret_cast<const char*>(Q->dense_vals);
+        const int64_t dstride = Q->dense_stride;
+        const double inv_ds = 1.0 / (double)Q->ds, inv_dt = 1.0 / (double)Q->dt;
         const uint2 start_info = node_row(g, start);
         const int64_t k_lo = (c - cb) * ppc;
         const int64_t k_hi = min(k_lo + ppc, eta);
@@ -165,17 +169,38 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
                         const uint32_t d = sub == 0 ? r[i].x : (sub == 1 ? r[i].y : (sub == 2 ? r[i].z : r[i].w));
                         nx[i] = act[i] ? __ldg(row_base(g, w[i], inf[i]) + __umulhi(d, inf[i].y)) : start;
                     }
-                    // next row records and first probes, all independent
+                    // next row records and first probes (or dense values), all independent
+                    if (mask >= 0) {
 #pragma unroll
-                    for (int i = 0; i < W; ++i) {
-                        hh[i] = hash32((uint32_t)nx[i]) & (uint32_t)mask;
-                        pr[i] = __ldg(reinterpret_cast<const int4*>(tab + hh[i]));
-                        if (act[i]) inf[i] = node_row(g, nx[i]);
-                    }
+                        for (int i = 0; i < W; ++i) {
+                            hh[i] = hash32((uint32_t)nx[i]) & (uint32_t)mask;
+                            pr[i] = __ldg(reinterpret_cast<const int4*>(tab + hh[i]));
+                            if (act[i]) inf[i] = node_row(g, nx[i]);
+                        }
 #pragma unroll
-                    for (int i = 0; i < W; ++i) {
-                        if (act[i]) z[i] += resolve_g(tab, mask, nx[i], pr[i], hh[i]);
-                        w[i] = nx[i];
+                        for (int i = 0; i < W; ++i) {
+                            if (act[i]) z[i] += resolve_g(tab, mask, nx[i], pr[i], hh[i]);
+                            w[i] = nx[i];
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < W; ++i) {
+                            double xs, xt;
+                            if (a.dense_fp64) {
+                                const double2 p2 = __ldg(reinterpret_cast<const double2*>(dvals + (size_t)nx[i] * dstride * 8));
+                                xs = p2.x;
+                                xt = p2.y;
+                            } else {
+                                const float2 p2 = __ldg(reinterpret_cast<const float2*>(dvals + (size_t)nx[i] * dstride * 4));
+                                xs = (double)p2.x;
+                                xt = (double)p2.y;
+                            }
+                            if (act[i]) {
+                                inf[i] = node_row(g, nx[i]);
+                                z[i] += xs * inv_ds - xt * inv_dt;
+                            }
+                            w[i] = nx[i];
+                        }
                     }
                 }
 #pragma unroll

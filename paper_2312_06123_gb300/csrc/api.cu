@@ -28,9 +28,10 @@ void note_launches(int k) {
 // ---------------------------------------------------------------------------
 // profiler: CUDA events around launches, on the launch stream
 // ---------------------------------------------------------------------------
-static const char* kFamilyNames[FAM_COUNT] = {"smm_setup", "smm_alloc", "smm_clear", "smm_push",
-                                              "smm_push_heavy", "smm_finish", "smm_top2", "smm_decide", "amc_schedule",
-                                              "amc_walk", "amc_reduce", "finalize", "lanczos"};
+static const char* kFamilyNames[] = {"smm_setup", "smm_alloc", "smm_clear", "smm_push",
+                                              "smm_push_heavy", "smm_finish", "smm_top2", "smm_decide", "dense_spmm",
+                                              "amc_schedule", "amc_walk", "amc_reduce", "finalize", "lanczos"};
+static_assert(sizeof(kFamilyNames) / sizeof(kFamilyNames[0]) == FAM_COUNT, "one name per kernel family");
 struct ProfRec {
     int fam;
     cudaEvent_t a, b;
@@ -148,7 +149,15 @@ struct Workspace {
     unsigned long long* sums = nullptr;  // 2 pool_cap
     double* yvals = nullptr;             // 2 pool_cap values (T = float or double)
     int64_t pool_cap = 0;
-    // counters: [1] error flag (int)
+    // dense engine
+    void* dX[2] = {nullptr, nullptr};
+    uint32_t* dS[2] = {nullptr, nullptr};
+    int32_t* dblock_q = nullptr;
+    int32_t* dblock_run = nullptr;
+    DensePartial* dpart = nullptr;
+    size_t dX_bytes = 0, dS_bytes = 0, dpart_n = 0;
+    int64_t dblock_q_n = 0;
+    // counters: [1] error flag (int), [2] AMC done counter
     int* counters = nullptr;
     // pinned readback
     int64_t* host_rb = nullptr;
@@ -166,6 +175,8 @@ struct BatchGraph {
     double lambda = 0;
     const void* pool = nullptr;
     const void* state = nullptr;
+    const void* dense = nullptr;
+    int dense_w = 0;
     bool prof = false;
     int64_t launches = 0;  // kernels outside the while body
     cudaGraph_t graph = nullptr;
@@ -185,6 +196,7 @@ struct ger_graph {
     double lambda = 0, lam2 = 0, lamn = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t stream2 = nullptr;  // captures the SMM while body
+    int dense_tuned[2] = {0, 0};     // autotuned dense block width (FP32, FP64), 0: not tuned
     geer::Workspace ws;
     geer::BatchGraph bg;
 };
@@ -196,6 +208,8 @@ static void free_ws(Workspace& w) {
     cudaFree(w.chunk_begin); cudaFree(w.partial); cudaFree(w.qsmm); cudaFree(w.seg_q); cudaFree(w.seg_off);
     cudaFree(w.ctl); cudaFree(w.ent); cudaFree(w.sums); cudaFree(w.yvals); cudaFree(w.counters);
     cudaFree(w.heavy);
+    cudaFree(w.dX[0]); cudaFree(w.dX[1]); cudaFree(w.dS[0]); cudaFree(w.dS[1]);
+    cudaFree(w.dblock_q); cudaFree(w.dblock_run); cudaFree(w.dpart);
     if (w.host_rb) cudaFreeHost(w.host_rb);
     w = Workspace();
 }
@@ -372,6 +386,102 @@ static int map_device_error(int e) {
     }
 }
 
+// Dense-engine block width: the option, else the autotuned choice of the
+// graph, else the widest block.
+static int dense_width_for(ger_graph* g, const ger_options& o) {
+    const bool fp64 = o.precision == GER_FP64;
+    if (o.dense_width) return o.dense_width;
+    const int tuned = fp64 ? g->dense_tuned[1] : g->dense_tuned[0];
+    return tuned ? tuned : (fp64 ? 64 : 128);
+}
+
+// Make room for the dense engine's blocks (nq queries at `width` columns).
+static int ensure_dense(ger_graph* g, int64_t nq, int width, bool fp64) {
+    Workspace& w = g->ws;
+    const int64_t qpb = width / 2;
+    const int64_t nblocks = (nq + qpb - 1) / qpb;
+    const size_t xb = (size_t)nblocks * (size_t)g->n * (size_t)width * (fp64 ? 8 : 4);
+    const size_t words = (size_t)std::max(width / 32, 1);
+    const size_t sb = (size_t)nblocks * (size_t)g->n * words * 4;
+    const int part_warps = g->sm_count * 2 * 8;
+    const size_t pn = (size_t)nblocks * (size_t)part_warps * (size_t)qpb;
+    if (xb > w.dX_bytes) {
+        cudaFree(w.dX[0]); cudaFree(w.dX[1]);
+        w.dX[0] = w.dX[1] = nullptr;
+        w.dX_bytes = 0;
+        if (cudaMalloc(&w.dX[0], xb) != cudaSuccess || cudaMalloc(&w.dX[1], xb) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(GER_ERR_OOM, "dense blocks (%zu bytes each)", xb);
+        }
+        w.dX_bytes = xb;
+    }
+    if (sb > w.dS_bytes) {
+        cudaFree(w.dS[0]); cudaFree(w.dS[1]);
+        w.dS[0] = w.dS[1] = nullptr;
+        w.dS_bytes = 0;
+        if (cudaMalloc(&w.dS[0], sb) != cudaSuccess || cudaMalloc(&w.dS[1], sb) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(GER_ERR_OOM, "dense support bits");
+        }
+        w.dS_bytes = sb;
+    }
+    if (pn > w.dpart_n) {
+        cudaFree(w.dpart);
+        w.dpart = nullptr;
+        w.dpart_n = 0;
+        if (alloc(&w.dpart, pn)) {
+            cudaGetLastError();
+            return fail(GER_ERR_OOM, "dense partials");
+        }
+        w.dpart_n = pn;
+    }
+    const int64_t nbq = nblocks * qpb;
+    if (nbq > w.dblock_q_n) {
+        cudaFree(w.dblock_q); cudaFree(w.dblock_run);
+        w.dblock_q = nullptr; w.dblock_run = nullptr; w.dblock_q_n = 0;
+        if (alloc(&w.dblock_q, nbq) || alloc(&w.dblock_run, nblocks)) {
+            cudaGetLastError();
+            return fail(GER_ERR_OOM, "dense block map");
+        }
+        w.dblock_q_n = nbq;
+    }
+    return GER_OK;
+}
+
+static DenseArgs make_dense_args(ger_graph* g, int64_t q0, int64_t nq, int width) {
+    Workspace& w = g->ws;
+    DenseArgs d;
+    d.g = DevGraph{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info};
+    d.width = width;
+    d.nblocks = (int32_t)((nq + width / 2 - 1) / (width / 2));
+    d.X[0] = w.dX[0];
+    d.X[1] = w.dX[1];
+    d.S[0] = w.dS[0];
+    d.S[1] = w.dS[1];
+    d.block_q = w.dblock_q;
+    d.block_run = w.dblock_run;
+    d.st = w.st + q0;
+    d.sm = w.qsmm + q0;
+    d.part = w.dpart;
+    d.part_warps = g->sm_count * 2 * 8;
+    d.ctl = w.ctl;
+    return d;
+}
+
+// Start of the dense engine for nq queries: empty blocks, the column map,
+// iteration 0 (stream-ordered; capturable).
+static void issue_dense_start(ger_graph* g, const DenseArgs& d, bool fp64, int64_t nq, cudaStream_t st) {
+    Workspace& w = g->ws;
+    const size_t xb = (size_t)d.nblocks * (size_t)g->n * (size_t)d.width * (fp64 ? 8 : 4);
+    const size_t sb = (size_t)d.nblocks * (size_t)g->n * (size_t)std::max(d.width / 32, 1) * 4;
+    cudaMemsetAsync(w.dX[0], 0, xb, st);
+    cudaMemsetAsync(w.dX[1], 0, xb, st);
+    cudaMemsetAsync(w.dS[0], 0, sb, st);
+    cudaMemsetAsync(w.dS[1], 0, sb, st);
+    launch_dense_map(d, nq, st);
+    launch_dense_init(fp64, d, st);
+}
+
 // Launch arguments of the SMM and AMC phases for queries [q0, q0 + nq).
 static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool fp64, SmmArgs* pa, AmcArgs* pm) {
     Workspace& w = g->ws;
@@ -411,6 +521,11 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
     a.seg_off[1] = w.seg_off + (w.q_cap + 1);
     a.heavy = w.heavy;
     a.heavy_cap = kHeavyCap;
+    a.dense_engine = p.o.smm_engine == GER_ENGINE_DENSE;
+    a.dense_width = a.dense_engine ? dense_width_for(g, p.o) : 2;
+    a.dense_fp64 = fp64;
+    a.dense_X[0] = w.dX[0];
+    a.dense_X[1] = w.dX[1];
     a.ctl = w.ctl;
     a.err_flag = w.counters + 1;
     AmcArgs& m = *pm;
@@ -425,6 +540,7 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
     m.seed = p.o.seed;
     m.tau = p.o.tau;
     m.delta = p.o.delta;
+    m.dense_fp64 = fp64;
     m.err_flag = w.counters + 1;
 }
 
@@ -450,7 +566,21 @@ static int run_queries(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool
     AmcArgs m;
     make_args(g, p, q0, nq, fp64, &a, &m);
     const int grid = g->sm_count * 8;
-    launch_smm_start(fp64, a, grid, p.st);
+    const bool dense = a.dense_engine != 0;
+    DenseArgs d{};
+    if (dense) {
+        int rc = ensure_dense(g, nq, a.dense_width, fp64);
+        if (rc) return rc;
+        a.dense_X[0] = w.dX[0];
+        a.dense_X[1] = w.dX[1];
+        d = make_dense_args(g, q0, nq, a.dense_width);
+        launch_smm_setup(a, p.st);
+        launch_smm_alloc(a, p.st);
+        issue_dense_start(g, d, fp64, nq, p.st);
+        launch_smm_decide(a, p.st);
+    } else {
+        launch_smm_start(fp64, a, grid, p.st);
+    }
     launch_smm_advance(a, 0, false, p.st);
     note_launches(8);
     int32_t* n_want = reinterpret_cast<int32_t*>(w.host_rb + 2);
@@ -458,7 +588,13 @@ static int run_queries(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool
         GER_CUDA(cudaMemcpyAsync(n_want, &w.ctl->n_want, sizeof(int32_t), cudaMemcpyDeviceToHost, p.st));
         GER_CUDA(cudaStreamSynchronize(p.st));
         if (*n_want == 0) break;
-        launch_smm_iteration(fp64, a, grid, p.st);
+        if (dense) {
+            launch_smm_alloc(a, p.st);
+            launch_dense_iteration(fp64, d, p.st);
+            launch_smm_decide(a, p.st);
+        } else {
+            launch_smm_iteration(fp64, a, grid, p.st);
+        }
         launch_smm_advance(a, 0, false, p.st);
         note_launches(8);
     }
@@ -478,7 +614,8 @@ static void destroy_graph(BatchGraph& bg) {
 
 static bool same_key(const BatchGraph& bg, const Plan& p, bool fp64, const ger_graph* g) {
     return bg.valid && bg.nq == p.q && bg.fp64 == fp64 && std::memcmp(&bg.o, &p.o, sizeof(ger_options)) == 0 &&
-           bg.lambda == g->lambda && bg.pool == g->ws.ent && bg.state == g->ws.st && bg.prof == g_prof_on;
+           bg.lambda == g->lambda && bg.pool == g->ws.ent && bg.state == g->ws.st && bg.prof == g_prof_on &&
+           bg.dense == g->ws.dX[0] && bg.dense_w == (p.o.smm_engine ? dense_width_for(const_cast<ger_graph*>(g), p.o) : 0);
 }
 
 // Capture the whole batch as one graph: the initial SMM iteration, a
@@ -496,6 +633,15 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
     AmcArgs m;
     make_args(g, p, 0, p.q, fp64, &a, &m);
     const int grid = g->sm_count * 8;
+    const bool dense = a.dense_engine != 0;
+    DenseArgs d{};
+    if (dense) {
+        int rc = ensure_dense(g, p.q, a.dense_width, fp64);
+        if (rc) return rc;
+        a.dense_X[0] = w.dX[0];
+        a.dense_X[1] = w.dX[1];
+        d = make_dense_args(g, 0, p.q, a.dense_width);
+    }
     cudaGraph_t graph = nullptr;
     GER_CUDA(cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle handle;
@@ -510,7 +656,14 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
     if (e == cudaSuccess) {
         cudaMemsetAsync(w.counters, 0, 4 * sizeof(int), st);
         cudaMemsetAsync(w.ctl, 0, sizeof(SmmCtl), st);
-        launch_smm_start(fp64, a, grid, st);
+        if (dense) {
+            launch_smm_setup(a, st);
+            launch_smm_alloc(a, st);
+            issue_dense_start(g, d, fp64, p.q, st);
+            launch_smm_decide(a, st);
+        } else {
+            launch_smm_start(fp64, a, grid, st);
+        }
         launch_smm_advance(a, handle, true, st);
         cudaStreamCaptureStatus cs;
         const cudaGraphNode_t* deps = nullptr;
@@ -533,7 +686,13 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
             e = cudaStreamBeginCaptureToGraph(st2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
             if (e == cudaSuccess) {
                 g_prof_suspend = true;  // no event records inside a conditional body
-                launch_smm_iteration(fp64, a, grid, st2);
+                if (dense) {
+                    launch_smm_alloc(a, st2);
+                    launch_dense_iteration(fp64, d, st2);
+                    launch_smm_decide(a, st2);
+                } else {
+                    launch_smm_iteration(fp64, a, grid, st2);
+                }
                 launch_smm_advance(a, handle, true, st2);
                 g_prof_suspend = false;
                 e = cudaStreamEndCapture(st2, &body);
@@ -566,6 +725,8 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
     bg.lambda = g->lambda;
     bg.pool = w.ent;
     bg.state = w.st;
+    bg.dense = w.dX[0];
+    bg.dense_w = dense ? a.dense_width : 0;
     bg.prof = g_prof_on;
     bg.launches = 8 + 1 + 2 * p.o.tau + 1;
     return GER_OK;
@@ -681,6 +842,8 @@ void ger_default_options(ger_options* o) {
     o->ell_formula = GER_ELL_REFINED;
     o->seed = 3;
     o->sparse_cap = 0;
+    o->smm_engine = GER_ENGINE_SPARSE;
+    o->dense_width = 0;
 }
 
 const char* ger_last_error(void) { return g_err; }
@@ -811,6 +974,14 @@ static int check_opts(const ger_options* opt, ger_options* o) {
     if (o->switch_policy != GER_SWITCH_RULE && o->switch_policy != GER_SWITCH_FIXED)
         return fail(GER_ERR_INVALID, "bad switch policy");
     if (o->ell_formula != GER_ELL_REFINED && o->ell_formula != GER_ELL_PENG) return fail(GER_ERR_INVALID, "bad ell formula");
+    if (o->smm_engine != GER_ENGINE_SPARSE && o->smm_engine != GER_ENGINE_DENSE)
+        return fail(GER_ERR_INVALID, "bad smm engine");
+    if (o->dense_width != 0) {
+        const int vec = o->precision == GER_FP64 ? 2 : 4;
+        const int lpr = o->dense_width / vec;
+        if (o->dense_width % vec || (lpr != 8 && lpr != 16 && lpr != 32))
+            return fail(GER_ERR_INVALID, "dense_width must be 8, 16 or 32 lanes times %d columns", vec);
+    }
     return GER_OK;
 }
 

@@ -37,6 +37,9 @@ struct QState {
     int64_t table_off;        // entry offset of this query's lookup table
     int32_t table_mask;       // capacity - 1 (power of two), -1: no table
     int32_t front;            // |V_s u V_t| after the last SMM iteration
+    const void* dense_vals;   // dense engine: (s*, t*) of node v at dense_vals + v * dense_stride
+    int32_t dense_stride;     // values per row of the query's dense block
+    int32_t pad1;
 };
 
 // One slot of a query's frontier table (open addressing, linear probing):
@@ -55,7 +58,9 @@ struct QSmm {
     int32_t shift_s, shift_t;    // fixed-point scales 2^shift of s*, t*
     int32_t lb_target;           // iterations wanted by a fixed policy, -1: rule
     int32_t want;                // slots requested for the next table, 0: none
-    int32_t pad;
+    int32_t dense;               // 1: this query's SMM runs on the dense engine
+    int32_t dgo;                 // dense engine: 1 while iterations continue
+    int32_t dblock, dcol;        // dense block and column pair
     int64_t tab_off, tab_cap;    // table of the current frontier
     int64_t ntab_off, ntab_cap;  // table being filled
     unsigned long long vol_paper;  // sum_{V_s} d + sum_{V_t} d (Eq. 17)

@@ -31,8 +31,34 @@ struct SmmArgs {
     int64_t* seg_off[2];   // nq + 1 entries: first slot (last entry: end)
     int64_t* heavy;        // per chunk of a high-degree frontier node: slot << 20 | chunk index
     int64_t heavy_cap;
+    // dense engine (all queries of the launch when dense_engine != 0)
+    int32_t dense_engine;
+    int32_t dense_width;   // columns per dense block (2 per query)
+    int32_t dense_fp64;
+    void* dense_X[2];      // value buffers: block b at b * n * dense_width
     SmmCtl* ctl;
     int* err_flag;
+};
+
+// Per-warp partial sums of the dense SpMM epilogue, per query.
+struct DensePartial {
+    unsigned long long vp, vu, cnt;
+    double s1, s2, t1, t2;
+};
+
+struct DenseArgs {
+    DevGraph g;
+    int32_t nblocks;
+    int32_t width;          // columns per block (B)
+    void* X[2];             // values, nblocks * n * width each
+    uint32_t* S[2];         // support bits, nblocks * n * max(width / 32, 1) words each
+    const int32_t* block_q; // nblocks * width/2: query of each column pair, -1: none
+    int32_t* block_run;     // per block: any query still iterating
+    QState* st;
+    QSmm* sm;
+    DensePartial* part;     // nblocks * part_warps * width/2
+    int32_t part_warps;     // warps of the SpMM grid per block (grid.x = part_warps / 8)
+    SmmCtl* ctl;
 };
 
 struct AmcArgs {
@@ -47,6 +73,7 @@ struct AmcArgs {
     uint64_t seed;
     int32_t tau;
     int32_t batch;         // 1-based batch index b
+    int32_t dense_fp64;    // element type of dense-engine values
     double delta;
     int* err_flag;
 };
@@ -69,6 +96,11 @@ void launch_smm_decide(const SmmArgs& a, cudaStream_t st);
 void launch_smm_advance(const SmmArgs& a, cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st);
 void launch_smm_start(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 void launch_smm_iteration(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
+// the dense engine: iteration 0 and one pull-SpMM iteration (+ its epilogue)
+int dense_lanes_per_row(int width, bool fp64);
+void launch_dense_map(const DenseArgs& d, int64_t nq, cudaStream_t st);
+void launch_dense_init(bool fp64, const DenseArgs& d, cudaStream_t st);
+void launch_dense_iteration(bool fp64, const DenseArgs& d, cudaStream_t st);
 void launch_amc_schedule(const AmcArgs& a, cudaStream_t st);
 void launch_amc_walk(const AmcArgs& a, int grid, cudaStream_t st);
 // batch statistics of batch a.batch; the last CTA schedules batch a.batch + 1
@@ -83,7 +115,7 @@ void note_launches(int k);
 
 // kernel families timed by the profiler
 enum Family : int { FAM_SMM_SETUP = 0, FAM_SMM_ALLOC, FAM_SMM_CLEAR, FAM_SMM_PUSH, FAM_SMM_PUSH_HEAVY, FAM_SMM_FINISH,
-                    FAM_SMM_TOP2, FAM_SMM_DECIDE, FAM_AMC_SCHEDULE, FAM_AMC_WALK, FAM_AMC_REDUCE,
+                    FAM_SMM_TOP2, FAM_SMM_DECIDE, FAM_DENSE_SPMM, FAM_AMC_SCHEDULE, FAM_AMC_WALK, FAM_AMC_REDUCE,
                     FAM_FINALIZE, FAM_LANCZOS, FAM_COUNT };
 // bracket one launch on stream st with profiler events (no-op when off)
 void prof_begin(int fam, cudaStream_t st);

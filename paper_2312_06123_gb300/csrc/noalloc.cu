@@ -102,6 +102,8 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
         (o.switch_policy != GER_SWITCH_RULE && o.switch_policy != GER_SWITCH_FIXED) ||
         (o.ell_formula != GER_ELL_REFINED && o.ell_formula != GER_ELL_PENG))
         return set_error(GER_ERR_INVALID, "invalid options");
+    if (o.smm_engine != GER_ENGINE_SPARSE)
+        return set_error(GER_ERR_INVALID, "the no-alloc entry point runs the sparse SMM engine only");
     DevGraph dg;
     double lambda;
     bool has_lambda;
@@ -161,6 +163,10 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     a.seg_q[1] = a.seg_q[0] + kNoAllocMaxQueries;
     a.seg_off[0] = reinterpret_cast<int64_t*>(base + kOffSegOff);
     a.seg_off[1] = a.seg_off[0] + (kNoAllocMaxQueries + 1);
+    a.dense_engine = 0;
+    a.dense_width = 2;
+    a.dense_fp64 = fp64;
+    a.dense_X[0] = a.dense_X[1] = nullptr;
     a.heavy = reinterpret_cast<int64_t*>(base + kOffHeavy);
     a.heavy_cap = kNoAllocHeavy;
     a.ctl = ctl;
@@ -190,6 +196,7 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     m.seed = o.seed;
     m.tau = o.tau;
     m.delta = o.delta;
+    m.dense_fp64 = fp64;
     m.err_flag = counters + 1;
     m.batch = 1;
     launch_amc_schedule(m, st);

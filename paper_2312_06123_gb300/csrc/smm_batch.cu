@@ -130,6 +130,12 @@ __global__ void smm_setup_kernel(SmmArgs a) {
         Q->walk_steps = 0; Q->checksum = 0; Q->ppc = 0; Q->nchunks = 0; Q->table_off = 0;
         Q->table_mask = -1; Q->front = 0; Q->ell = 0; Q->ell_b = 0; Q->lf = 0; Q->ds = 0; Q->dt = 0;
         M->run = 0; M->want = 0; M->tab_off = M->tab_cap = M->ntab_off = M->ntab_cap = 0;
+        M->dense = a.dense_engine ? 1 : 0;
+        M->dgo = 0;
+        M->dblock = a.dense_engine ? (int32_t)(q / (a.dense_width / 2)) : -1;
+        M->dcol = a.dense_engine ? (int32_t)(q % (a.dense_width / 2)) : -1;
+        Q->dense_vals = nullptr;
+        Q->dense_stride = 0;
         M->vol_paper = M->vol_union = M->count = 0;
         M->max1s = M->max1t = M->max2s = M->max2t = M->cnt1s = M->cnt1t = 0;
         M->sval[0] = M->sval[1] = M->sval[2] = M->sval[3] = 0.0;
@@ -172,7 +178,8 @@ __global__ void smm_setup_kernel(SmmArgs a) {
         M->inv_ds = 1.0 / ds;
         M->inv_dt = 1.0 / dt;
         M->lb_target = a.policy == 2 ? (a.fixed_lb < 0 ? (int32_t)ell : min(a.fixed_lb, (int32_t)ell)) : -1;
-        M->want = 8;  // F_0 = {s, t}
+        if (M->dense) M->dgo = 1;  // the dense engine sets up F_0 in its own buffers
+        else M->want = 8;          // F_0 = {s, t}
     }
 }
 
@@ -200,7 +207,7 @@ __global__ void __launch_bounds__(kCta) smm_alloc_kernel(SmmArgs a) {
             QSmm* M = a.sm + q;
             want = M->want;
             M->want = 0;
-            M->run = want > 0;
+            M->run = M->dense ? M->dgo : (want > 0);
         }
         int64_t tot, ntot;
         const int64_t ex = cta_excl_scan(want, scan, &tot);
@@ -496,10 +503,7 @@ __device__ void switch_quantities(int64_t lf, double s1, double s2, double t1, d
 // decide: one thread per query whose table was just finished
 __global__ void smm_decide_kernel(SmmArgs a) {
     const int iter = a.ctl->iter;
-    const int parity = iter & 1;
-    const int nseg = a.ctl->nseg[parity];
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nseg; k += gridDim.x * blockDim.x) {
-        const int q = a.seg_q[parity][k];
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < a.nq; q += gridDim.x * blockDim.x) {
         QSmm* M = a.sm + q;
         QState* Q = a.st + q;
         if (!M->run || Q->status != ST_SMM) continue;
@@ -529,7 +533,10 @@ __global__ void smm_decide_kernel(SmmArgs a) {
         // the table just finished holds the current frontier
         M->tab_off = M->ntab_off;
         M->tab_cap = M->ntab_cap;
-        if (go) {
+        if (go && M->dense) {
+            M->dgo = 1;
+            atomicAdd(&a.ctl->n_want, 1);
+        } else if (go) {
             int64_t cap = 16;
             while (cap < 2 * (int64_t)M->vol_union) cap <<= 1;
             if (cap > a.max_table) {
@@ -543,6 +550,7 @@ __global__ void smm_decide_kernel(SmmArgs a) {
             M->want = (int32_t)cap;
             atomicAdd(&a.ctl->n_want, 1);
         } else {
+            M->dgo = 0;
             Q->ell_b = (int32_t)lb;
             Q->lf = (int32_t)lf;
             Q->psi = psi;
@@ -551,8 +559,18 @@ __global__ void smm_decide_kernel(SmmArgs a) {
             Q->eta0 = eta0;
             Q->eta = eta0;
             Q->front = (int32_t)M->count;
-            Q->table_off = M->tab_off;
-            Q->table_mask = (int32_t)(M->tab_cap - 1);
+            if (M->dense) {
+                // the values of the last iteration sit in dense buffer (iter & 1)
+                const size_t esz = a.dense_fp64 ? sizeof(double) : sizeof(float);
+                const char* base = reinterpret_cast<const char*>(a.dense_X[iter & 1]);
+                Q->dense_vals = base + ((size_t)M->dblock * (size_t)a.g.n * (size_t)a.dense_width + 2 * (size_t)M->dcol) * esz;
+                Q->dense_stride = a.dense_width;
+                Q->table_off = 0;
+                Q->table_mask = -1;
+            } else {
+                Q->table_off = M->tab_off;
+                Q->table_mask = (int32_t)(M->tab_cap - 1);
+            }
             if (lf > 0) {
                 Q->status = ST_AMC;
             } else {

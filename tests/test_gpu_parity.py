@@ -183,6 +183,44 @@ def test_peng_ell(c1):
 
 
 # ---------------------------------------------------------------------------
+# dense engine (pull SpMM over blocks of query vectors)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec,rel,width", [(geer.GER_FP64, 1e-9, 64), (geer.GER_FP64, 1e-9, 16),
+                                            (geer.GER_FP32, 1e-5, 128), (geer.GER_FP32, 1e-5, 32)])
+def test_dense_engine_standalone_smm(c1, prec, rel, width):
+    # standalone SMM (l_b = l) on the dense engine equals the truncated series
+    w, g, G, lam = c1
+    q = 40
+    r, st = G.query(w.s[:q], w.t[:q], 0.1, _opts(precision=prec, switch_policy=geer.GER_SWITCH_FIXED,
+                                                  fixed_ell_b=-1, smm_engine=geer.GER_ENGINE_DENSE,
+                                                  dense_width=width), stats=True)
+    for i in range(q):
+        assert st[i]["walks"] == 0 and st[i]["ell_b"] == st[i]["ell"]
+        ref = oracle.geer(g, int(w.s[i]), int(w.t[i]), 0.1, lam, forced_ell_b=int(st[i]["ell"]))
+        assert r[i] == pytest.approx(ref.r, rel=rel)
+        assert st[i]["volume"] == ref.volume
+
+
+@pytest.mark.parametrize("prec,rel", [(geer.GER_FP64, 1e-9), (geer.GER_FP32, 1e-5)])
+def test_dense_engine_rule_matches_oracle(c1, prec, rel):
+    w, g, G, lam = c1
+    r, st = G.query(w.s, w.t, w.eps, _opts(precision=prec, smm_engine=geer.GER_ENGINE_DENSE), stats=True)
+    _check_against_oracle(w, g, lam, r, st, rel, rel, max_disagree=1 if prec == geer.GER_FP64 else 10)
+
+
+def test_dense_and_sparse_engines_agree(c1):
+    w, g, G, lam = c1
+    o = dict(precision=geer.GER_FP64)
+    r1, s1 = G.query(w.s, w.t, w.eps, _opts(**o), stats=True)
+    r2, s2 = G.query(w.s, w.t, w.eps, _opts(smm_engine=geer.GER_ENGINE_DENSE, **o), stats=True)
+    same = (s1["ell_b"] == s2["ell_b"]) & (s1["eta0"] == s2["eta0"]) & (s1["batches"] == s2["batches"])
+    assert same.sum() >= w.q - 1
+    assert np.array_equal(s1["checksum"][same], s2["checksum"][same])
+    assert np.allclose(r1[same], r2[same], rtol=1e-9, atol=0)
+
+
+# ---------------------------------------------------------------------------
 # closed forms and edge cases
 # ---------------------------------------------------------------------------
 
