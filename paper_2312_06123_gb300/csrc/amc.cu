@@ -188,12 +188,12 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
                             double xs, xt;
                             if (a.dense_fp64) {
                                 const double2 p2 = __ldg(reinterpret_cast<const double2*>(dvals + (size_t)nx[i] * dstride * 8));
-                                xs = p2.x;
-                                xt = p2.y;
+                                xs = fabs(p2.x);  // the sign bit carries the support
+                                xt = fabs(p2.y);
                             } else {
                                 const float2 p2 = __ldg(reinterpret_cast<const float2*>(dvals + (size_t)nx[i] * dstride * 4));
-                                xs = (double)p2.x;
-                                xt = (double)p2.y;
+                                xs = (double)fabsf(p2.x);
+                                xt = (double)fabsf(p2.y);
                             }
                             if (act[i]) {
                                 inf[i] = node_row(g, nx[i]);

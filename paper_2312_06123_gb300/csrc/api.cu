@@ -151,11 +151,13 @@ struct Workspace {
     int64_t pool_cap = 0;
     // dense engine
     void* dX[2] = {nullptr, nullptr};
-    uint32_t* dS[2] = {nullptr, nullptr};
     int32_t* dblock_q = nullptr;
     int32_t* dblock_run = nullptr;
+    unsigned int* dunit_ctr = nullptr;
+    unsigned int* dheavy_ctr = nullptr;
+    void* dpieces = nullptr;
     DensePartial* dpart = nullptr;
-    size_t dX_bytes = 0, dS_bytes = 0, dpart_n = 0;
+    size_t dX_bytes = 0, dpart_n = 0, dpieces_bytes = 0, dheavy_ctr_n = 0;
     int64_t dblock_q_n = 0;
     // counters: [1] error flag (int), [2] AMC done counter
     int* counters = nullptr;
@@ -197,6 +199,11 @@ struct ger_graph {
     cudaStream_t stream = nullptr;
     cudaStream_t stream2 = nullptr;  // captures the SMM while body
     int dense_tuned[2] = {0, 0};     // autotuned dense block width (FP32, FP64), 0: not tuned
+    int dense_ctas = 0;              // dense SpMM CTAs per SM and block, 0: default
+    int4* dense_units = nullptr;     // dense SpMM work units (null when nnz >= 2^32)
+    int4* dense_heavy = nullptr;     // dense SpMM heavy rows
+    int32_t dense_nunits = 0, dense_nheavy = 0, dense_nslots = 0;
+    bool dense_ready = false;        // SpMM kernels opted into their shared memory
     geer::Workspace ws;
     geer::BatchGraph bg;
 };
@@ -208,8 +215,9 @@ static void free_ws(Workspace& w) {
     cudaFree(w.chunk_begin); cudaFree(w.partial); cudaFree(w.qsmm); cudaFree(w.seg_q); cudaFree(w.seg_off);
     cudaFree(w.ctl); cudaFree(w.ent); cudaFree(w.sums); cudaFree(w.yvals); cudaFree(w.counters);
     cudaFree(w.heavy);
-    cudaFree(w.dX[0]); cudaFree(w.dX[1]); cudaFree(w.dS[0]); cudaFree(w.dS[1]);
-    cudaFree(w.dblock_q); cudaFree(w.dblock_run); cudaFree(w.dpart);
+    cudaFree(w.dX[0]); cudaFree(w.dX[1]);
+    cudaFree(w.dblock_q); cudaFree(w.dblock_run); cudaFree(w.dunit_ctr); cudaFree(w.dheavy_ctr);
+    cudaFree(w.dpieces); cudaFree(w.dpart);
     if (w.host_rb) cudaFreeHost(w.host_rb);
     w = Workspace();
 }
@@ -395,16 +403,34 @@ static int dense_width_for(ger_graph* g, const ger_options& o) {
     return tuned ? tuned : (fp64 ? 64 : 128);
 }
 
+// Warps of the dense SpMM grid per block (one partial slot each).
+static int dense_part_warps(const ger_graph* g) {
+    int c = g->dense_ctas;
+    if (c <= 0) {
+        const char* v = std::getenv("GEER_DENSE_CTAS");
+        c = v ? std::atoi(v) : 0;
+    }
+    if (c <= 0 || c > 8) c = 2;
+    return g->sm_count * c * 8;
+}
+
 // Make room for the dense engine's blocks (nq queries at `width` columns).
 static int ensure_dense(ger_graph* g, int64_t nq, int width, bool fp64) {
     Workspace& w = g->ws;
+    if (!g->dense_units) return fail(GER_ERR_INVALID, "the dense engine needs fewer than 2^32 stored edges");
+    if (!g->dense_ready) {
+        const int e = dense_prepare();
+        if (e) return cuda_fail((cudaError_t)e, "dense SpMM shared-memory opt-in");
+        g->dense_ready = true;
+    }
     const int64_t qpb = width / 2;
     const int64_t nblocks = (nq + qpb - 1) / qpb;
-    const size_t xb = (size_t)nblocks * (size_t)g->n * (size_t)width * (fp64 ? 8 : 4);
-    const size_t words = (size_t)std::max(width / 32, 1);
-    const size_t sb = (size_t)nblocks * (size_t)g->n * words * 4;
-    const int part_warps = g->sm_count * 2 * 8;
+    const size_t esz = fp64 ? 8 : 4;
+    const size_t xb = (size_t)nblocks * (size_t)g->n * (size_t)width * esz;
+    const int part_warps = dense_part_warps(g);
     const size_t pn = (size_t)nblocks * (size_t)part_warps * (size_t)qpb;
+    const size_t pb = std::max<size_t>((size_t)nblocks * (size_t)g->dense_nslots * (size_t)width * esz, 16);
+    const size_t hn = std::max<size_t>((size_t)nblocks * (size_t)g->dense_nheavy, 1);
     if (xb > w.dX_bytes) {
         cudaFree(w.dX[0]); cudaFree(w.dX[1]);
         w.dX[0] = w.dX[1] = nullptr;
@@ -415,15 +441,26 @@ static int ensure_dense(ger_graph* g, int64_t nq, int width, bool fp64) {
         }
         w.dX_bytes = xb;
     }
-    if (sb > w.dS_bytes) {
-        cudaFree(w.dS[0]); cudaFree(w.dS[1]);
-        w.dS[0] = w.dS[1] = nullptr;
-        w.dS_bytes = 0;
-        if (cudaMalloc(&w.dS[0], sb) != cudaSuccess || cudaMalloc(&w.dS[1], sb) != cudaSuccess) {
+    if (pb > w.dpieces_bytes) {
+        cudaFree(w.dpieces);
+        w.dpieces = nullptr;
+        w.dpieces_bytes = 0;
+        if (cudaMalloc(&w.dpieces, pb) != cudaSuccess) {
             cudaGetLastError();
-            return fail(GER_ERR_OOM, "dense support bits");
+            return fail(GER_ERR_OOM, "dense heavy-row pieces");
         }
-        w.dS_bytes = sb;
+        w.dpieces_bytes = pb;
+    }
+    if (hn > w.dheavy_ctr_n) {
+        cudaFree(w.dheavy_ctr);
+        w.dheavy_ctr = nullptr;
+        w.dheavy_ctr_n = 0;
+        // zero once: the warp that finishes a heavy row resets its counter
+        if (alloc(&w.dheavy_ctr, hn) || cudaMemset(w.dheavy_ctr, 0, hn * sizeof(unsigned int))) {
+            cudaGetLastError();
+            return fail(GER_ERR_OOM, "dense heavy-row counters");
+        }
+        w.dheavy_ctr_n = hn;
     }
     if (pn > w.dpart_n) {
         cudaFree(w.dpart);
@@ -437,9 +474,9 @@ static int ensure_dense(ger_graph* g, int64_t nq, int width, bool fp64) {
     }
     const int64_t nbq = nblocks * qpb;
     if (nbq > w.dblock_q_n) {
-        cudaFree(w.dblock_q); cudaFree(w.dblock_run);
-        w.dblock_q = nullptr; w.dblock_run = nullptr; w.dblock_q_n = 0;
-        if (alloc(&w.dblock_q, nbq) || alloc(&w.dblock_run, nblocks)) {
+        cudaFree(w.dblock_q); cudaFree(w.dblock_run); cudaFree(w.dunit_ctr);
+        w.dblock_q = nullptr; w.dblock_run = nullptr; w.dunit_ctr = nullptr; w.dblock_q_n = 0;
+        if (alloc(&w.dblock_q, nbq) || alloc(&w.dblock_run, nblocks) || alloc(&w.dunit_ctr, nblocks)) {
             cudaGetLastError();
             return fail(GER_ERR_OOM, "dense block map");
         }
@@ -456,15 +493,22 @@ static DenseArgs make_dense_args(ger_graph* g, int64_t q0, int64_t nq, int width
     d.nblocks = (int32_t)((nq + width / 2 - 1) / (width / 2));
     d.X[0] = w.dX[0];
     d.X[1] = w.dX[1];
-    d.S[0] = w.dS[0];
-    d.S[1] = w.dS[1];
     d.block_q = w.dblock_q;
     d.block_run = w.dblock_run;
     d.st = w.st + q0;
     d.sm = w.qsmm + q0;
     d.part = w.dpart;
-    d.part_warps = g->sm_count * 2 * 8;
+    d.part_warps = dense_part_warps(g);
     d.ctl = w.ctl;
+    d.units = g->dense_units;
+    d.nunits = g->dense_nunits;
+    d.heavy = g->dense_heavy;
+    d.nheavy = g->dense_nheavy;
+    d.nslots = g->dense_nslots;
+    d.unit_ctr = w.dunit_ctr;
+    d.heavy_ctr = w.dheavy_ctr;
+    d.pieces = w.dpieces;
+
     return d;
 }
 
@@ -473,11 +517,9 @@ static DenseArgs make_dense_args(ger_graph* g, int64_t q0, int64_t nq, int width
 static void issue_dense_start(ger_graph* g, const DenseArgs& d, bool fp64, int64_t nq, cudaStream_t st) {
     Workspace& w = g->ws;
     const size_t xb = (size_t)d.nblocks * (size_t)g->n * (size_t)d.width * (fp64 ? 8 : 4);
-    const size_t sb = (size_t)d.nblocks * (size_t)g->n * (size_t)std::max(d.width / 32, 1) * 4;
+    // buffer 0 starts as zeros plus e_s, e_t; buffer 1 is written in full by
+    // iteration 1 in every column that is ever read
     cudaMemsetAsync(w.dX[0], 0, xb, st);
-    cudaMemsetAsync(w.dX[1], 0, xb, st);
-    cudaMemsetAsync(w.dS[0], 0, sb, st);
-    cudaMemsetAsync(w.dS[1], 0, sb, st);
     launch_dense_map(d, nq, st);
     launch_dense_init(fp64, d, st);
 }
@@ -920,6 +962,24 @@ int ger_load_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int 
             ger_free(g);
             return fail(GER_ERR_OOM, "device copy of the node records");
         }
+        if (n < INT32_MAX) {
+            std::vector<int4> units, heavy;
+            int32_t nslots = 0;
+            build_dense_units(n, row_ptr, &units, &heavy, &nslots);
+            if (cudaMalloc(&g->dense_units, units.size() * sizeof(int4) + 16) != cudaSuccess ||
+                cudaMalloc(&g->dense_heavy, heavy.size() * sizeof(int4) + 16) != cudaSuccess ||
+                cudaMemcpy(g->dense_units, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice) !=
+                    cudaSuccess ||
+                cudaMemcpy(g->dense_heavy, heavy.data(), heavy.size() * sizeof(int4), cudaMemcpyHostToDevice) !=
+                    cudaSuccess) {
+                cudaGetLastError();
+                ger_free(g);
+                return fail(GER_ERR_OOM, "device copy of the dense work units");
+            }
+            g->dense_nunits = (int32_t)units.size();
+            g->dense_nheavy = (int32_t)heavy.size();
+            g->dense_nslots = nslots;
+        }
     }
     *out = g;
     return GER_OK;
@@ -934,6 +994,8 @@ void ger_free(ger_graph* g) {
     cudaFree(g->row_ptr);
     cudaFree(g->col_idx);
     cudaFree(g->node_info);
+    cudaFree(g->dense_units);
+    cudaFree(g->dense_heavy);
     if (g->stream) cudaStreamDestroy(g->stream);
     if (g->stream2) cudaStreamDestroy(g->stream2);
     delete g;
@@ -976,12 +1038,8 @@ static int check_opts(const ger_options* opt, ger_options* o) {
     if (o->ell_formula != GER_ELL_REFINED && o->ell_formula != GER_ELL_PENG) return fail(GER_ERR_INVALID, "bad ell formula");
     if (o->smm_engine != GER_ENGINE_SPARSE && o->smm_engine != GER_ENGINE_DENSE)
         return fail(GER_ERR_INVALID, "bad smm engine");
-    if (o->dense_width != 0) {
-        const int vec = o->precision == GER_FP64 ? 2 : 4;
-        const int lpr = o->dense_width / vec;
-        if (o->dense_width % vec || (lpr != 8 && lpr != 16 && lpr != 32))
-            return fail(GER_ERR_INVALID, "dense_width must be 8, 16 or 32 lanes times %d columns", vec);
-    }
+    if (o->dense_width != 0 && !dense_width_ok(o->dense_width, o->precision == GER_FP64))
+        return fail(GER_ERR_INVALID, "dense_width must be 32, 64 or 128 (FP32) or 32 or 64 (FP64)");
     return GER_OK;
 }
 

@@ -3,17 +3,33 @@
 // frontiers cover much of the graph (deep SMM: small eps, low degrees, or a
 // fixed l_b such as the standalone SMM of Section 4.1.1).
 //
-// A dense block holds B = LPR * VEC columns, the (s*, t*) pairs of B/2
-// queries, row-major: X[v * B + c], double-buffered across iterations, and
-// one support bit per column and row (Eq. 17's V_s, V_t, kept
-// structurally). Per row v of the graph, LPR lanes each own VEC columns:
-//   y(v, c) = (sum over u in N(v), in CSR order, of x(u, c)) / d(v),
+// A dense block holds B = 32 * VEC columns, the (s*, t*) pairs of B/2
+// queries, row-major: X[v * B + c], double-buffered across iterations. Lane
+// l of a warp owns columns [l * VEC, (l + 1) * VEC), so one gathered row is
+// one coalesced B * sizeof(T) load. Per row v:
+//   y(v, c) = (sum over u in N(v) of x(u, c)) / d(v),
 //   support(v, c) = OR over u in N(v) of support(u, c),
-// so each column's sum is sequential in CSR order, as in the oracle's pull.
+// with support kept structurally (Eq. 17's V_s, V_t) in the sign bit of the
+// stored value: every value is >= 0, a stored -y means "y, in the support".
+// Once every running column of a block covers all n nodes (support at i
+// steps then stays full, the graph being connected), the kernel stops
+// tracking it.
+//
+// Work is split into units built once per graph: runs of up to 32 light rows
+// (at most kUnitEdges edges), and pieces of kPieceEdges edges of the heavy
+// rows (degree > kHeavyDeg), handed out by an atomic counter per block,
+// heavy pieces first. A warp walks the edges of its unit with G row gathers
+// in flight; a heavy row's pieces write partial sums, and the warp that
+// completes a row's last piece adds them in piece order and finishes the
+// row, so every sum has a fixed order and the result is deterministic.
+//
 // Columns of queries that left SMM keep their last values (the walks read
-// them). The epilogue is fused: per query, Eq. 17's volume, the next
-// push volume, |V|, max_1/max_2 of s* and t* (per-warp partials merged in a
-// fixed order) and the values at s and t for the series terms.
+// them). The epilogue is fused: per query, Eq. 17's volume, the support
+// union's volume and size, max_1/max_2 of s* and t* (per-warp partials
+// merged in a fixed order) and the values at s and t for the series terms.
+#include <algorithm>
+#include <vector>
+
 #include "geer_internal.cuh"
 #include "geer_kernels.h"
 
@@ -21,39 +37,89 @@ namespace geer {
 
 namespace {
 
-template <typename T> struct Vec;
-template <> struct Vec<float> {
-    using type = float4;
-    static constexpr int n = 4;
+constexpr int kHeavyDeg = 512;    // rows above this degree are split into pieces
+constexpr int kPieceEdges = 512;  // edges per heavy-row piece
+constexpr int kUnitRows = 32;     // rows per light unit (one node record per lane)
+constexpr int kUnitEdges = 512;   // edges per light unit
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T, int VEC>
+struct Pack {
+    T e[VEC];
 };
-template <> struct Vec<double> {
-    using type = double2;
-    static constexpr int n = 2;
-};
+
+// One lane's VEC consecutive values of a row, read-only path (the gathers).
+template <typename T, int VEC>
+__device__ __forceinline__ Pack<T, VEC> ld_row(const T* p) {
+    Pack<T, VEC> r;
+    if constexpr (sizeof(T) == 4 && VEC == 4) {
+        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+        r.e[0] = v.x; r.e[1] = v.y; r.e[2] = v.z; r.e[3] = v.w;
+    } else if constexpr (sizeof(T) == 4 && VEC == 2) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+        r.e[0] = v.x; r.e[1] = v.y;
+    } else if constexpr (sizeof(T) == 8 && VEC == 2) {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(p));
+        r.e[0] = v.x; r.e[1] = v.y;
+    } else {
+        static_assert(VEC == 1, "unsupported lane width");
+        r.e[0] = __ldg(p);
+    }
+    return r;
+}
+
+// Same, through L2 only (pieces written by other warps of the same launch).
+template <typename T, int VEC>
+__device__ __forceinline__ Pack<T, VEC> ld_l2(const T* p) {
+    Pack<T, VEC> r;
+    if constexpr (sizeof(T) == 4 && VEC == 4) {
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(p));
+        r.e[0] = v.x; r.e[1] = v.y; r.e[2] = v.z; r.e[3] = v.w;
+    } else if constexpr (sizeof(T) == 4 && VEC == 2) {
+        const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+        r.e[0] = v.x; r.e[1] = v.y;
+    } else if constexpr (sizeof(T) == 8 && VEC == 2) {
+        const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+        r.e[0] = v.x; r.e[1] = v.y;
+    } else {
+        r.e[0] = __ldcg(p);
+    }
+    return r;
+}
+
+// Vector store; `streaming` marks it evict-first (the next iteration's rows),
+// else it stays in L2 (piece partials).
+template <typename T, int VEC, bool streaming>
+__device__ __forceinline__ void st_row(T* p, const Pack<T, VEC>& r) {
+    if constexpr (sizeof(T) == 4 && VEC == 4) {
+        const float4 v = make_float4(r.e[0], r.e[1], r.e[2], r.e[3]);
+        if constexpr (streaming) __stcs(reinterpret_cast<float4*>(p), v);
+        else __stcg(reinterpret_cast<float4*>(p), v);
+    } else if constexpr (sizeof(T) == 4 && VEC == 2) {
+        const float2 v = make_float2(r.e[0], r.e[1]);
+        if constexpr (streaming) __stcs(reinterpret_cast<float2*>(p), v);
+        else __stcg(reinterpret_cast<float2*>(p), v);
+    } else if constexpr (sizeof(T) == 8 && VEC == 2) {
+        const double2 v = make_double2(r.e[0], r.e[1]);
+        if constexpr (streaming) __stcs(reinterpret_cast<double2*>(p), v);
+        else __stcg(reinterpret_cast<double2*>(p), v);
+    } else {
+        if constexpr (streaming) __stcs(p, r.e[0]);
+        else __stcg(p, r.e[0]);
+    }
+}
+
+// High 32 bits of a value: bit 31 is its sign, i.e. its support bit.
+__device__ __forceinline__ uint32_t hiword(float x) { return __float_as_uint(x); }
+__device__ __forceinline__ uint32_t hiword(double x) { return (uint32_t)__double2hiint(x); }
+// y >= 0 with the support bit (bit 31 of s) as its sign.
+__device__ __forceinline__ float with_support(float y, uint32_t s) {
+    return __uint_as_float(__float_as_uint(y) | (s & 0x80000000u));
+}
+__device__ __forceinline__ double with_support(double y, uint32_t s) { return (s & 0x80000000u) ? -y : y; }
 
 template <typename T>
-__device__ __forceinline__ void vadd(typename Vec<T>::type& a, const typename Vec<T>::type& b);
-template <>
-__device__ __forceinline__ void vadd<float>(float4& a, const float4& b) {
-    a.x += b.x; a.y += b.y; a.z += b.z; a.w += b.w;
-}
-template <>
-__device__ __forceinline__ void vadd<double>(double2& a, const double2& b) {
-    a.x += b.x; a.y += b.y;
-}
-
-template <typename T>
-__device__ __forceinline__ T vget(const typename Vec<T>::type& a, int i);
-template <>
-__device__ __forceinline__ float vget<float>(const float4& a, int i) {
-    return i == 0 ? a.x : (i == 1 ? a.y : (i == 2 ? a.z : a.w));
-}
-template <>
-__device__ __forceinline__ double vget<double>(const double2& a, int i) {
-    return i == 0 ? a.x : a.y;
-}
-
-__device__ __forceinline__ void top2_push(double& a, double& b, double v) {
+__device__ __forceinline__ void top2_push(T& a, T& b, T v) {
     if (v > a) {
         b = a;
         a = v;
@@ -62,17 +128,267 @@ __device__ __forceinline__ void top2_push(double& a, double& b, double v) {
     }
 }
 
+// What one lane knows about its columns, and its epilogue accumulators.
+template <typename T, int VEC>
+struct Lane {
+    static constexpr int QPL = VEC >= 2 ? VEC / 2 : 1;  // queries per lane
+    int32_t q[QPL];
+    bool act[QPL];
+    int32_t s_node[QPL], t_node[QPL];
+    bool all_act;
+    // per-warp sums stay below the stored edge count, < 2^32 for this engine
+    uint32_t vol[VEC];  // sum of d(v) over support rows, per column
+    T m1[VEC], m2[VEC]; // top-2 of the column's values
+    uint32_t vu[QPL], cnt[QPL];
+};
+
+template <int VEC>
+__device__ __forceinline__ int lane_query(int e) {
+    return VEC >= 2 ? e / 2 : 0;
+}
+
+// Finish row v: y = acc / d(v), the support bits, the store of the running
+// columns and the epilogue. Called by the whole warp.
+template <typename T, int VEC, bool SUP>
+__device__ __forceinline__ void flush_row(Lane<T, VEC>& L, const DenseArgs& d, T* xrow, int64_t v, uint32_t deg,
+                                          const T (&acc)[VEC], const uint32_t (&sg)[VEC], int lane) {
+    const T inv = deg ? T(1) / (T)deg : T(0);
+    Pack<T, VEC> out;
+    uint32_t bit[VEC];
+    T y[VEC];
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+        bit[e] = SUP ? (sg[e] >> 31) : 1u;
+        y[e] = acc[e] * inv;
+        out.e[e] = with_support(y[e], bit[e] << 31);
+    }
+    if (L.all_act) {
+        st_row<T, VEC, true>(xrow, out);
+    } else {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e)
+            if (L.act[lane_query<VEC>(e)]) __stcs(xrow + e, out.e[e]);
+    }
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+        const int i = lane_query<VEC>(e);
+        const int which = VEC >= 2 ? (e & 1) : (lane & 1);  // 0: s*, 1: t*
+        if (!L.act[i]) continue;
+        L.vol[e] += deg * bit[e];
+        top2_push(L.m1[e], L.m2[e], y[e]);
+        if (v == L.s_node[i]) d.sm[L.q[i]].sval[which] = (double)y[e];
+        if (v == L.t_node[i]) d.sm[L.q[i]].sval[2 + which] = (double)y[e];
+    }
+#pragma unroll
+    for (int i = 0; i < Lane<T, VEC>::QPL; ++i) {
+        uint32_t both;
+        if constexpr (VEC >= 2) both = bit[2 * i] | bit[2 * i + 1];
+        else both = bit[0] | __shfl_xor_sync(kFull, bit[0], 1);
+        if (L.act[i]) {
+            L.vu[i] += deg * both;
+            L.cnt[i] += both;
+        }
+    }
+}
+
+// Asynchronous copy of one lane's VEC values of a gathered row into its
+// shared-memory ring slot (cp.async; completion tracked per thread by
+// commit/wait groups, so each lane later reads only bytes it copied itself).
+template <int BYTES>
+__device__ __forceinline__ void cp_async_lane(uint32_t dst, const void* src) {
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(dst), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ Pack<T, VEC> ld_ring(const T* p) {
+    Pack<T, VEC> r;
+    if constexpr (sizeof(T) == 4 && VEC == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        r.e[0] = v.x; r.e[1] = v.y; r.e[2] = v.z; r.e[3] = v.w;
+    } else if constexpr (sizeof(T) == 4 && VEC == 2) {
+        const float2 v = *reinterpret_cast<const float2*>(p);
+        r.e[0] = v.x; r.e[1] = v.y;
+    } else if constexpr (sizeof(T) == 8 && VEC == 2) {
+        const double2 v = *reinterpret_cast<const double2*>(p);
+        r.e[0] = v.x; r.e[1] = v.y;
+    } else {
+        r.e[0] = *p;
+    }
+    return r;
+}
+
+#ifndef GEER_DENSE_RING_BYTES
+#define GEER_DENSE_RING_BYTES 12288
+#endif
+constexpr int kRingBytes = GEER_DENSE_RING_BYTES;  // shared-memory gather ring per warp
+#ifndef GEER_DENSE_GROUP
+#define GEER_DENSE_GROUP 8
+#endif
+constexpr int kGroup = GEER_DENSE_GROUP;           // row gathers per cp.async group
+
+// Process the work units of block `blk` until they run out. Gathered rows
+// stream through the warp's ring: RING slots of one row each, D = RING / 8
+// groups of 8 rows in flight ahead of the consumer.
+template <typename T, int VEC, bool SUP>
+__device__ __forceinline__ void run_units(Lane<T, VEC>& L, const DenseArgs& d, int blk, int lane, T* ring) {
+    constexpr int B = 32 * VEC;
+    constexpr int LB = VEC * (int)sizeof(T);  // bytes per lane and row
+    constexpr int RING = kRingBytes / (B * (int)sizeof(T));
+    constexpr int D = RING / kGroup;
+    static_assert(D >= 2, "ring too small");
+    const int64_t n = d.g.n;
+    const int iter = d.ctl->iter;
+    const T* Xc = reinterpret_cast<const T*>(d.X[(iter & 1) ^ 1]) + (int64_t)blk * n * B + lane * VEC;
+    T* Xn = reinterpret_cast<T*>(d.X[iter & 1]) + (int64_t)blk * n * B + lane * VEC;
+    const int32_t* col = d.g.col_idx;
+    T* my = ring + lane * VEC;
+    const uint32_t my_s = (uint32_t)__cvta_generic_to_shared(my);
+
+    unsigned u = 0;
+    if (lane == 0) u = atomicAdd(d.unit_ctr + blk, 1u);
+    u = __shfl_sync(kFull, u, 0);
+    while (u < (unsigned)d.nunits) {
+        unsigned nu = 0;
+        if (lane == 0) nu = atomicAdd(d.unit_ctr + blk, 1u);  // next unit, used at the end
+        const int4 U = __ldg(d.units + u);
+        const bool heavy = U.x < 0;
+        const uint32_t e0 = (uint32_t)U.z, e1 = (uint32_t)U.w;
+        int nr = 0;
+        uint2 ni = make_uint2(0u, 0u);
+        if (!heavy) {
+            nr = U.y - U.x;
+            if (lane < nr) ni = __ldcs(d.g.node_info + U.x + lane);
+        }
+        // producer state: next edge to gather, its ring slot, the index chunk holding it
+        uint32_t ie = e0;
+        int islot = 0;
+        uint32_t icb = e0;
+        int32_t cid = e0 + lane < e1 ? __ldcs(col + e0 + lane) : 0;
+        int32_t cid_next = e0 + 32 + lane < e1 ? __ldcs(col + e0 + 32 + lane) : 0;
+        auto issue_group = [&]() {
+#pragma unroll
+            for (int j = 0; j < kGroup; ++j) {
+                if (ie < e1) {
+                    if (ie == icb + 32) {
+                        icb += 32;
+                        cid = cid_next;
+                        cid_next = icb + 32 + lane < e1 ? __ldcs(col + icb + 32 + lane) : 0;
+                    }
+                    const int32_t nb = __shfl_sync(kFull, cid, (int)(ie - icb));
+                    cp_async_lane<LB>(my_s + islot * (B * (int)sizeof(T)), Xc + (int64_t)nb * B);
+                    ++ie;
+                    islot = islot + 1 == RING ? 0 : islot + 1;
+                }
+            }
+            cp_async_commit();
+        };
+#pragma unroll 1
+        for (int g = 0; g < D; ++g) issue_group();
+
+        int ri = 0;
+        uint32_t row_end = heavy ? 0xffffffffu : __shfl_sync(kFull, ni.x + ni.y, 0);
+        T acc[VEC];
+        uint32_t sg[VEC];
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+            acc[e] = T(0);
+            sg[e] = 0u;
+        }
+        uint32_t ce = e0;
+        int cslot = 0;
+        while (ce < e1) {
+            cp_async_wait<D - 1>();  // the oldest group in flight has landed
+#pragma unroll
+            for (int j = 0; j < kGroup; ++j) {
+                if (ce < e1) {
+                    const Pack<T, VEC> v = ld_ring<T, VEC>(my + cslot * B);
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) {
+                        acc[e] += fabs(v.e[e]);
+                        if (SUP) sg[e] |= hiword(v.e[e]);
+                    }
+                    if (ce + 1 == row_end) {
+                        const int64_t row = (int64_t)U.x + ri;
+                        const uint32_t deg = __shfl_sync(kFull, ni.y, ri);
+                        flush_row<T, VEC, SUP>(L, d, Xn + row * B, row, deg, acc, sg, lane);
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) {
+                            acc[e] = T(0);
+                            sg[e] = 0u;
+                        }
+                        ++ri;
+                        const uint32_t nxt = __shfl_sync(kFull, ni.x + ni.y, ri & 31);
+                        row_end = ri < nr ? nxt : 0xffffffffu;
+                    }
+                    ++ce;
+                    cslot = cslot + 1 == RING ? 0 : cslot + 1;
+                }
+            }
+            issue_group();  // refill the slots just read (empty past the unit's end)
+        }
+        cp_async_wait<0>();
+        if (heavy) {
+            // a piece of a heavy row: store its partial sum; the last piece done finishes the row
+            const int h = -U.x - 1, p = U.y;
+            const int4 H = __ldg(d.heavy + h);  // {row, first slot, pieces, degree}
+            T* P = reinterpret_cast<T*>(d.pieces) + ((int64_t)blk * d.nslots + H.y) * B + lane * VEC;
+            Pack<T, VEC> out;
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) out.e[e] = with_support(acc[e], SUP ? sg[e] : 0x80000000u);
+            st_row<T, VEC, false>(P + (int64_t)p * B, out);
+            __threadfence();
+            unsigned old = 0;
+            unsigned* ctr = d.heavy_ctr + (int64_t)blk * d.nheavy + h;
+            if (lane == 0) old = atomicAdd(ctr, 1u);
+            old = __shfl_sync(kFull, old, 0);
+            if (old + 1 == (unsigned)H.z) {
+                __threadfence();
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    acc[e] = T(0);
+                    sg[e] = 0u;
+                }
+                constexpr int G = 8;
+                for (int p0 = 0; p0 < H.z; p0 += G) {
+                    Pack<T, VEC> w[G];
+#pragma unroll
+                    for (int j = 0; j < G; ++j)
+                        if (p0 + j < H.z) w[j] = ld_l2<T, VEC>(P + (int64_t)(p0 + j) * B);
+#pragma unroll
+                    for (int j = 0; j < G; ++j)
+                        if (p0 + j < H.z) {
+#pragma unroll
+                            for (int e = 0; e < VEC; ++e) {
+                                acc[e] += fabs(w[j].e[e]);
+                                if (SUP) sg[e] |= hiword(w[j].e[e]);
+                            }
+                        }
+                }
+                flush_row<T, VEC, SUP>(L, d, Xn + (int64_t)H.x * B, H.x, (uint32_t)H.w, acc, sg, lane);
+                if (lane == 0) *ctr = 0u;  // every piece of this launch has counted
+            }
+        }
+        u = __shfl_sync(kFull, nu, 0);
+    }
+}
+
 }  // namespace
 
-// Iteration 0 of the dense queries: columns e_s, e_t in buffer 0 and the
-// per-query sums of the initial frontier {s, t}.
+// Iteration 0 of the dense queries: columns e_s, e_t (in the support) in
+// buffer 0 and the per-query sums of the initial frontier {s, t}.
 template <typename T>
 __global__ void dense_init_kernel(DenseArgs d) {
     const int nq_block = d.width / 2;
     const int64_t total = (int64_t)d.nblocks * nq_block;
     T* X0 = reinterpret_cast<T*>(d.X[0]);
-    uint32_t* S0 = d.S[0];
-    const int words = d.width >= 32 ? d.width / 32 : 1;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
         const int b = (int)(k / nq_block), j = (int)(k % nq_block);
         const int q = d.block_q[k];
@@ -81,11 +397,8 @@ __global__ void dense_init_kernel(DenseArgs d) {
         QSmm* M = d.sm + q;
         if (Q->status != ST_SMM) continue;
         const int64_t base = (int64_t)b * d.g.n;
-        const int cs = 2 * j, ct = 2 * j + 1;
-        X0[(base + Q->s) * d.width + cs] = T(1);
-        X0[(base + Q->t) * d.width + ct] = T(1);
-        atomicOr(&S0[(base + Q->s) * words + cs / 32], 1u << (cs % 32));
-        atomicOr(&S0[(base + Q->t) * words + ct / 32], 1u << (ct % 32));
+        X0[(base + Q->s) * d.width + 2 * j] = T(-1);  // 1, in the support
+        X0[(base + Q->t) * d.width + 2 * j + 1] = T(-1);
         M->vol_paper = (unsigned long long)(Q->ds + Q->dt);
         M->vol_union = (unsigned long long)(Q->ds + Q->dt);
         M->count = 2;
@@ -100,162 +413,68 @@ __global__ void dense_init_kernel(DenseArgs d) {
 }
 
 // One pull SpMM iteration over every dense block with a running query.
-// grid.y = dense block; LPR lanes per row, 32/LPR rows per warp.
-template <typename T, int LPR>
-__global__ void __launch_bounds__(256) dense_spmm_kernel(DenseArgs d) {
-    using V = typename Vec<T>::type;
-    constexpr int VEC = Vec<T>::n;
-    constexpr int B = LPR * VEC;
-    constexpr int RPW = 32 / LPR;  // rows per warp
+// grid.y = dense block; grid.x * 8 = part_warps persistent warps per block.
+#ifndef GEER_DENSE_MINB
+#define GEER_DENSE_MINB 2
+#endif
+template <typename T, int VEC>
+__global__ void __launch_bounds__(256, GEER_DENSE_MINB) dense_spmm_kernel(DenseArgs d) {
+    constexpr int B = 32 * VEC;
+    using L_t = Lane<T, VEC>;
+    constexpr int QPL = L_t::QPL;
     const int blk = blockIdx.y;
-    if (!d.block_run[blk]) return;
-    const int iter = d.ctl->iter;
-    const T* Xc = reinterpret_cast<const T*>(d.X[(iter & 1) ^ 1]);
-    T* Xn = reinterpret_cast<T*>(d.X[iter & 1]);
-    const uint32_t* Sc = d.S[(iter & 1) ^ 1];
-    uint32_t* Sn = d.S[iter & 1];
-    constexpr int WORDS = B >= 32 ? B / 32 : 1;
+    const int run = d.block_run[blk];
+    if (!run) return;
     const int lane = threadIdx.x & 31;
-    const int sub = lane % LPR;       // column group of this lane
-    const int rsub = lane / LPR;      // row of this lane within the warp's rows
-    const unsigned gmask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1) << (rsub * LPR));
-    const int64_t n = d.g.n;
-    const int64_t boff = (int64_t)blk * n;
-    // the queries of this lane's columns: VEC/2 per lane
-    constexpr int QPL = VEC / 2;
-    int qs[QPL];
-    bool act[QPL];
-    int32_t s_node[QPL], t_node[QPL];
+    L_t L;
+    L.all_act = true;
 #pragma unroll
     for (int i = 0; i < QPL; ++i) {
-        const int j = sub * QPL + i;
-        qs[i] = d.block_q[blk * (B / 2) + j];
-        act[i] = qs[i] >= 0 && d.sm[qs[i]].run && d.sm[qs[i]].dense;
-        s_node[i] = act[i] ? d.st[qs[i]].s : -1;
-        t_node[i] = act[i] ? d.st[qs[i]].t : -1;
+        const int j = VEC >= 2 ? lane * QPL + i : lane / 2;
+        L.q[i] = d.block_q[blk * (B / 2) + j];
+        L.act[i] = L.q[i] >= 0 && d.sm[L.q[i]].run && d.sm[L.q[i]].dense;
+        L.s_node[i] = L.act[i] ? d.st[L.q[i]].s : -1;
+        L.t_node[i] = L.act[i] ? d.st[L.q[i]].t : -1;
+        L.all_act &= L.act[i];
+        L.vu[i] = L.cnt[i] = 0u;
     }
-    // per-lane epilogue accumulators
-    unsigned long long vp[QPL], vu[QPL], cnt[QPL];
-    double a1[QPL], a2[QPL], b1[QPL], b2[QPL];
 #pragma unroll
-    for (int i = 0; i < QPL; ++i) {
-        vp[i] = vu[i] = cnt[i] = 0;
-        a1[i] = a2[i] = b1[i] = b2[i] = 0.0;  // entries are >= 0; zeros are in the multiset
+    for (int e = 0; e < VEC; ++e) {
+        L.vol[e] = 0u;
+        L.m1[e] = L.m2[e] = T(0);  // entries are >= 0; zeros are in the multiset
     }
+    extern __shared__ __align__(16) unsigned char dense_smem[];
+    T* ring = reinterpret_cast<T*>(dense_smem + (threadIdx.x >> 5) * kRingBytes);
+    if (run == 1) run_units<T, VEC, true>(L, d, blk, lane, ring);
+    else run_units<T, VEC, false>(L, d, blk, lane, ring);
+
+    // one partial per warp and query
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r0 = warp * RPW; r0 < n; r0 += nwarps * RPW) {
-        const int64_t v = r0 + rsub;
-        const bool row_ok = v < n;
-        int64_t start = 0;
-        uint32_t deg = 0;
-        if (row_ok) {
-            if (d.g.node_info) {
-                const uint2 inf = __ldg(d.g.node_info + v);
-                start = inf.x;
-                deg = inf.y;
-            } else {
-                start = __ldg(d.g.row_ptr + v);
-                deg = (uint32_t)(__ldg(d.g.row_ptr + v + 1) - start);
-            }
-        }
-        V acc;
-        if constexpr (VEC == 4) acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        else acc = make_double2(0.0, 0.0);
-        uint32_t nib = 0;
-        // the rows of a warp may differ in degree: loop to the warp's largest
-        uint32_t dmax = deg;
-#pragma unroll
-        for (int o = LPR; o < 32; o <<= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-        for (uint32_t base = 0; base < dmax; base += LPR) {
-            const uint32_t e = base + sub;
-            const int32_t u_l = (row_ok && e < deg) ? __ldg(d.g.col_idx + start + e) : -1;
-            const uint32_t lim = deg > base ? min((uint32_t)LPR, deg - base) : 0u;
-#pragma unroll 4
-            for (uint32_t k = 0; k < (uint32_t)LPR; ++k) {
-                const int32_t u = __shfl_sync(0xffffffffu, u_l, (int)k, LPR);
-                if (k < lim) {
-                    const int64_t ru = boff + u;
-                    vadd<T>(acc, __ldg(reinterpret_cast<const V*>(Xc + ru * B) + sub));
-                    const uint32_t wd = __ldg(Sc + ru * WORDS + (sub * VEC) / 32);
-                    nib |= (wd >> ((sub * VEC) % 32)) & ((1u << VEC) - 1);
-                }
-            }
-        }
-        if (row_ok) {
-            const T dv = (T)deg;
-            V y;
-            if constexpr (VEC == 4) y = make_float4(acc.x / dv, acc.y / dv, acc.z / dv, acc.w / dv);
-            else y = make_double2(acc.x / dv, acc.y / dv);
-            const int64_t rv = boff + v;
-            V* dst = reinterpret_cast<V*>(Xn + rv * B) + sub;
-            // keep the frozen columns of queries that left SMM
-            bool all_act = true;
-#pragma unroll
-            for (int i = 0; i < QPL; ++i) all_act &= act[i];
-            if (all_act) {
-                *dst = y;
-            } else {
-#pragma unroll
-                for (int i = 0; i < QPL; ++i)
-                    if (act[i]) {
-                        T* p = Xn + rv * B + sub * VEC + 2 * i;
-                        p[0] = vget<T>(y, 2 * i);
-                        p[1] = vget<T>(y, 2 * i + 1);
-                    }
-            }
-#pragma unroll
-            for (int i = 0; i < QPL; ++i) {
-                if (!act[i]) continue;
-                const uint32_t bs = (nib >> (2 * i)) & 1u, bt = (nib >> (2 * i + 1)) & 1u;
-                const double ys = (double)vget<T>(y, 2 * i), yt = (double)vget<T>(y, 2 * i + 1);
-                vp[i] += (unsigned long long)deg * (bs + bt);
-                vu[i] += (unsigned long long)deg * (bs | bt);
-                cnt[i] += (bs | bt);
-                top2_push(a1[i], a2[i], ys);
-                top2_push(b1[i], b2[i], yt);
-                if (v == s_node[i]) {
-                    d.sm[qs[i]].sval[0] = ys;
-                    d.sm[qs[i]].sval[1] = yt;
-                }
-                if (v == t_node[i]) {
-                    d.sm[qs[i]].sval[2] = ys;
-                    d.sm[qs[i]].sval[3] = yt;
-                }
-            }
-        }
-        // support word(s) of the row: OR the lanes' nibbles
-        uint32_t wv = row_ok ? (nib << ((sub * VEC) % 32)) : 0u;
-        constexpr int LPW = 32 / VEC;  // lanes per support word
-#pragma unroll
-        for (int o = 1; o < LPW && o < LPR; o <<= 1) wv |= __shfl_xor_sync(0xffffffffu, wv, o);
-        if (row_ok && (sub % LPW) == 0) Sn[(boff + v) * WORDS + (sub * VEC) / 32] = wv;
-    }
-    // merge the row groups of the warp, then one partial per warp and query
-#pragma unroll
-    for (int i = 0; i < QPL; ++i) {
-#pragma unroll
-        for (int o = LPR; o < 32; o <<= 1) {
-            vp[i] += __shfl_xor_sync(0xffffffffu, vp[i], o);
-            vu[i] += __shfl_xor_sync(0xffffffffu, vu[i], o);
-            cnt[i] += __shfl_xor_sync(0xffffffffu, cnt[i], o);
-            top2_merge(a1[i], a2[i], __shfl_xor_sync(0xffffffffu, a1[i], o), __shfl_xor_sync(0xffffffffu, a2[i], o));
-            top2_merge(b1[i], b2[i], __shfl_xor_sync(0xffffffffu, b1[i], o), __shfl_xor_sync(0xffffffffu, b2[i], o));
-        }
-    }
-    (void)gmask;
-    if (rsub == 0) {
+    DensePartial* base = d.part + ((int64_t)blk * d.part_warps + warp) * (B / 2);
+    if constexpr (VEC >= 2) {
 #pragma unroll
         for (int i = 0; i < QPL; ++i) {
-            const int j = sub * QPL + i;
-            DensePartial* p = d.part + ((int64_t)blk * d.part_warps + warp) * (B / 2) + j;
-            p->vp = vp[i];
-            p->vu = vu[i];
-            p->cnt = cnt[i];
-            p->s1 = a1[i];
-            p->s2 = a2[i];
-            p->t1 = b1[i];
-            p->t2 = b2[i];
+            DensePartial* p = base + lane * QPL + i;
+            p->vp = (unsigned long long)L.vol[2 * i] + L.vol[2 * i + 1];
+            p->vu = L.vu[i];
+            p->cnt = L.cnt[i];
+            p->s1 = (double)L.m1[2 * i];
+            p->s2 = (double)L.m2[2 * i];
+            p->t1 = (double)L.m1[2 * i + 1];
+            p->t2 = (double)L.m2[2 * i + 1];
+        }
+    } else {
+        const uint32_t ovol = __shfl_xor_sync(kFull, L.vol[0], 1);
+        const T om1 = __shfl_xor_sync(kFull, L.m1[0], 1), om2 = __shfl_xor_sync(kFull, L.m2[0], 1);
+        if ((lane & 1) == 0) {
+            DensePartial* p = base + lane / 2;
+            p->vp = (unsigned long long)L.vol[0] + ovol;
+            p->vu = L.vu[0];
+            p->cnt = L.cnt[0];
+            p->s1 = (double)L.m1[0];
+            p->s2 = (double)L.m2[0];
+            p->t1 = (double)om1;
+            p->t2 = (double)om2;
         }
     }
 }
@@ -285,11 +504,11 @@ __global__ void __launch_bounds__(256) dense_reduce_kernel(DenseArgs d) {
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        vp += __shfl_xor_sync(0xffffffffu, vp, o);
-        vu += __shfl_xor_sync(0xffffffffu, vu, o);
-        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        top2_merge(a1, a2, __shfl_xor_sync(0xffffffffu, a1, o), __shfl_xor_sync(0xffffffffu, a2, o));
-        top2_merge(b1, b2, __shfl_xor_sync(0xffffffffu, b1, o), __shfl_xor_sync(0xffffffffu, b2, o));
+        vp += __shfl_xor_sync(kFull, vp, o);
+        vu += __shfl_xor_sync(kFull, vu, o);
+        cnt += __shfl_xor_sync(kFull, cnt, o);
+        top2_merge(a1, a2, __shfl_xor_sync(kFull, a1, o), __shfl_xor_sync(kFull, a2, o));
+        top2_merge(b1, b2, __shfl_xor_sync(kFull, b1, o), __shfl_xor_sync(kFull, b2, o));
     }
     if (lane == 0) {
         M->vol_paper = vp;
@@ -310,23 +529,74 @@ __global__ void dense_map_kernel(DenseArgs d, int64_t nq) {
         const_cast<int32_t*>(d.block_q)[k] = k < nq ? (int32_t)k : -1;
 }
 
-// Blocks with at least one query still in SMM.
+// Per block: 0 when no query is still in SMM, 1 when one is, 2 when, in
+// addition, every such query's support covers all n nodes after the last
+// iteration. Resets the blocks' unit counters.
 __global__ void dense_block_flags_kernel(DenseArgs d) {
     const int nq_block = d.width / 2;
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < d.nblocks; b += gridDim.x * blockDim.x) {
-        int any = 0;
+        int any = 0, partial = 0;
         for (int j = 0; j < nq_block; ++j) {
             const int q = d.block_q[b * nq_block + j];
-            if (q >= 0 && d.sm[q].run && d.sm[q].dense) any = 1;
+            if (q >= 0 && d.sm[q].run && d.sm[q].dense) {
+                any = 1;
+                if (d.sm[q].count < (unsigned long long)d.g.n) partial = 1;
+            }
         }
-        d.block_run[b] = any;
+        d.block_run[b] = any ? (partial ? 1 : 2) : 0;
+        d.unit_ctr[b] = 0u;
     }
 }
 
 // ---------------------------------------------------------------------------
-// launchers
+// host side
 // ---------------------------------------------------------------------------
-int dense_lanes_per_row(int width, bool fp64) { return width / (fp64 ? 2 : 4); }
+bool dense_width_ok(int width, bool fp64) {
+    return fp64 ? (width == 32 || width == 64) : (width == 32 || width == 64 || width == 128);
+}
+
+void build_dense_units(int64_t n, const int64_t* row_ptr, std::vector<int4>* units, std::vector<int4>* heavy,
+                       int32_t* nslots) {
+    units->clear();
+    heavy->clear();
+    std::vector<int32_t> big;
+    for (int64_t v = 0; v < n; ++v)
+        if (row_ptr[v + 1] - row_ptr[v] > kHeavyDeg) big.push_back((int32_t)v);
+    std::stable_sort(big.begin(), big.end(), [&](int32_t a, int32_t b) {
+        return row_ptr[a + 1] - row_ptr[a] > row_ptr[b + 1] - row_ptr[b];
+    });
+    int32_t slot = 0;
+    for (size_t h = 0; h < big.size(); ++h) {
+        const int32_t v = big[h];
+        const int64_t deg = row_ptr[v + 1] - row_ptr[v];
+        const int32_t np = (int32_t)((deg + kPieceEdges - 1) / kPieceEdges);
+        heavy->push_back(make_int4(v, slot, np, (int32_t)deg));
+        for (int32_t p = 0; p < np; ++p) {
+            const int64_t a = row_ptr[v] + (int64_t)p * kPieceEdges;
+            const int64_t b = std::min<int64_t>(a + kPieceEdges, row_ptr[v + 1]);
+            units->push_back(make_int4(-(int32_t)h - 1, p, (int32_t)(uint32_t)a, (int32_t)(uint32_t)b));
+        }
+        slot += np;
+    }
+    int64_t v = 0;
+    while (v < n) {
+        if (row_ptr[v + 1] - row_ptr[v] > kHeavyDeg) {
+            ++v;
+            continue;
+        }
+        const int64_t r0 = v;
+        int64_t edges = 0;
+        while (v < n && v - r0 < kUnitRows) {
+            const int64_t dv = row_ptr[v + 1] - row_ptr[v];
+            if (dv > kHeavyDeg || (v > r0 && edges + dv > kUnitEdges)) break;
+            edges += dv;
+            ++v;
+        }
+        units->push_back(
+            make_int4((int32_t)r0, (int32_t)v, (int32_t)(uint32_t)row_ptr[r0], (int32_t)(uint32_t)row_ptr[v]));
+    }
+    *nslots = slot;
+}
 
 void launch_dense_map(const DenseArgs& d, int64_t nq, cudaStream_t st) {
     const int64_t total = (int64_t)d.nblocks * (d.width / 2);
@@ -342,19 +612,38 @@ void launch_dense_init(bool fp64, const DenseArgs& d, cudaStream_t st) {
     note_launches(1);
 }
 
+constexpr int kSpmmSmem = 8 * kRingBytes;  // 8 warps per CTA
+
+template <typename T, int VEC>
+static void launch_spmm(const DenseArgs& d, cudaStream_t st) {
+    dense_spmm_kernel<T, VEC><<<dim3(d.part_warps / 8, d.nblocks), 256, kSpmmSmem, st>>>(d);
+}
+
+// Opt the SpMM kernels into their shared-memory rings (current device;
+// called before any launch, outside stream capture).
+int dense_prepare() {
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void* f) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kSpmmSmem);
+    };
+    set((const void*)dense_spmm_kernel<float, 1>);
+    set((const void*)dense_spmm_kernel<float, 2>);
+    set((const void*)dense_spmm_kernel<float, 4>);
+    set((const void*)dense_spmm_kernel<double, 1>);
+    set((const void*)dense_spmm_kernel<double, 2>);
+    return (int)e;
+}
+
 void launch_dense_iteration(bool fp64, const DenseArgs& d, cudaStream_t st) {
     dense_block_flags_kernel<<<1, 256, 0, st>>>(d);
-    const dim3 grid(d.part_warps / 8, d.nblocks);
     prof_begin(FAM_DENSE_SPMM, st);
-    const int lpr = dense_lanes_per_row(d.width, fp64);
     if (fp64) {
-        if (lpr == 32) dense_spmm_kernel<double, 32><<<grid, 256, 0, st>>>(d);
-        else if (lpr == 16) dense_spmm_kernel<double, 16><<<grid, 256, 0, st>>>(d);
-        else dense_spmm_kernel<double, 8><<<grid, 256, 0, st>>>(d);
+        if (d.width == 64) launch_spmm<double, 2>(d, st);
+        else launch_spmm<double, 1>(d, st);
     } else {
-        if (lpr == 32) dense_spmm_kernel<float, 32><<<grid, 256, 0, st>>>(d);
-        else if (lpr == 16) dense_spmm_kernel<float, 16><<<grid, 256, 0, st>>>(d);
-        else dense_spmm_kernel<float, 8><<<grid, 256, 0, st>>>(d);
+        if (d.width == 128) launch_spmm<float, 4>(d, st);
+        else if (d.width == 64) launch_spmm<float, 2>(d, st);
+        else launch_spmm<float, 1>(d, st);
     }
     prof_end(FAM_DENSE_SPMM, st);
     const int64_t total = (int64_t)d.nblocks * (d.width / 2);

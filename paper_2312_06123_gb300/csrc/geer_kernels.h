@@ -2,6 +2,8 @@
 // CUDA library (internal).
 #pragma once
 
+#include <vector>
+
 #include "geer_internal.cuh"
 
 namespace geer {
@@ -50,15 +52,23 @@ struct DenseArgs {
     DevGraph g;
     int32_t nblocks;
     int32_t width;          // columns per block (B)
-    void* X[2];             // values, nblocks * n * width each
-    uint32_t* S[2];         // support bits, nblocks * n * max(width / 32, 1) words each
+    void* X[2];             // values (sign bit: support), nblocks * n * width each
     const int32_t* block_q; // nblocks * width/2: query of each column pair, -1: none
-    int32_t* block_run;     // per block: any query still iterating
+    int32_t* block_run;     // per block: 0 idle, 1 running, 2 running with full supports
     QState* st;
     QSmm* sm;
     DensePartial* part;     // nblocks * part_warps * width/2
     int32_t part_warps;     // warps of the SpMM grid per block (grid.x = part_warps / 8)
     SmmCtl* ctl;
+    // balanced work units of the graph (built once per graph)
+    const int4* units;      // light: {first row, end row, first edge, end edge}; heavy piece: {-h-1, piece, edges}
+    int32_t nunits;
+    const int4* heavy;      // per heavy row h: {row, first piece slot, pieces, degree}
+    int32_t nheavy;
+    int32_t nslots;         // piece slots per block
+    unsigned int* unit_ctr; // per block: next unit
+    unsigned int* heavy_ctr;// per block and heavy row: pieces done (reset by the finishing warp)
+    void* pieces;           // per block: nslots * width partial sums
 };
 
 struct AmcArgs {
@@ -97,7 +107,10 @@ void launch_smm_advance(const SmmArgs& a, cudaGraphConditionalHandle h, bool use
 void launch_smm_start(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 void launch_smm_iteration(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 // the dense engine: iteration 0 and one pull-SpMM iteration (+ its epilogue)
-int dense_lanes_per_row(int width, bool fp64);
+bool dense_width_ok(int width, bool fp64);
+int dense_prepare();  // cudaError_t of the shared-memory opt-in
+void build_dense_units(int64_t n, const int64_t* row_ptr, std::vector<int4>* units, std::vector<int4>* heavy,
+                       int32_t* nslots);
 void launch_dense_map(const DenseArgs& d, int64_t nq, cudaStream_t st);
 void launch_dense_init(bool fp64, const DenseArgs& d, cudaStream_t st);
 void launch_dense_iteration(bool fp64, const DenseArgs& d, cudaStream_t st);

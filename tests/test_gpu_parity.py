@@ -186,7 +186,7 @@ def test_peng_ell(c1):
 # dense engine (pull SpMM over blocks of query vectors)
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("prec,rel,width", [(geer.GER_FP64, 1e-9, 64), (geer.GER_FP64, 1e-9, 16),
+@pytest.mark.parametrize("prec,rel,width", [(geer.GER_FP64, 1e-9, 64), (geer.GER_FP64, 1e-9, 32),
                                             (geer.GER_FP32, 1e-5, 128), (geer.GER_FP32, 1e-5, 32)])
 def test_dense_engine_standalone_smm(c1, prec, rel, width):
     # standalone SMM (l_b = l) on the dense engine equals the truncated series
