@@ -31,6 +31,9 @@ os.environ.setdefault("GEER_SYNTH_CACHE", "/tmp/geer_synth_cache")
 
 METRIC = "ER queries/s at eps=0.05 (batched FP32 GEER)"
 WALK_STEP_BYTES = 20  # row_ptr pair 8 B + one col_idx 4 B + one (s*, t*) FP32 pair 8 B
+# DRAM bytes (read + write) per dense_spmm launch from the ncu capture of the
+# current kernel on this workload (profiles/dense_spmm_c2_w128.md), per width.
+SPMM_TRAFFIC: dict = {}
 
 
 def _peaks():
@@ -139,6 +142,51 @@ def run_reference(args, world, rank):
             "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def spmm_leg(G, w, geer, peak, nq=64, width=128, lb=10, reps=3):
+    """Dense pull SpMM (the SMM step as a block SpMM, FP32, B = width columns
+    = width/2 queries) on the bench graph: standalone SMM for `lb` iterations
+    of `nq` pairs of the workload whose l >= lb, timed per launch with CUDA
+    events on the launching stream (host-driven loop, no graph capture)."""
+    g = w.graph
+    r, st = G.query(w.s, w.t, w.eps, geer.default_options(), stats=True)
+    sel = np.nonzero(st["ell"] >= lb)[0][:nq]
+    if len(sel) < nq:
+        return None
+    o = geer.default_options(precision=geer.GER_FP32, switch_policy=geer.GER_SWITCH_FIXED, fixed_ell_b=lb,
+                             smm_engine=geer.GER_ENGINE_DENSE, dense_width=width)
+    old = os.environ.get("GEER_NO_GRAPH")
+    os.environ["GEER_NO_GRAPH"] = "1"
+    try:
+        G.query(w.s[sel], w.t[sel], w.eps[sel], o)
+        geer.profile_enable(True)
+        for _ in range(reps):
+            G.query(w.s[sel], w.t[sel], w.eps[sel], o)
+        prof = geer.profile_read()
+        geer.profile_enable(False)
+    finally:
+        if old is None:
+            del os.environ["GEER_NO_GRAPH"]
+        else:
+            os.environ["GEER_NO_GRAPH"] = old
+    nl, tms = prof["dense_spmm"]
+    nnz = int(g.row_ptr[-1])
+    nblocks = max(nq * 2 // width, 1)
+    # algorithmic bytes per launch: col_idx, row_ptr, X read once, Y written once
+    alg = nblocks * (4 * nnz + 4 * (g.n + 1) + 2 * 4 * g.n * width)
+    per = tms / nl / 1000.0
+    out = {"kernel": "dense_spmm", "workload": f"{nq} pairs (l >= {lb}) of the bench workload, FP32 block of "
+                                               f"{width} columns, {lb} SMM iterations (standalone SMM)",
+           "launches": nl, "ms_per_launch": per * 1000.0, "algorithmic_bytes_per_launch": alg,
+           "achieved": alg / per / 1e9, "peak": peak, "unit": "GB/s", "frac": alg / per / 1e9 / peak,
+           "us_per_query_iteration": per * 1e6 / nq}
+    tr = SPMM_TRAFFIC.get(width)
+    if tr is not None:
+        out["traffic"] = tr
+        out["dram_gbs"] = tr / per / 1e9
+        out["dram_frac"] = tr / per / 1e9 / peak
+    return out
 
 
 def _config(w):
@@ -280,6 +328,7 @@ def main():
         nl, tms = fam[1]
         roof = {"kernel": fam[0], "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s",
                 "frac": None, "peak_source": peak_kind, "traffic": None}
+    spmm = None if args.no_extras else spmm_leg(G, w, geer, peak)
     # CPU baseline: the oracle as it stands, one host thread, bounded sample
     cpu = None
     if not args.no_extras:
@@ -293,6 +342,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": _config(w),
         "roofline": roof,
+        "spmm": spmm,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": int(w.q * (4 + 4 + 8)),
                 "d2h_bytes_per_step": int(w.q * 8)},

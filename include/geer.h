@@ -50,6 +50,7 @@ extern "C" {
 
 /* switch policy between SMM and AMC */
 #define GER_SWITCH_RULE  0  /* Eq. (17): stop SMM once the support volume exceeds h(l - l_b) */
+#define GER_SWITCH_MLP   1  /* the learned switch installed by ger_set_switch_mlp; Eq. (17) if none */
 #define GER_SWITCH_FIXED 2  /* run exactly min(fixed_ell_b, l) SMM iterations; fixed_ell_b < 0 means l */
 
 /* engine of the SMM iterations */
@@ -67,7 +68,7 @@ typedef struct ger_options {
     int32_t  tau;           /* maximum number of AMC batches tau (paper default 5), 1..20 */
     int32_t  precision;     /* GER_FP32 (default) or GER_FP64 */
     int32_t  per_query;     /* 0: all queries of the batch together; 1: one query at a time */
-    int32_t  switch_policy; /* GER_SWITCH_RULE (default) or GER_SWITCH_FIXED */
+    int32_t  switch_policy; /* GER_SWITCH_RULE (default), GER_SWITCH_MLP or GER_SWITCH_FIXED */
     int32_t  fixed_ell_b;   /* used by GER_SWITCH_FIXED */
     int32_t  ell_formula;   /* GER_ELL_REFINED (default) or GER_ELL_PENG */
     uint64_t seed;          /* walk RNG seed */
@@ -204,6 +205,78 @@ int ger_profile_enable(int on);
 /* Copy up to max_entries family records into out; returns the number of
    families with at least one timed launch (>= 0), or GER_ERR_INVALID. */
 int ger_profile_read(ger_kernel_profile *out, int max_entries);
+
+/* ------------------------------------------------------------------------
+ * The learned SMM -> AMC switch (no counterpart in the paper; it replaces
+ * the cost comparison of Eq. (17), Section 4.3, by a small network; the
+ * truncation length l of Eq. (6) is unchanged, so Theorem 2's eps guarantee
+ * holds whatever it decides).
+ *
+ * Network: 6 -> 64 -> 64 -> 1, ReLU, FP16 weights (IEEE binary16 bit
+ * patterns), FP32 arithmetic. Parameter order, GER_MLP_PARAMS values:
+ * W1[64][6], b1[64], W2[64][64] (W2[j][k] multiplies hidden unit k of the
+ * first layer), b2[64], W3[64], b3. Inputs after SMM iteration l_b, each
+ * normalised as (f - mean) / std: log d(s), log d(t), l - l_b,
+ * log(Eq. 17's volume), log h(l - l_b), max_1(s*)/d(s) + max_1(t*)/d(t).
+ * Output: predicted log C(l_b + 1) - log C(l_b), C(j) being the query's
+ * cost when it switches after j iterations; the query switches when the
+ * output is >= 0 (and always once l_b = l).
+ * ------------------------------------------------------------------------ */
+#define GER_MLP_INPUTS 6
+#define GER_MLP_HIDDEN 64
+#define GER_MLP_PARAMS 4673
+#define GER_LOG_WIDTH  8   /* columns of one cost-log row, see ger_smm_trace */
+
+/* Install (weights != NULL) or remove (weights == NULL) the learned switch
+ * of graph g. norm = {mean[6], std[6]} (std > 0), weights = GER_MLP_PARAMS
+ * FP16 values; both are copied. Queries with switch_policy GER_SWITCH_MLP use
+ * it from the next call on.
+ * Errors: GER_ERR_INVALID, GER_ERR_OOM, GER_ERR_CUDA. */
+int ger_set_switch_mlp(ger_graph *g, const float *norm, const uint16_t *weights);
+
+/* Cost log of the learned switch: runs the batch with min(max_steps, l)
+ * SMM iterations (GER_SWITCH_FIXED; the other options are used as given)
+ * and writes, for query i and iteration j = 1..ell_b(i),
+ * log_out[(i * max_steps + j - 1) * GER_LOG_WIDTH + k] =
+ *   k = 0..5: the six raw (unnormalised) network inputs after iteration j,
+ *   k = 6:    sum of d(v) over V_s u V_t after iteration j (the size of the
+ *             push that computes iteration j + 1),
+ *   k = 7:    Eq. (17)'s volume after iteration j.
+ * Rows past ell_b(i) are zero. stats (nullable) as for ger_query_batch.
+ * Host pointers. Errors: as ger_query_batch_eps; GER_ERR_INVALID for
+ * max_steps outside 1..4096. */
+int ger_smm_trace(ger_graph *g, int64_t q, const int32_t *s, const int32_t *t, const double *eps,
+                  const ger_options *opt, int32_t max_steps, float *log_out, ger_query_stats *stats);
+
+/* Network output for `rows` normalised input rows x[rows][6] (host
+ * pointers), on the current device. Errors: GER_ERR_INVALID, GER_ERR_OOM,
+ * GER_ERR_CUDA. */
+int ger_mlp_forward(int64_t rows, const float *x, const uint16_t *weights, float *y);
+
+/* Gradient of L = (1/rows) sum_i (y_i - target_i)^2 with respect to the
+ * GER_MLP_PARAMS parameters (FP32, same order), and L (nullable), at the
+ * given FP16 weights. Host pointers; current device. */
+int ger_mlp_gradient(int64_t rows, const float *x, const float *target, const uint16_t *weights, float *grad,
+                     float *loss);
+
+typedef struct ger_mlp_train_options {
+    int32_t  epochs;     /* passes over the rows (default 60) */
+    int32_t  batch;      /* rows per Adam step (default 1024) */
+    float    lr;         /* Adam step size (default 2e-3) */
+    float    beta1, beta2, adam_eps;  /* Adam moments (0.9, 0.999, 1e-8) */
+    uint64_t seed;       /* row shuffling */
+} ger_mlp_train_options;
+
+void ger_default_mlp_train_options(ger_mlp_train_options *o);
+
+/* Train the network on the GPU (current device): minibatch Adam on FP32
+ * master weights, FP16 weights in every forward and backward pass, the
+ * mean squared error of the rows x[rows][6] (normalised) against target.
+ * weights: initial values in, trained values out (FP16). loss_per_epoch
+ * (nullable, epochs entries): mean loss over each epoch's minibatches before
+ * their updates. Errors: GER_ERR_INVALID, GER_ERR_OOM, GER_ERR_CUDA. */
+int ger_mlp_train(int64_t rows, const float *x, const float *target, const ger_mlp_train_options *o,
+                  uint16_t *weights, float *loss_per_epoch);
 
 #ifdef __cplusplus
 }

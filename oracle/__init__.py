@@ -225,7 +225,7 @@ def geer(g, s, t, eps, lam, delta=0.01, tau=5, seed=3, q_index=0, forced_ell_b=-
     o = _GeerOut()
     tr = None
     if trace:
-        cap = 4 * (max(ell(g.degrees()[s], g.degrees()[t], eps, lam), forced_ell_b, 0) + 2)
+        cap = 6 * (max(ell(g.degrees()[s], g.degrees()[t], eps, lam), forced_ell_b, 0) + 2)
         tr = np.zeros(cap)
     rc = lib().og_geer(g.n, _ptr(rp), _ptr(ci), int(s), int(t), float(eps), float(delta),
                        int(tau), int(seed), float(lam), int(q_index), int(forced_ell_b),
@@ -236,7 +236,7 @@ def geer(g, s, t, eps, lam, delta=0.01, tau=5, seed=3, q_index=0, forced_ell_b=-
     res = GeerResult(o.r, o.r_b, o.r_f, o.ell, o.ell_b, o.free_ell_b, o.volume, o.h,
                      _amc_result(o.amc))
     if tr is not None:
-        res.trace = tr[:4 * o.ell_b].reshape(-1, 4)
+        res.trace = tr[:6 * o.ell_b].reshape(-1, 6)
     return res
 
 

@@ -349,8 +349,11 @@ typedef struct {
 } og_geer_out;
 
 /* forced_ell_b < 0: free-running switch (Eq. (17) or l_b >= l).
-   trace (nullable) receives, per SMM iteration i = 1..l_b, the 4-tuple
-   (r_b after i, volume, h(l - i), psi(l - i)) at trace[4(i-1) ..]. */
+   trace (nullable) receives, per SMM iteration i = 1..l_b, the 6-tuple
+   (r_b after i, volume, h(l - i), psi(l - i), max_1(s*)/d(s) + max_1(t*)/d(t),
+   volume of the union V_s u V_t) at trace[6(i-1) ..]: Eq. (17)'s quantities,
+   Eq. (9)'s leading term and the next push's size (the learned switch's
+   features and cost). */
 int og_geer(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
             int32_t s, int32_t t, double eps, double delta, int tau, uint64_t seed,
             double lambda, int64_t q_index, int64_t forced_ell_b, int64_t forced_eta0,
@@ -403,12 +406,16 @@ int og_geer(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
             if (vs[v]) vol += d;
             if (vt[v]) vol += d;
         }
+        double vol_union = 0.0;
+        for (int64_t v = 0; v < n; ++v)
+            if (vs[v] || vt[v])
+                vol_union += (double)(row_ptr[v + 1] - row_ptr[v]);
         int64_t lf = ell - lb;
         double psi = 0.0, h = 0.0;
+        double s1, s2, t1, t2;
+        og_top2(n, xs, &s1, &s2);
+        og_top2(n, xt, &t1, &t2);
         if (lf > 0) {
-            double s1, s2, t1, t2;
-            og_top2(n, xs, &s1, &s2);
-            og_top2(n, xt, &t1, &t2);
             psi = og_psi(lf, s1, s2, t1, t2, ds, dt);
             int64_t eta = (int64_t)ceil(og_eta_star(psi, eps, delta, (double)tau) / ldexp(1.0, tau - 1));
             if (eta < 1)
@@ -418,10 +425,12 @@ int og_geer(int64_t n, const int64_t *row_ptr, const int32_t *col_idx,
         o->volume = vol;
         o->h = h;
         if (trace) {
-            trace[4 * (lb - 1) + 0] = rb;
-            trace[4 * (lb - 1) + 1] = vol;
-            trace[4 * (lb - 1) + 2] = h;
-            trace[4 * (lb - 1) + 3] = psi;
+            trace[6 * (lb - 1) + 0] = rb;
+            trace[6 * (lb - 1) + 1] = vol;
+            trace[6 * (lb - 1) + 2] = h;
+            trace[6 * (lb - 1) + 3] = psi;
+            trace[6 * (lb - 1) + 4] = s1 / ds + t1 / dt;
+            trace[6 * (lb - 1) + 5] = vol_union;
         }
         int free_stop = (vol > h) || (lb >= ell);
         if (free_stop && o->free_ell_b == 0)

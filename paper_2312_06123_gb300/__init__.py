@@ -22,7 +22,9 @@ GER_ERR = {
     -9: "GER_ERR_CAPACITY", -10: "GER_ERR_NO_LAMBDA",
 }
 GER_FP64, GER_FP32 = 0, 1
-GER_SWITCH_RULE, GER_SWITCH_FIXED = 0, 2
+GER_SWITCH_RULE, GER_SWITCH_MLP, GER_SWITCH_FIXED = 0, 1, 2
+MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 6, 64, 4673
+LOG_WIDTH = 8
 GER_ELL_REFINED, GER_ELL_PENG = 0, 1
 GER_ENGINE_SPARSE, GER_ENGINE_DENSE = 0, 1
 
@@ -47,6 +49,12 @@ class QueryStats(ctypes.Structure):
                 ("walk_steps", ctypes.c_int64), ("r_b", ctypes.c_double), ("r_f", ctypes.c_double),
                 ("psi", ctypes.c_double), ("f_last", ctypes.c_double), ("volume", ctypes.c_double),
                 ("h", ctypes.c_double), ("checksum", ctypes.c_uint64)]
+
+
+class MlpTrainOptions(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_int32), ("batch", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("adam_eps", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
 
 
 class KernelProfile(ctypes.Structure):
@@ -95,9 +103,17 @@ def load_library(build_if_missing: bool = True):
     L.ger_profile_enable.restype = ctypes.c_int
     L.ger_profile_read.argtypes = [ctypes.POINTER(KernelProfile), ctypes.c_int]
     L.ger_profile_read.restype = ctypes.c_int
+    L.ger_set_switch_mlp.argtypes = [_P, _P, _P]
+    L.ger_smm_trace.argtypes = [_P, i64, _P, _P, _P, ctypes.POINTER(Options), i32, _P, _P]
+    L.ger_mlp_forward.argtypes = [i64, _P, _P, _P]
+    L.ger_mlp_gradient.argtypes = [i64, _P, _P, _P, _P, _P]
+    L.ger_default_mlp_train_options.argtypes = [ctypes.POINTER(MlpTrainOptions)]
+    L.ger_default_mlp_train_options.restype = None
+    L.ger_mlp_train.argtypes = [i64, _P, _P, ctypes.POINTER(MlpTrainOptions), _P, _P]
     for name in ("ger_load_csr", "ger_graph_size", "ger_spectral_bound", "ger_set_spectral_bound",
                  "ger_query_batch", "ger_query_batch_eps", "ger_query_batch_dev",
-                 "ger_query_batch_dev_noalloc"):
+                 "ger_query_batch_dev_noalloc", "ger_set_switch_mlp", "ger_smm_trace", "ger_mlp_forward",
+                 "ger_mlp_gradient", "ger_mlp_train"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -129,15 +145,73 @@ def profile_enable(on: bool = True):
 
 def profile_read() -> dict:
     """{family: (launches, total_ms)} since the last profile_enable(True)."""
-    buf = (KernelProfile * 16)()
-    k = load_library().ger_profile_read(buf, 16)
+    buf = (KernelProfile * 32)()
+    k = load_library().ger_profile_read(buf, 32)
     if k < 0:
         _check(k)
-    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(k, 16))}
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(min(k, 32))}
 
 
 def _arr(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _fp16_bits(w) -> np.ndarray:
+    """FP16 weights as their IEEE binary16 bit patterns (uint16)."""
+    w = np.asarray(w)
+    if w.dtype == np.uint16:
+        out = np.ascontiguousarray(w)
+    else:
+        out = np.ascontiguousarray(w, dtype=np.float16).view(np.uint16)
+    if out.shape != (MLP_PARAMS,):
+        raise ValueError(f"expected {MLP_PARAMS} weights")
+    return out
+
+
+def mlp_forward(x, weights) -> np.ndarray:
+    """Network outputs for normalised inputs x[rows][6] (GPU kernel)."""
+    x = _arr(x, np.float32).reshape(-1, MLP_INPUTS)
+    w = _fp16_bits(weights)
+    y = np.zeros(x.shape[0], dtype=np.float32)
+    _check(load_library().ger_mlp_forward(x.shape[0], x.ctypes.data_as(_P), w.ctypes.data_as(_P),
+                                          y.ctypes.data_as(_P)))
+    return y
+
+
+def mlp_gradient(x, target, weights):
+    """(gradient over the MLP_PARAMS parameters, loss) of the mean squared
+    error, computed by the GPU backward kernels."""
+    x = _arr(x, np.float32).reshape(-1, MLP_INPUTS)
+    t = _arr(target, np.float32)
+    w = _fp16_bits(weights)
+    g = np.zeros(MLP_PARAMS, dtype=np.float32)
+    loss = ctypes.c_float()
+    _check(load_library().ger_mlp_gradient(x.shape[0], x.ctypes.data_as(_P), t.ctypes.data_as(_P),
+                                           w.ctypes.data_as(_P), g.ctypes.data_as(_P), ctypes.byref(loss)))
+    return g, float(loss.value)
+
+
+def mlp_train_options(**kw) -> MlpTrainOptions:
+    o = MlpTrainOptions()
+    load_library().ger_default_mlp_train_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def mlp_train(x, target, weights, options: MlpTrainOptions | None = None):
+    """Train on the GPU (Adam, FP16 weights in the passes); returns
+    (trained FP16 weights as uint16 bits, per-epoch loss)."""
+    x = _arr(x, np.float32).reshape(-1, MLP_INPUTS)
+    t = _arr(target, np.float32)
+    w = _fp16_bits(weights).copy()
+    o = options if options is not None else mlp_train_options()
+    loss = np.zeros(max(o.epochs, 1), dtype=np.float32)
+    _check(load_library().ger_mlp_train(x.shape[0], x.ctypes.data_as(_P), t.ctypes.data_as(_P), ctypes.byref(o),
+                                        w.ctypes.data_as(_P), loss.ctypes.data_as(_P)))
+    return w, loss[:o.epochs]
 
 
 class Graph:
@@ -204,6 +278,32 @@ class Graph:
                                        e.ctypes.data_as(_P), ctypes.byref(opt), r.ctypes.data_as(_P), sp)
         _check(rc)
         return (r, st) if stats else r
+
+    def set_switch_mlp(self, norm, weights):
+        """Install the learned switch: norm = (mean[6], std[6]) of the raw
+        inputs, FP16 weights; None removes it."""
+        L = load_library()
+        if weights is None:
+            _check(L.ger_set_switch_mlp(self._h, None, None))
+            return
+        nv = _arr(norm, np.float32).reshape(2 * MLP_INPUTS)
+        w = _fp16_bits(weights)
+        _check(L.ger_set_switch_mlp(self._h, nv.ctypes.data_as(_P), w.ctypes.data_as(_P)))
+
+    def smm_trace(self, s, t, eps, options: Options | None = None, max_steps: int = 16):
+        """Cost log: (log[q][max_steps][LOG_WIDTH], stats) of a batch run
+        with min(max_steps, l) SMM iterations; see ger_smm_trace."""
+        s = _arr(s, np.int32)
+        t = _arr(t, np.int32)
+        q = s.shape[0]
+        e = _arr(np.broadcast_to(eps, (q,)), np.float64)
+        log = np.zeros((q, max_steps, LOG_WIDTH), dtype=np.float32)
+        st = np.zeros(q, dtype=STATS_DTYPE)
+        opt = options if options is not None else default_options()
+        _check(load_library().ger_smm_trace(self._h, q, s.ctypes.data_as(_P), t.ctypes.data_as(_P),
+                                            e.ctypes.data_as(_P), ctypes.byref(opt), int(max_steps),
+                                            log.ctypes.data_as(_P), st.ctypes.data_as(_P)))
+        return log, st
 
     def query_dev(self, s_dev, t_dev, eps_dev, r_dev, stats_dev=None, options: Options | None = None,
                   stream=None):

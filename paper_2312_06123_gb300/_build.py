@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgeer.so")
-SOURCES = ["api.cu", "smm_batch.cu", "dense.cu", "amc.cu", "lanczos.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "smm_batch.cu", "dense.cu", "amc.cu", "lanczos.cu", "noalloc.cu", "mlp.cu"]
 HEADERS = ["geer_internal.cuh", "geer_kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -19,10 +19,12 @@
 namespace geer {
 
 static std::atomic<int64_t> g_launches{0};
-static bool g_capturing = false;  // graph capture: launches are counted per replay instead
+static bool g_capturing = false;    // graph capture: launches are counted per replay instead
+static int64_t g_captured = 0;      // kernels captured so far
 constexpr int64_t kHeavyCap = 1 << 16;
 void note_launches(int k) {
-    if (!g_capturing) g_launches.fetch_add(k, std::memory_order_relaxed);
+    if (g_capturing) g_captured += k;
+    else g_launches.fetch_add(k, std::memory_order_relaxed);
 }
 
 // ---------------------------------------------------------------------------
@@ -30,7 +32,8 @@ void note_launches(int k) {
 // ---------------------------------------------------------------------------
 static const char* kFamilyNames[] = {"smm_setup", "smm_alloc", "smm_clear", "smm_push",
                                               "smm_push_heavy", "smm_finish", "smm_top2", "smm_decide", "dense_spmm",
-                                              "amc_schedule", "amc_walk", "amc_reduce", "finalize", "lanczos"};
+                                              "amc_schedule", "amc_walk", "amc_reduce", "finalize", "lanczos",
+                                     "smm_mlp", "mlp_train"};
 static_assert(sizeof(kFamilyNames) / sizeof(kFamilyNames[0]) == FAM_COUNT, "one name per kernel family");
 struct ProfRec {
     int fam;
@@ -180,7 +183,9 @@ struct BatchGraph {
     const void* dense = nullptr;
     int dense_w = 0;
     bool prof = false;
-    int64_t launches = 0;  // kernels outside the while body
+    int64_t launches = 0;       // kernels outside the while body
+    int64_t body_launches = 0;  // kernels per pass of the while body
+    bool mlp = false;           // captured with the learned switch's kernel
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<ProfRec> prof_recs;
@@ -204,6 +209,8 @@ struct ger_graph {
     int4* dense_heavy = nullptr;     // dense SpMM heavy rows
     int32_t dense_nunits = 0, dense_nheavy = 0, dense_nslots = 0;
     bool dense_ready = false;        // SpMM kernels opted into their shared memory
+    unsigned short* mlp_w = nullptr; // learned switch: FP16 weights (null: none installed)
+    float* mlp_norm = nullptr;       // learned switch: input mean[6], std[6]
     geer::Workspace ws;
     geer::BatchGraph bg;
 };
@@ -381,6 +388,8 @@ struct Plan {
     double* r;            // device
     ger_query_stats* stats;  // device, nullable
     cudaStream_t st;
+    float* trace = nullptr;  // device cost log (stream-ordered runs only), nullable
+    int32_t trace_steps = 0;
 };
 
 
@@ -570,6 +579,10 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
     a.dense_X[1] = w.dX[1];
     a.ctl = w.ctl;
     a.err_flag = w.counters + 1;
+    a.mlp_norm = g->mlp_norm;
+    a.mlp_w = p.o.switch_policy == GER_SWITCH_MLP ? g->mlp_w : nullptr;
+    a.trace = p.trace ? p.trace + q0 * (int64_t)p.trace_steps * kTraceWidth : nullptr;
+    a.trace_steps = p.trace_steps;
     AmcArgs& m = *pm;
     m.g = dg;
     m.nq = (int32_t)nq;
@@ -624,7 +637,6 @@ static int run_queries(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool
         launch_smm_start(fp64, a, grid, p.st);
     }
     launch_smm_advance(a, 0, false, p.st);
-    note_launches(8);
     int32_t* n_want = reinterpret_cast<int32_t*>(w.host_rb + 2);
     for (int iter = 1; iter < 100000; ++iter) {
         GER_CUDA(cudaMemcpyAsync(n_want, &w.ctl->n_want, sizeof(int32_t), cudaMemcpyDeviceToHost, p.st));
@@ -638,7 +650,6 @@ static int run_queries(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool
             launch_smm_iteration(fp64, a, grid, p.st);
         }
         launch_smm_advance(a, 0, false, p.st);
-        note_launches(8);
     }
     issue_amc(g, m, nq, p.st);
     return GER_OK;
@@ -657,7 +668,8 @@ static void destroy_graph(BatchGraph& bg) {
 static bool same_key(const BatchGraph& bg, const Plan& p, bool fp64, const ger_graph* g) {
     return bg.valid && bg.nq == p.q && bg.fp64 == fp64 && std::memcmp(&bg.o, &p.o, sizeof(ger_options)) == 0 &&
            bg.lambda == g->lambda && bg.pool == g->ws.ent && bg.state == g->ws.st && bg.prof == g_prof_on &&
-           bg.dense == g->ws.dX[0] && bg.dense_w == (p.o.smm_engine ? dense_width_for(const_cast<ger_graph*>(g), p.o) : 0);
+           bg.dense == g->ws.dX[0] && bg.dense_w == (p.o.smm_engine ? dense_width_for(const_cast<ger_graph*>(g), p.o) : 0) &&
+           bg.mlp == (g->mlp_w != nullptr);
 }
 
 // Capture the whole batch as one graph: the initial SMM iteration, a
@@ -694,6 +706,8 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
     }
     g_prof_sink = &bg.prof_recs;
     g_capturing = true;
+    g_captured = 0;
+    int64_t body_launches = 0;
     e = cudaStreamBeginCaptureToGraph(st, graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
         cudaMemsetAsync(w.counters, 0, 4 * sizeof(int), st);
@@ -728,6 +742,7 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
             e = cudaStreamBeginCaptureToGraph(st2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
             if (e == cudaSuccess) {
                 g_prof_suspend = true;  // no event records inside a conditional body
+                const int64_t before = g_captured;
                 if (dense) {
                     launch_smm_alloc(a, st2);
                     launch_dense_iteration(fp64, d, st2);
@@ -736,6 +751,8 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
                     launch_smm_iteration(fp64, a, grid, st2);
                 }
                 launch_smm_advance(a, handle, true, st2);
+                body_launches = g_captured - before;
+                g_captured = before;
                 g_prof_suspend = false;
                 e = cudaStreamEndCapture(st2, &body);
             }
@@ -746,6 +763,7 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
             prof_begin(FAM_FINALIZE, st);
             finalize_kernel<<<fg, 256, 0, st>>>(w.st, p.q, p.r, p.stats);
             prof_end(FAM_FINALIZE, st);
+            note_launches(1);
         }
         cudaGraph_t done = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(st, &done);
@@ -770,7 +788,9 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
     bg.dense = w.dX[0];
     bg.dense_w = dense ? a.dense_width : 0;
     bg.prof = g_prof_on;
-    bg.launches = 8 + 1 + 2 * p.o.tau + 1;
+    bg.launches = g_captured;  // kernels outside the while body, once per replay
+    bg.body_launches = body_launches;
+    bg.mlp = g->mlp_w != nullptr;
     return GER_OK;
 }
 
@@ -789,7 +809,7 @@ static int run_batch(ger_graph* g, Plan& p) {
     if (rc) return rc;
     const bool per_query = p.o.per_query != 0;
     const bool fp64 = p.o.precision == GER_FP64;
-    const bool use_graph = !per_query && graphs_enabled();
+    const bool use_graph = !per_query && !p.trace && graphs_enabled();
     int64_t pool = std::max<int64_t>(g->ws.pool_cap, (int64_t)1 << 22);
     for (int attempt = 0; attempt < 6; ++attempt) {
         rc = ensure_ws(g, p.q, pool);
@@ -828,9 +848,9 @@ static int run_batch(ger_graph* g, Plan& p) {
         GER_CUDA(cudaStreamSynchronize(p.st));
         if (use_graph) {
             prof_collect_graph(g->bg.prof_recs);
-            // the while body ran iter - 1 times, 8 kernels each
+            // the while body ran iter - 1 times
             const int32_t iters = *reinterpret_cast<int32_t*>(w.host_rb + 3);
-            if (iters > 1) note_launches(8 * (iters - 1));
+            if (iters > 1) note_launches((int)(g->bg.body_launches * (iters - 1)));
         }
         prof_collect();
         const int derr = (int)(reinterpret_cast<int*>(w.host_rb)[0]);
@@ -996,6 +1016,8 @@ void ger_free(ger_graph* g) {
     cudaFree(g->node_info);
     cudaFree(g->dense_units);
     cudaFree(g->dense_heavy);
+    cudaFree(g->mlp_w);
+    cudaFree(g->mlp_norm);
     if (g->stream) cudaStreamDestroy(g->stream);
     if (g->stream2) cudaStreamDestroy(g->stream2);
     delete g;
@@ -1033,7 +1055,8 @@ static int check_opts(const ger_options* opt, ger_options* o) {
     if (!(o->delta > 0.0 && o->delta < 1.0)) return fail(GER_ERR_INVALID, "delta must be in (0, 1)");
     if (o->tau < 1 || o->tau > 20) return fail(GER_ERR_INVALID, "tau must be in 1..20");
     if (o->precision != GER_FP32 && o->precision != GER_FP64) return fail(GER_ERR_INVALID, "bad precision");
-    if (o->switch_policy != GER_SWITCH_RULE && o->switch_policy != GER_SWITCH_FIXED)
+    if (o->switch_policy != GER_SWITCH_RULE && o->switch_policy != GER_SWITCH_FIXED &&
+        o->switch_policy != GER_SWITCH_MLP)
         return fail(GER_ERR_INVALID, "bad switch policy");
     if (o->ell_formula != GER_ELL_REFINED && o->ell_formula != GER_ELL_PENG) return fail(GER_ERR_INVALID, "bad ell formula");
     if (o->smm_engine != GER_ENGINE_SPARSE && o->smm_engine != GER_ENGINE_DENSE)
@@ -1044,7 +1067,8 @@ static int check_opts(const ger_options* opt, ger_options* o) {
 }
 
 static int host_batch(ger_graph* g, int64_t q, const int32_t* s, const int32_t* t, const double* eps_arr,
-                      double eps, const ger_options* opt, double* r_out, ger_query_stats* stats) {
+                      double eps, const ger_options* opt, double* r_out, ger_query_stats* stats,
+                      float* trace_out = nullptr, int32_t trace_steps = 0) {
     if (!g || q < 0 || (q > 0 && (!s || !t || !r_out))) return fail(GER_ERR_INVALID, "null argument or q < 0");
     if (q > 0x7fffffff) return fail(GER_ERR_INVALID, "q too large");
     Plan p;
@@ -1079,7 +1103,24 @@ static int host_batch(ger_graph* g, int64_t q, const int32_t* s, const int32_t* 
     p.r = w.r;
     p.stats = w.stats;
     p.st = st;
+    float* tr = nullptr;
+    const size_t tr_bytes = trace_out ? (size_t)q * (size_t)trace_steps * kTraceWidth * sizeof(float) : 0;
+    if (trace_out) {
+        if (cudaMalloc(&tr, tr_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(GER_ERR_OOM, "cost log (%zu bytes)", tr_bytes);
+        }
+        p.trace = tr;
+        p.trace_steps = trace_steps;
+        cudaMemsetAsync(tr, 0, tr_bytes, st);
+    }
     rc = run_batch(g, p);
+    if (!rc && trace_out) {
+        const cudaError_t e = cudaMemcpyAsync(trace_out, tr, tr_bytes, cudaMemcpyDeviceToHost, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "reading the cost log");
+        cudaStreamSynchronize(st);
+    }
+    cudaFree(tr);
     if (rc) return rc;
     GER_CUDA(cudaMemcpyAsync(r_out, w.r, q * sizeof(double), cudaMemcpyDeviceToHost, st));
     if (stats) GER_CUDA(cudaMemcpyAsync(stats, w.stats, q * sizeof(ger_query_stats), cudaMemcpyDeviceToHost, st));
@@ -1097,6 +1138,48 @@ int ger_query_batch_eps(ger_graph* g, int64_t q, const int32_t* s, const int32_t
                         const ger_options* opt, double* r_out, ger_query_stats* stats) {
     if (q > 0 && !eps) return fail(GER_ERR_INVALID, "null eps");
     return host_batch(g, q, s, t, eps, 0.0, opt, r_out, stats);
+}
+
+int ger_smm_trace(ger_graph* g, int64_t q, const int32_t* s, const int32_t* t, const double* eps,
+                  const ger_options* opt, int32_t max_steps, float* log_out, ger_query_stats* stats) {
+    if (q > 0 && (!eps || !log_out)) return fail(GER_ERR_INVALID, "null eps or log");
+    if (max_steps < 1 || max_steps > 4096) return fail(GER_ERR_INVALID, "max_steps must be in 1..4096");
+    ger_options o;
+    if (opt) o = *opt; else ger_default_options(&o);
+    o.switch_policy = GER_SWITCH_FIXED;
+    o.fixed_ell_b = max_steps;
+    o.per_query = 0;
+    std::vector<double> r((size_t)std::max<int64_t>(q, 1));
+    return host_batch(g, q, s, t, eps, 0.0, &o, r.data(), stats, log_out, max_steps);
+}
+
+int ger_set_switch_mlp(ger_graph* g, const float* norm, const uint16_t* weights) {
+    if (!g) return fail(GER_ERR_INVALID, "null graph");
+    cudaSetDevice(g->device);
+    if (!weights) {
+        if (g->stream) cudaStreamSynchronize(g->stream);
+        cudaFree(g->mlp_w);
+        cudaFree(g->mlp_norm);
+        g->mlp_w = nullptr;
+        g->mlp_norm = nullptr;
+        return GER_OK;
+    }
+    if (!norm) return fail(GER_ERR_INVALID, "null normalisation");
+    for (int k = 0; k < kMlpIn; ++k)
+        if (!(norm[kMlpIn + k] > 0.f) || !std::isfinite(norm[k])) return fail(GER_ERR_INVALID, "bad normalisation");
+    if (!g->mlp_w) {
+        if (cudaMalloc(&g->mlp_w, kMlpParams * sizeof(uint16_t) + 16) != cudaSuccess ||
+            cudaMalloc(&g->mlp_norm, 2 * kMlpIn * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(g->mlp_w);
+            g->mlp_w = nullptr;
+            return fail(GER_ERR_OOM, "switch network");
+        }
+    }
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    GER_CUDA(cudaMemcpy(g->mlp_w, weights, kMlpParams * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    GER_CUDA(cudaMemcpy(g->mlp_norm, norm, 2 * kMlpIn * sizeof(float), cudaMemcpyHostToDevice));
+    return GER_OK;
 }
 
 int ger_query_batch_dev(ger_graph* g, int64_t q, const int32_t* s_dev, const int32_t* t_dev, const double* eps_dev,

@@ -61,6 +61,7 @@ struct QSmm {
     int32_t dense;               // 1: this query's SMM runs on the dense engine
     int32_t dgo;                 // dense engine: 1 while iterations continue
     int32_t dblock, dcol;        // dense block and column pair
+    int32_t mlp_stop;            // learned switch: 1 when its network says to stop now
     int64_t tab_off, tab_cap;    // table of the current frontier
     int64_t ntab_off, ntab_cap;  // table being filled
     unsigned long long vol_paper;  // sum_{V_s} d + sum_{V_t} d (Eq. 17)
@@ -199,6 +200,68 @@ __device__ __forceinline__ void warp_top2(double& a, double& b) {
         double b2 = __shfl_xor_sync(0xffffffffu, b, o);
         top2_merge(a, b, a2, b2);
     }
+}
+
+// ---------------------------------------------------------------------------
+// switch quantities (Eqs. 8, 9, 17) and the learned switch's inputs
+// ---------------------------------------------------------------------------
+
+// psi (Eq. 9), eta0 = max(1, ceil(eta*/2^(tau-1))) with eta* from Eq. (8),
+// h = (2^tau - 1) eta0
+__device__ __forceinline__ void switch_quantities(int64_t lf, double s1, double s2, double t1, double t2, double ds,
+                                                  double dt, double eps, double delta, int tau, double* psi,
+                                                  int64_t* eta0, double* h) {
+    const double up = (double)((lf + 1) / 2), dn = (double)(lf / 2);
+    const double p = 2.0 * up * (s1 / ds + t1 / dt) + 2.0 * dn * (s2 / ds + t2 / dt);
+    const double es = 2.0 * p * p * log(2.0 * (double)tau / delta) / (eps * eps);
+    int64_t e0 = (int64_t)ceil(es / ldexp(1.0, tau - 1));
+    if (e0 < 1) e0 = 1;
+    *psi = p;
+    *eta0 = e0;
+    *h = (double)((((int64_t)1 << tau) - 1) * e0);
+}
+
+// max_1, max_2 of s* and t* after an SMM iteration (entries outside the
+// frontier are zero, so accumulators starting at 0.0 already include them)
+__device__ __forceinline__ void smm_maxima(const QSmm* M, double* s1, double* s2, double* t1, double* t2) {
+    *s1 = __longlong_as_double((long long)M->max1s);
+    *t1 = __longlong_as_double((long long)M->max1t);
+    *s2 = M->cnt1s >= 2 ? *s1 : __longlong_as_double((long long)M->max2s);
+    *t2 = M->cnt1t >= 2 ? *t1 : __longlong_as_double((long long)M->max2t);
+}
+
+// The learned switch: a 6 -> 64 -> 64 -> 1 ReLU network with FP16 weights and
+// FP32 arithmetic. Parameter order (one FP16 array): W1[64][6], b1[64],
+// W2[64][64] (W2[j][k] multiplies hidden unit k of layer 1), b2[64], W3[64], b3.
+constexpr int kMlpIn = 6;
+constexpr int kMlpH = 64;
+constexpr int kMlpOffW1 = 0;
+constexpr int kMlpOffB1 = kMlpOffW1 + kMlpH * kMlpIn;
+constexpr int kMlpOffW2 = kMlpOffB1 + kMlpH;
+constexpr int kMlpOffB2 = kMlpOffW2 + kMlpH * kMlpH;
+constexpr int kMlpOffW3 = kMlpOffB2 + kMlpH;
+constexpr int kMlpOffB3 = kMlpOffW3 + kMlpH;
+constexpr int kMlpParams = kMlpOffB3 + 1;  // 4673
+
+// Raw inputs of the learned switch after SMM iteration lb (Eq. 17's state):
+// log d(s), log d(t), l - l_b, log(volume), log h(l - l_b),
+// max_1(s*)/d(s) + max_1(t*)/d(t). Returns h through *h_out.
+__device__ __forceinline__ void switch_features(const QState* Q, const QSmm* M, int64_t lb, double delta, int tau,
+                                                float f[kMlpIn], double* h_out) {
+    double s1, s2, t1, t2;
+    smm_maxima(M, &s1, &s2, &t1, &t2);
+    const double ds = (double)Q->ds, dt = (double)Q->dt;
+    const int64_t lf = (int64_t)Q->ell - lb;
+    double psi = 0.0, h = 0.0;
+    int64_t eta0 = 0;
+    if (lf > 0) switch_quantities(lf, s1, s2, t1, t2, ds, dt, Q->eps, delta, tau, &psi, &eta0, &h);
+    f[0] = (float)log(ds);
+    f[1] = (float)log(dt);
+    f[2] = (float)lf;
+    f[3] = (float)log((double)M->vol_paper);
+    f[4] = h > 0.0 ? (float)log(h) : 0.0f;
+    f[5] = (float)(s1 / ds + t1 / dt);
+    *h_out = h;
 }
 
 }  // namespace geer

@@ -40,7 +40,17 @@ struct SmmArgs {
     void* dense_X[2];      // value buffers: block b at b * n * dense_width
     SmmCtl* ctl;
     int* err_flag;
+    // learned switch (policy 1): input normalisation (mean[6], std[6]) and FP16 weights
+    const float* mlp_norm = nullptr;
+    const unsigned short* mlp_w = nullptr;  // null: no network, the rule of Eq. (17) decides
+    // cost log: per query and SMM iteration 1..trace_steps, kTraceWidth floats
+    float* trace = nullptr;
+    int32_t trace_steps = 0;
 };
+
+// Columns of one cost-log row: the six switch inputs, the union frontier's
+// volume (the next push's size) and Eq. (17)'s volume.
+constexpr int kTraceWidth = 8;
 
 // Per-warp partial sums of the dense SpMM epilogue, per query.
 struct DensePartial {
@@ -103,6 +113,7 @@ void launch_smm_push(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 void launch_smm_finish(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 void launch_smm_top2(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 void launch_smm_decide(const SmmArgs& a, cudaStream_t st);
+void launch_smm_mlp(const SmmArgs& a, cudaStream_t st);  // the learned switch's call per query
 void launch_smm_advance(const SmmArgs& a, cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st);
 void launch_smm_start(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 void launch_smm_iteration(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
@@ -129,7 +140,7 @@ void note_launches(int k);
 // kernel families timed by the profiler
 enum Family : int { FAM_SMM_SETUP = 0, FAM_SMM_ALLOC, FAM_SMM_CLEAR, FAM_SMM_PUSH, FAM_SMM_PUSH_HEAVY, FAM_SMM_FINISH,
                     FAM_SMM_TOP2, FAM_SMM_DECIDE, FAM_DENSE_SPMM, FAM_AMC_SCHEDULE, FAM_AMC_WALK, FAM_AMC_REDUCE,
-                    FAM_FINALIZE, FAM_LANCZOS, FAM_COUNT };
+                    FAM_FINALIZE, FAM_LANCZOS, FAM_SMM_MLP, FAM_MLP_TRAIN, FAM_COUNT };
 // bracket one launch on stream st with profiler events (no-op when off)
 void prof_begin(int fam, cudaStream_t st);
 void prof_end(int fam, cudaStream_t st);

@@ -174,7 +174,6 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     const int grid = sm_count * 8;
     launch_smm_start(fp64, a, grid, st);
     launch_smm_advance(a, 0, false, st);
-    note_launches(8);
     for (int iter = 1; iter < 100000; ++iter) {
         int n_want = 0;
         rc = sync_read_int(&ctl->n_want, &n_want, st);
@@ -182,8 +181,7 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
         if (n_want == 0) break;
         launch_smm_iteration(fp64, a, grid, st);
         launch_smm_advance(a, 0, false, st);
-        note_launches(8);
-    }
+        }
     AmcArgs m;
     m.g = dg;
     m.nq = (int32_t)q;

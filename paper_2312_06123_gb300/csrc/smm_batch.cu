@@ -486,20 +486,6 @@ __global__ void __launch_bounds__(256) smm_top2_kernel(SmmArgs a) {
     }
 }
 
-// psi (Eq. 9), eta0 = max(1, ceil(eta*/2^(tau-1))) with eta* from Eq. (8),
-// h = (2^tau - 1) eta0
-__device__ void switch_quantities(int64_t lf, double s1, double s2, double t1, double t2, double ds, double dt,
-                                  double eps, double delta, int tau, double* psi, int64_t* eta0, double* h) {
-    const double up = (double)((lf + 1) / 2), dn = (double)(lf / 2);
-    const double p = 2.0 * up * (s1 / ds + t1 / dt) + 2.0 * dn * (s2 / ds + t2 / dt);
-    const double es = 2.0 * p * p * log(2.0 * (double)tau / delta) / (eps * eps);
-    int64_t e0 = (int64_t)ceil(es / ldexp(1.0, tau - 1));
-    if (e0 < 1) e0 = 1;
-    *psi = p;
-    *eta0 = e0;
-    *h = (double)((((int64_t)1 << tau) - 1) * e0);
-}
-
 // decide: one thread per query whose table was just finished
 __global__ void smm_decide_kernel(SmmArgs a) {
     const int iter = a.ctl->iter;
@@ -512,12 +498,8 @@ __global__ void smm_decide_kernel(SmmArgs a) {
         Q->r_b += M->sval[0] / ds + M->sval[3] / dt - M->sval[2] / ds - M->sval[1] / dt;
         const int64_t lb = iter;
         const int64_t ell = Q->ell;
-        // max_1, max_2 of the full vectors: entries outside the table are zero,
-        // so the accumulators starting at 0.0 already include them
-        const double s1 = __longlong_as_double((long long)M->max1s);
-        const double t1 = __longlong_as_double((long long)M->max1t);
-        const double s2 = M->cnt1s >= 2 ? s1 : __longlong_as_double((long long)M->max2s);
-        const double t2 = M->cnt1t >= 2 ? t1 : __longlong_as_double((long long)M->max2t);
+        double s1, s2, t1, t2;
+        smm_maxima(M, &s1, &s2, &t1, &t2);
         const double vol = (double)M->vol_paper;
         const int64_t lf = ell - lb;
         double psi = 0.0, h = 0.0;
@@ -527,8 +509,21 @@ __global__ void smm_decide_kernel(SmmArgs a) {
         if (iter == 0) {
             go = M->lb_target >= 0 ? (M->lb_target > 0) : (ell >= 1);  // the loop runs once when l >= 1
         } else {
-            const bool free_stop = (vol > h) || (lb >= ell);  // Eq. (17)
+            // Eq. (17), or the learned switch's call when a network is installed
+            const bool learned = a.policy == 1 && a.mlp_w != nullptr;
+            const bool free_stop = (lb >= ell) || (learned ? M->mlp_stop != 0 : vol > h);
             go = M->lb_target >= 0 ? (lb < M->lb_target) : !free_stop;
+            if (a.trace && lb <= a.trace_steps) {
+                // cost log of the learned switch: its inputs and the next push's size
+                float f[kMlpIn];
+                double hh;
+                switch_features(Q, M, lb, a.delta, a.tau, f, &hh);
+                float* row = a.trace + ((int64_t)q * a.trace_steps + (lb - 1)) * kTraceWidth;
+#pragma unroll
+                for (int k = 0; k < kMlpIn; ++k) row[k] = f[k];
+                row[6] = (float)M->vol_union;
+                row[7] = (float)M->vol_paper;
+            }
         }
         // the table just finished holds the current frontier
         M->tab_off = M->ntab_off;
@@ -538,7 +533,9 @@ __global__ void smm_decide_kernel(SmmArgs a) {
             atomicAdd(&a.ctl->n_want, 1);
         } else if (go) {
             int64_t cap = 16;
-            while (cap < 2 * (int64_t)M->vol_union) cap <<= 1;
+            // the next frontier has at most min(push pairs, n) distinct nodes; load <= 1/2
+            const int64_t most = min((int64_t)M->vol_union, (int64_t)a.g.n);
+            while (cap < 2 * most) cap <<= 1;
             if (cap > a.max_table) {
                 Q->status = ST_ERROR;
                 Q->err = DERR_CAPACITY;
@@ -600,18 +597,21 @@ void launch_smm_setup(const SmmArgs& a, cudaStream_t st) {
     prof_begin(FAM_SMM_SETUP, st);
     smm_setup_kernel<<<grid, 256, 0, st>>>(a);
     prof_end(FAM_SMM_SETUP, st);
+    note_launches(1);
 }
 
 void launch_smm_alloc(const SmmArgs& a, cudaStream_t st) {
     prof_begin(FAM_SMM_ALLOC, st);
     smm_alloc_kernel<<<1, kCta, 0, st>>>(a);
     prof_end(FAM_SMM_ALLOC, st);
+    note_launches(1);
 }
 
 void launch_smm_clear(const SmmArgs& a, int grid, cudaStream_t st) {
     prof_begin(FAM_SMM_CLEAR, st);
     smm_clear_kernel<<<grid, 256, 0, st>>>(a);
     prof_end(FAM_SMM_CLEAR, st);
+    note_launches(1);
 }
 
 void launch_smm_seed(const SmmArgs& a, cudaStream_t st) {
@@ -619,6 +619,7 @@ void launch_smm_seed(const SmmArgs& a, cudaStream_t st) {
     prof_begin(FAM_SMM_PUSH, st);
     smm_seed_kernel<<<grid, 256, 0, st>>>(a);
     prof_end(FAM_SMM_PUSH, st);
+    note_launches(1);
 }
 
 void launch_smm_push(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
@@ -630,6 +631,7 @@ void launch_smm_push(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
     if (fp64) smm_push_heavy_kernel<double><<<grid, 256, 0, st>>>(a);
     else smm_push_heavy_kernel<float><<<grid, 256, 0, st>>>(a);
     prof_end(FAM_SMM_PUSH_HEAVY, st);
+    note_launches(2);
 }
 
 void launch_smm_finish(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
@@ -637,6 +639,7 @@ void launch_smm_finish(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
     if (fp64) smm_finish_kernel<double><<<grid, 256, 0, st>>>(a);
     else smm_finish_kernel<float><<<grid, 256, 0, st>>>(a);
     prof_end(FAM_SMM_FINISH, st);
+    note_launches(1);
 }
 
 void launch_smm_top2(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
@@ -644,17 +647,21 @@ void launch_smm_top2(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
     if (fp64) smm_top2_kernel<double><<<grid, 256, 0, st>>>(a);
     else smm_top2_kernel<float><<<grid, 256, 0, st>>>(a);
     prof_end(FAM_SMM_TOP2, st);
+    note_launches(1);
 }
 
 void launch_smm_decide(const SmmArgs& a, cudaStream_t st) {
     const int grid = (int)std::min<int64_t>((a.nq + 255) / 256, 1024);
+    if (a.policy == 1 && a.mlp_w != nullptr) launch_smm_mlp(a, st);
     prof_begin(FAM_SMM_DECIDE, st);
     smm_decide_kernel<<<grid, 256, 0, st>>>(a);
     prof_end(FAM_SMM_DECIDE, st);
+    note_launches(1);
 }
 
 void launch_smm_advance(const SmmArgs& a, cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st) {
     smm_advance_kernel<<<1, 1, 0, st>>>(a, h, use_handle ? 1 : 0);
+    note_launches(1);
 }
 
 void launch_smm_iteration(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {

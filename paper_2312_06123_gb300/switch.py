@@ -1,0 +1,191 @@
+"""The learned SMM -> AMC switch: cost logs, training and evaluation.
+
+Algorithm 3 stops its SMM iterations by the cost comparison of Eq. (17)
+(Section 4.3): support volume against h(l - l_b). The learned switch makes
+the same decision with a 6 -> 64 -> 64 -> 1 network fed the state after
+each iteration (log d(s), log d(t), l - l_b, log volume, log h(l - l_b),
+max_1(s*)/d(s) + max_1(t*)/d(t)); it predicts
+
+    log C(j + 1) - log C(j),   C(j) = kappa * sum_{i < j} push(i) + walks(j),
+
+the change of the query's cost from one more iteration, where push(i) is
+the size of the push that computes iteration i + 1 (sum of d(v) over the
+union frontier V_s u V_t after iteration i) and walks(j) the AMC walk steps
+when the query switches after j iterations; kappa is the price of one push
+pair in walk steps. The query switches once the prediction is >= 0. The
+truncation length l is not touched, so Theorem 2's guarantee holds whatever
+the network decides.
+
+This module is host-side bookkeeping on small arrays: every SMM iteration,
+walk, network evaluation, gradient and Adam step runs in the CUDA library
+(ger_smm_trace, ger_query_batch_eps, ger_mlp_train, ...).
+"""
+from __future__ import annotations
+
+import copy
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import (GER_ENGINE_DENSE, GER_SWITCH_FIXED, GER_SWITCH_MLP, GER_SWITCH_RULE, MLP_HIDDEN, MLP_INPUTS,
+               MLP_PARAMS,
+               default_options, mlp_train, mlp_train_options, profile_enable, profile_read)
+
+FEATURES = ("log d(s)", "log d(t)", "l - l_b", "log volume", "log h(l - l_b)", "max1 s*/d(s) + max1 t*/d(t)")
+TARGET_CLIP = 4.0
+
+
+@dataclass
+class CostLog:
+    """Rows (inputs after iteration j, log C(j+1) - log C(j)) of a query set."""
+    feats: np.ndarray          # [rows][6] raw network inputs
+    target: np.ndarray         # [rows]
+    query: np.ndarray          # [rows] query index
+    step: np.ndarray           # [rows] j
+    cost: np.ndarray           # [q][max_steps + 1] C(j) (nan where undefined)
+    push: np.ndarray           # [q][max_steps + 1] push(i)
+    walks: np.ndarray          # [q][max_steps + 1] walks(j)
+    ell: np.ndarray            # [q]
+    kappa: float
+
+
+@dataclass
+class SwitchModel:
+    norm: np.ndarray           # mean[6], std[6]
+    weights: np.ndarray        # FP16 bit patterns (uint16[MLP_PARAMS])
+    loss: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    kappa: float = 1.0
+
+
+def _with(o, **kw):
+    o = copy.copy(o) if o is not None else default_options()
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def cost_log(G, s, t, eps, degrees, options=None, max_steps: int = 12, kappa: float = 1.0,
+             engine: int = GER_ENGINE_DENSE) -> CostLog:
+    """Log the inputs after every SMM iteration j <= max_steps (one traced
+    batch) and the walk steps of switching after j (one batch per j), and
+    turn them into training rows. The logging runs use `engine` (dense by
+    default: their SMM goes deep); the logged values do not depend on it."""
+    options = _with(options, smm_engine=engine)
+    s = np.asarray(s, np.int32)
+    t = np.asarray(t, np.int32)
+    q = len(s)
+    eps = np.broadcast_to(np.asarray(eps, np.float64), (q,)).copy()
+    log, st = G.smm_trace(s, t, eps, options, max_steps)
+    ell = st["ell"].astype(np.int64)
+    push = np.zeros((q, max_steps + 1))
+    push[:, 0] = degrees[s].astype(np.float64) + degrees[t]
+    push[:, 1:] = log[:, :, 6]
+    walks = np.full((q, max_steps + 1), np.nan)
+    for j in range(1, max_steps + 1):
+        _, sj = G.query(s, t, eps, _with(options, switch_policy=GER_SWITCH_FIXED, fixed_ell_b=j), stats=True)
+        walks[:, j] = sj["walk_steps"]
+    cost = np.full((q, max_steps + 1), np.nan)
+    cum = np.cumsum(push, axis=1)  # cum[:, j - 1] = sum_{i < j} push(i)
+    for j in range(1, max_steps + 1):
+        cost[:, j] = kappa * cum[:, j - 1] + walks[:, j]
+    rows_f, rows_t, rows_q, rows_j = [], [], [], []
+    for i in range(q):
+        top = int(min(ell[i], max_steps))
+        for j in range(1, top):
+            c0, c1 = cost[i, j], cost[i, j + 1]
+            if not (c0 > 0 and c1 > 0):
+                continue
+            rows_f.append(log[i, j - 1, :MLP_INPUTS])
+            rows_t.append(np.clip(np.log(c1) - np.log(c0), -TARGET_CLIP, TARGET_CLIP))
+            rows_q.append(i)
+            rows_j.append(j)
+    return CostLog(np.asarray(rows_f, np.float32).reshape(-1, MLP_INPUTS), np.asarray(rows_t, np.float32),
+                   np.asarray(rows_q, np.int64), np.asarray(rows_j, np.int64), cost, push, walks, ell, kappa)
+
+
+def calibrate_kappa(G, s, t, eps, push, options=None, lb: int = 2) -> float:
+    """Price of one push pair in walk steps, from the kernel time of a batch
+    switching after `lb` iterations: (SMM time / pushed pairs) / (AMC time /
+    walk steps), both measured with CUDA events around every launch."""
+    o = _with(options, switch_policy=GER_SWITCH_FIXED, fixed_ell_b=lb, per_query=0)
+    import os
+    prev = os.environ.get("GEER_NO_GRAPH")
+    os.environ["GEER_NO_GRAPH"] = "1"  # per-launch events need the stream-ordered loop
+    try:
+        G.query(s, t, eps, o)
+        profile_enable(True)
+        _, st = G.query(s, t, eps, o, stats=True)
+        prof = profile_read()
+        profile_enable(False)
+    finally:
+        if prev is None:
+            del os.environ["GEER_NO_GRAPH"]
+        else:
+            os.environ["GEER_NO_GRAPH"] = prev
+    smm = sum(v[1] for k, v in prof.items() if k.startswith("smm_") or k.startswith("dense_"))
+    amc = sum(v[1] for k, v in prof.items() if k.startswith("amc_"))
+    lbq = np.minimum(st["ell_b"], lb)
+    pushed = float(sum(push[i, :lbq[i]].sum() for i in range(len(lbq))))
+    steps = float(st["walk_steps"].sum())
+    if pushed <= 0 or steps <= 0 or amc <= 0:
+        return 1.0
+    return float((smm / pushed) / (amc / steps))
+
+
+def init_weights(seed: int = 11) -> np.ndarray:
+    """He-normal hidden layers, small output layer, zero biases (FP16 bits)."""
+    rng = np.random.default_rng(seed)
+    w = np.zeros(MLP_PARAMS, np.float32)
+    k = 0
+    w[k:k + MLP_HIDDEN * MLP_INPUTS] = rng.normal(0, np.sqrt(2.0 / MLP_INPUTS), MLP_HIDDEN * MLP_INPUTS)
+    k += MLP_HIDDEN * MLP_INPUTS + MLP_HIDDEN
+    w[k:k + MLP_HIDDEN * MLP_HIDDEN] = rng.normal(0, np.sqrt(2.0 / MLP_HIDDEN), MLP_HIDDEN * MLP_HIDDEN)
+    k += MLP_HIDDEN * MLP_HIDDEN + MLP_HIDDEN
+    w[k:k + MLP_HIDDEN] = rng.normal(0, np.sqrt(1.0 / MLP_HIDDEN), MLP_HIDDEN)
+    return w.astype(np.float16).view(np.uint16)
+
+
+def normalisation(feats) -> np.ndarray:
+    mean = feats.mean(axis=0)
+    std = np.maximum(feats.std(axis=0), 1e-3)
+    return np.concatenate([mean, std]).astype(np.float32)
+
+
+def train(log: CostLog, epochs: int = 60, batch: int = 1024, lr: float = 2e-3, seed: int = 7) -> SwitchModel:
+    """Fit the network to a cost log on the GPU."""
+    norm = normalisation(log.feats)
+    x = (log.feats - norm[:MLP_INPUTS]) / norm[MLP_INPUTS:]
+    w, loss = mlp_train(x, log.target, init_weights(seed), mlp_train_options(epochs=epochs, batch=batch, lr=lr,
+                                                                              seed=seed))
+    return SwitchModel(norm, w, loss, log.kappa)
+
+
+def policy_cost(log: CostLog, ell_b) -> np.ndarray:
+    """C(ell_b) per query from a cost log (nan where ell_b is outside it)."""
+    q = log.cost.shape[0]
+    out = np.full(q, np.nan)
+    for i in range(q):
+        j = int(ell_b[i])
+        if 1 <= j < log.cost.shape[1]:
+            out[i] = log.cost[i, j]
+    return out
+
+
+def evaluate(G, s, t, eps, model: SwitchModel, log: CostLog, options=None, repeats: int = 3) -> dict:
+    """Rule against learned switch on one query set: switch points, modelled
+    cost C(l_b) from the set's cost log, and measured batch time."""
+    out = {}
+    G.set_switch_mlp(model.norm, model.weights)
+    for name, pol in (("rule", GER_SWITCH_RULE), ("mlp", GER_SWITCH_MLP)):
+        o = _with(options, switch_policy=pol)
+        r, st = G.query(s, t, eps, o, stats=True)
+        times = []
+        for _ in range(repeats):
+            t0 = time.perf_counter()
+            G.query(s, t, eps, o)
+            times.append(time.perf_counter() - t0)
+        c = policy_cost(log, st["ell_b"])
+        out[name] = {"ell_b": st["ell_b"].copy(), "r": r, "cost": c, "mean_cost": float(np.nanmean(c)),
+                     "seconds": float(np.median(times)), "walk_steps": int(st["walk_steps"].sum())}
+    return out

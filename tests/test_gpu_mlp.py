@@ -1,0 +1,181 @@
+"""GPU tests of the learned SMM -> AMC switch: its forward and backward
+kernels against the FP64 network oracle, its Adam step, training, the cost
+log against the GEER oracle's trace, parity and eps of GEER run under the
+learned switch, and what the trained network gains over Eq. (17)'s rule."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2312_06123_gb300 as geer
+import synth
+from oracle import exact
+from oracle import mlp as omlp
+from paper_2312_06123_gb300 import switch
+from synth import graphs, pairs
+
+from _parity import compare, replay
+
+pytestmark = pytest.mark.gpu
+
+
+def _weights(seed, scale=0.3):
+    """Random FP16 weights and their exact FP64 values."""
+    w16 = np.random.default_rng(seed).normal(0, scale, omlp.NPARAMS).astype(np.float16)
+    return w16.view(np.uint16), w16.astype(np.float64)
+
+
+@pytest.mark.parametrize("rows", [1, 63, 64, 65, 1000])
+def test_forward_matches_oracle(rows):
+    bits, theta = _weights(1)
+    x = np.random.default_rng(2).normal(size=(rows, 6)).astype(np.float32)
+    y = geer.mlp_forward(x, bits)
+    ref, _ = omlp.forward(theta, x.astype(np.float64))
+    # FP32 arithmetic against FP64 on the same FP16 weights
+    assert np.allclose(y, ref, rtol=1e-4, atol=1e-4 * max(1.0, np.abs(ref).max()))
+
+
+@pytest.mark.parametrize("rows", [1, 64, 65, 1000])
+def test_gradient_matches_oracle(rows):
+    bits, theta = _weights(3)
+    rng = np.random.default_rng(4)
+    x = rng.normal(size=(rows, 6)).astype(np.float32)
+    t = rng.normal(size=rows).astype(np.float32)
+    g, L = geer.mlp_gradient(x, t, bits)
+    gr, Lr = omlp.gradient(theta, x.astype(np.float64), t.astype(np.float64))
+    assert L == pytest.approx(Lr, rel=1e-5)
+    scale = np.abs(gr).max()
+    assert np.all(np.abs(g - gr) <= 1e-4 * scale + 1e-4 * np.abs(gr)), np.abs(g - gr).max() / scale
+
+
+def test_one_training_step_is_the_oracle_adam_step():
+    bits, theta = _weights(5)
+    rng = np.random.default_rng(6)
+    x = rng.normal(size=(300, 6)).astype(np.float32)
+    t = rng.normal(size=300).astype(np.float32)
+    lr = 1e-2
+    w1, loss = geer.mlp_train(x, t, bits, geer.mlp_train_options(epochs=1, batch=300, lr=lr))
+    gr, Lr = omlp.gradient(theta, x.astype(np.float64), t.astype(np.float64))
+    assert loss[0] == pytest.approx(Lr, rel=1e-5)
+    ref, _, _ = omlp.adam_step(theta, np.zeros_like(theta), np.zeros_like(theta), gr, 1, lr)
+    got = w1.view(np.float16).astype(np.float64)
+    want = ref.astype(np.float16).astype(np.float64)
+    # the first Adam step moves each weight by ~lr * sign(gradient); it lands on
+    # the same FP16 value except at rounding ties of nearly-zero gradients
+    big = np.abs(gr) > 1e-3 * np.abs(gr).max()
+    assert np.mean(got[big] == want[big]) > 0.99
+    ulp = np.spacing(np.abs(want).astype(np.float16)).astype(np.float64)
+    assert np.all(np.abs(got - want) <= ulp + 1e-12)
+
+
+def test_training_fits_a_smooth_target():
+    rng = np.random.default_rng(7)
+    x = rng.normal(size=(4000, 6)).astype(np.float32)
+    t = (np.tanh(x[:, 0] - 0.5 * x[:, 2]) + 0.3 * x[:, 4] ** 2 - 0.2).astype(np.float32)
+    w, loss = geer.mlp_train(x, t, switch.init_weights(1), geer.mlp_train_options(epochs=40, batch=256, lr=3e-3))
+    assert loss[-1] < 0.1 * loss[0]
+    y = geer.mlp_forward(x, w)
+    assert np.mean((y - t) ** 2) < 0.05 * np.var(t) + 0.01
+
+
+@pytest.fixture(scope="module")
+def c1():
+    w = synth.workload("c1")
+    g = w.graph
+    lam = oracle.lam(g)
+    G = geer.Graph.from_csr(g)
+    G.set_spectral_bound(lam)
+    return w, g, G, lam
+
+
+@pytest.mark.parametrize("prec", [geer.GER_FP64, geer.GER_FP32])
+def test_cost_log_matches_oracle_trace(c1, prec):
+    w, g, G, lam = c1
+    q = 30
+    d = g.degrees()
+    log, st = G.smm_trace(w.s[:q], w.t[:q], w.eps[:q], geer.default_options(precision=prec), max_steps=8)
+    for i in range(q):
+        lb = int(st["ell_b"][i])
+        assert lb == min(8, int(st["ell"][i]))
+        ref = oracle.geer(g, int(w.s[i]), int(w.t[i]), float(w.eps[i]), lam, q_index=i, forced_ell_b=lb,
+                          trace=True)
+        for j in range(1, lb + 1):
+            row = log[i, j - 1]
+            tr = ref.trace[j - 1]
+            assert row[7] == tr[1]                       # Eq. (17)'s volume, integer-exact
+            assert row[6] == tr[5]                       # the next push's size
+            assert row[0] == np.float32(np.log(d[w.s[i]])) and row[1] == np.float32(np.log(d[w.t[i]]))
+            assert row[2] == ref.ell - j
+            assert row[3] == pytest.approx(np.log(tr[1]), rel=1e-6)
+            assert row[5] == pytest.approx(tr[4], rel=1e-5)
+            if tr[2] > 0:
+                assert row[4] == pytest.approx(np.log(tr[2]), rel=1e-6)
+        assert np.all(log[i, lb:] == 0)
+
+
+def _small_rmat():
+    g = graphs.rmat(13, 16, 0.57, 0.19, 0.19, 1, "rmat scale=13 ef=16")
+    return g
+
+
+@pytest.fixture(scope="module")
+def rmat_model():
+    g = _small_rmat()
+    G = geer.Graph.from_csr(g)
+    lam, _, _ = G.spectral_bound()
+    d = g.degrees()
+    s, t = pairs.uniform_pairs(g.n, 768, 21)
+    kappa = 1.0
+    log = switch.cost_log(G, s, t, 0.05, d, max_steps=12, kappa=kappa)
+    model = switch.train(log, epochs=60, batch=512)
+    return g, G, lam, model, log
+
+
+def test_training_on_cost_logs_converges(rmat_model):
+    g, G, lam, model, log = rmat_model
+    assert log.feats.shape[0] > 1000
+    assert np.all(np.isfinite(model.loss))
+    assert model.loss[-1] < 0.7 * model.loss[0]
+
+
+def test_learned_switch_gains_over_the_rule(rmat_model):
+    # held-out pairs: the trained switch's modelled cost C(l_b) beats Eq. (17)
+    g, G, lam, model, _ = rmat_model
+    d = g.degrees()
+    s, t = pairs.uniform_pairs(g.n, 512, 22)
+    log = switch.cost_log(G, s, t, 0.05, d, max_steps=12, kappa=model.kappa)
+    res = switch.evaluate(G, s, t, 0.05, model, log)
+    ok = np.isfinite(res["rule"]["cost"]) & np.isfinite(res["mlp"]["cost"])
+    assert ok.mean() > 0.9
+    rule, learned = res["rule"]["cost"][ok].sum(), res["mlp"]["cost"][ok].sum()
+    print(f"learned switch: cost {learned:.4g} vs rule {rule:.4g} ({rule / learned:.3f}x); "
+          f"time {res['mlp']['seconds'] * 1e3:.2f} ms vs {res['rule']['seconds'] * 1e3:.2f} ms")
+    assert learned < rule
+    # the best switch point in hindsight bounds what any policy can reach
+    best = np.nanmin(log.cost[:, 1:], axis=1)[ok].sum()
+    assert best <= learned
+
+
+def test_learned_switch_keeps_parity_and_eps(c1, rmat_model):
+    # a network trained on one graph, run on another: any switch point is
+    # valid; walks replay bit-exactly and r stays within eps of L^+
+    w, g, G, lam = c1
+    model = rmat_model[3]
+    G.set_switch_mlp(model.norm, model.weights)
+    try:
+        r, st = G.query(w.s, w.t, w.eps, geer.default_options(precision=geer.GER_FP64,
+                                                                switch_policy=geer.GER_SWITCH_MLP), stats=True)
+    finally:
+        G.set_switch_mlp(None, None)
+    exact_r = exact.er_dense(g, w.s, w.t, exact.laplacian_pinv(g))
+    for i in range(w.q):
+        ref = replay(g, w.s[i], w.t[i], w.eps[i], lam, st[i], i)
+        compare(r[i], st[i], ref, 1e-9, 1e-9)
+    assert np.all(np.abs(r - exact_r) <= w.eps)
+
+
+def test_without_a_network_the_learned_policy_is_the_rule(c1):
+    w, g, G, lam = c1
+    G.set_switch_mlp(None, None)
+    r1, s1 = G.query(w.s, w.t, w.eps, geer.default_options(switch_policy=geer.GER_SWITCH_MLP), stats=True)
+    r2, s2 = G.query(w.s, w.t, w.eps, geer.default_options(), stats=True)
+    assert np.array_equal(r1, r2) and np.array_equal(s1["ell_b"], s2["ell_b"])

@@ -188,11 +188,18 @@ def test_geer_trace_volume_and_rb_match_dense():
     terms = exact.series_terms_dense(g, s, t, 6)
     reach_s = np.zeros(g.n, dtype=bool); reach_s[s] = True
     reach_t = np.zeros(g.n, dtype=bool); reach_t[t] = True
+    P = A / d[:, None]
+    xs = np.zeros(g.n); xs[s] = 1.0
+    xt = np.zeros(g.n); xt[t] = 1.0
     for i in range(1, 7):
         reach_s = (A @ reach_s.astype(np.int64)) > 0
         reach_t = (A @ reach_t.astype(np.int64)) > 0
+        xs, xt = P @ xs, P @ xt
         assert res.trace[i - 1, 1] == d[reach_s].sum() + d[reach_t].sum()
         assert res.trace[i - 1, 0] == pytest.approx(terms[:i + 1].sum(), rel=1e-12)
+        # the learned switch's inputs: Eq. (9)'s leading maxima and the union's volume
+        assert res.trace[i - 1, 4] == pytest.approx(xs.max() / d[s] + xt.max() / d[t], rel=1e-12)
+        assert res.trace[i - 1, 5] == d[reach_s | reach_t].sum()
 
 
 def test_geer_mean_over_seeds_is_r_ell():
