@@ -56,6 +56,8 @@ extern "C" {
 /* engine of the SMM iterations */
 #define GER_ENGINE_SPARSE 0 /* per-query frontier tables, push (fits the small frontiers of Eq. (17)'s switch) */
 #define GER_ENGINE_DENSE  1 /* blocks of query vectors, pull SpMM over all rows (deep SMM) */
+#define GER_ENGINE_HYBRID 2 /* sparse push first; a query whose next push reaches dense_switch pairs
+                               moves to a dense column (as many as dense_budget_mb holds) */
 
 /* truncation length formula */
 #define GER_ELL_REFINED 0   /* Eq. (6), Theorem 1 */
@@ -73,8 +75,11 @@ typedef struct ger_options {
     int32_t  ell_formula;   /* GER_ELL_REFINED (default) or GER_ELL_PENG */
     uint64_t seed;          /* walk RNG seed */
     int64_t  sparse_cap;    /* max SMM push pairs of one query iteration (0: no limit beyond the pool) */
-    int32_t  smm_engine;    /* GER_ENGINE_SPARSE (default) or GER_ENGINE_DENSE */
+    int32_t  smm_engine;    /* GER_ENGINE_SPARSE (default), GER_ENGINE_DENSE or GER_ENGINE_HYBRID */
     int32_t  dense_width;   /* dense engine: columns per block (2 per query); 0: autotuned per graph */
+    int64_t  dense_switch;  /* hybrid engine: push pairs at which a query moves to the SpMM; 0: nnz / 16 */
+    int32_t  dense_budget_mb; /* hybrid engine: device memory for dense columns (MiB); 0: 8192 */
+    int32_t  reserved0;
 } ger_options;
 
 /* Per-query statistics (all optional outputs). */

@@ -26,7 +26,7 @@ GER_SWITCH_RULE, GER_SWITCH_MLP, GER_SWITCH_FIXED = 0, 1, 2
 MLP_INPUTS, MLP_HIDDEN, MLP_PARAMS = 6, 64, 4673
 LOG_WIDTH = 8
 GER_ELL_REFINED, GER_ELL_PENG = 0, 1
-GER_ENGINE_SPARSE, GER_ENGINE_DENSE = 0, 1
+GER_ENGINE_SPARSE, GER_ENGINE_DENSE, GER_ENGINE_HYBRID = 0, 1, 2
 
 
 class GeerError(RuntimeError):
@@ -40,7 +40,8 @@ class Options(ctypes.Structure):
                 ("per_query", ctypes.c_int32), ("switch_policy", ctypes.c_int32),
                 ("fixed_ell_b", ctypes.c_int32), ("ell_formula", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("sparse_cap", ctypes.c_int64), ("smm_engine", ctypes.c_int32),
-                ("dense_width", ctypes.c_int32)]
+                ("dense_width", ctypes.c_int32), ("dense_switch", ctypes.c_int64), ("dense_budget_mb", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32)]
 
 
 class QueryStats(ctypes.Structure):

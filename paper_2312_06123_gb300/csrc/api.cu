@@ -162,6 +162,10 @@ struct Workspace {
     DensePartial* dpart = nullptr;
     size_t dX_bytes = 0, dpart_n = 0, dpieces_bytes = 0, dheavy_ctr_n = 0;
     int64_t dblock_q_n = 0;
+    int32_t* dmig = nullptr;          // hybrid engine: queries moved by one decision
+    int64_t dmig_n = 0;
+    int64_t dblock_n = 0;             // blocks the per-block arrays hold
+    uint64_t gen = 0;                 // bumped by every (re)allocation: captured graphs go stale
     // counters: [1] error flag (int), [2] AMC done counter
     int* counters = nullptr;
     // pinned readback
@@ -186,6 +190,10 @@ struct BatchGraph {
     int64_t launches = 0;       // kernels outside the while body
     int64_t body_launches = 0;  // kernels per pass of the while body
     bool mlp = false;           // captured with the learned switch's kernel
+    int64_t dense_cols = 0;     // dense columns of the captured engine
+    const void* dense_dev = nullptr;  // dense column map and move list the capture uses
+    const void* mig = nullptr;
+    uint64_t gen = 0;                 // workspace generation the capture saw
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<ProfRec> prof_recs;
@@ -224,7 +232,7 @@ static void free_ws(Workspace& w) {
     cudaFree(w.heavy);
     cudaFree(w.dX[0]); cudaFree(w.dX[1]);
     cudaFree(w.dblock_q); cudaFree(w.dblock_run); cudaFree(w.dunit_ctr); cudaFree(w.dheavy_ctr);
-    cudaFree(w.dpieces); cudaFree(w.dpart);
+    cudaFree(w.dpieces); cudaFree(w.dpart); cudaFree(w.dmig);
     if (w.host_rb) cudaFreeHost(w.host_rb);
     w = Workspace();
 }
@@ -258,6 +266,7 @@ static int ensure_ws(ger_graph* g, int64_t q, int64_t pool_cap) {
             return fail(GER_ERR_OOM, "workspace for %lld queries", (long long)q);
         }
         w.q_cap = qc;
+        ++w.gen;
         w.partial_cap = pc;
     }
     if (pool_cap > w.pool_cap) {
@@ -268,6 +277,7 @@ static int ensure_ws(ger_graph* g, int64_t q, int64_t pool_cap) {
             return fail(GER_ERR_OOM, "frontier-table pool of %lld slots", (long long)pool_cap);
         }
         w.pool_cap = pool_cap;
+        ++w.gen;
     }
     return GER_OK;
 }
@@ -449,6 +459,7 @@ static int ensure_dense(ger_graph* g, int64_t nq, int width, bool fp64) {
             return fail(GER_ERR_OOM, "dense blocks (%zu bytes each)", xb);
         }
         w.dX_bytes = xb;
+        ++w.gen;
     }
     if (pb > w.dpieces_bytes) {
         cudaFree(w.dpieces);
@@ -459,6 +470,7 @@ static int ensure_dense(ger_graph* g, int64_t nq, int width, bool fp64) {
             return fail(GER_ERR_OOM, "dense heavy-row pieces");
         }
         w.dpieces_bytes = pb;
+        ++w.gen;
     }
     if (hn > w.dheavy_ctr_n) {
         cudaFree(w.dheavy_ctr);
@@ -470,6 +482,7 @@ static int ensure_dense(ger_graph* g, int64_t nq, int width, bool fp64) {
             return fail(GER_ERR_OOM, "dense heavy-row counters");
         }
         w.dheavy_ctr_n = hn;
+        ++w.gen;
     }
     if (pn > w.dpart_n) {
         cudaFree(w.dpart);
@@ -480,21 +493,25 @@ static int ensure_dense(ger_graph* g, int64_t nq, int width, bool fp64) {
             return fail(GER_ERR_OOM, "dense partials");
         }
         w.dpart_n = pn;
+        ++w.gen;
     }
     const int64_t nbq = nblocks * qpb;
-    if (nbq > w.dblock_q_n) {
+    if (nbq > w.dblock_q_n || nblocks > w.dblock_n) {
+        const int64_t nq_alloc = std::max(nbq, w.dblock_q_n), nb_alloc = std::max<int64_t>(nblocks, w.dblock_n);
         cudaFree(w.dblock_q); cudaFree(w.dblock_run); cudaFree(w.dunit_ctr);
-        w.dblock_q = nullptr; w.dblock_run = nullptr; w.dunit_ctr = nullptr; w.dblock_q_n = 0;
-        if (alloc(&w.dblock_q, nbq) || alloc(&w.dblock_run, nblocks) || alloc(&w.dunit_ctr, nblocks)) {
+        w.dblock_q = nullptr; w.dblock_run = nullptr; w.dunit_ctr = nullptr; w.dblock_q_n = 0; w.dblock_n = 0;
+        if (alloc(&w.dblock_q, nq_alloc) || alloc(&w.dblock_run, nb_alloc) || alloc(&w.dunit_ctr, nb_alloc)) {
             cudaGetLastError();
             return fail(GER_ERR_OOM, "dense block map");
         }
-        w.dblock_q_n = nbq;
+        w.dblock_q_n = nq_alloc;
+        w.dblock_n = nb_alloc;
+        ++w.gen;
     }
     return GER_OK;
 }
 
-static DenseArgs make_dense_args(ger_graph* g, int64_t q0, int64_t nq, int width) {
+static DenseArgs make_dense_args(ger_graph* g, int64_t q0, int64_t nq, int width, bool fp64) {
     Workspace& w = g->ws;
     DenseArgs d;
     d.g = DevGraph{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info};
@@ -517,6 +534,7 @@ static DenseArgs make_dense_args(ger_graph* g, int64_t q0, int64_t nq, int width
     d.unit_ctr = w.dunit_ctr;
     d.heavy_ctr = w.dheavy_ctr;
     d.pieces = w.dpieces;
+    d.fp64 = fp64 ? 1 : 0;
 
     return d;
 }
@@ -612,46 +630,114 @@ static void issue_amc(ger_graph* g, AmcArgs m, int64_t nq, cudaStream_t st) {
     note_launches(1 + 2 * m.tau);
 }
 
+// Dense columns of the hybrid engine for a batch of nq queries: as many as
+// the memory budget holds (two buffers of n values per column), at most nq.
+static int64_t hybrid_columns(const ger_graph* g, const ger_options& o, int64_t nq) {
+    const int64_t budget = (int64_t)(o.dense_budget_mb > 0 ? o.dense_budget_mb : 8192) << 20;
+    const int64_t per = 2 * g->n * (o.precision == GER_FP64 ? 8 : 4);
+    return std::min<int64_t>(nq, budget / std::max<int64_t>(per, 1));
+}
+
+// Launch arguments of one batch (or one query) and its SMM engine.
+struct Engine {
+    SmmArgs a;
+    AmcArgs m;
+    DenseArgs d{};
+    bool dense = false, hybrid = false;
+    int grid = 0;
+    int64_t cols = 0;  // dense columns
+};
+
+static int prepare_engine(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool fp64, Engine* E) {
+    Workspace& w = g->ws;
+    make_args(g, p, q0, nq, fp64, &E->a, &E->m);
+    E->grid = g->sm_count * 8;
+    E->dense = p.o.smm_engine == GER_ENGINE_DENSE;
+    E->hybrid = p.o.smm_engine == GER_ENGINE_HYBRID;
+    SmmArgs& a = E->a;
+    if (!E->dense && !E->hybrid) return GER_OK;
+    a.dense_width = dense_width_for(g, p.o);
+    E->cols = E->dense ? nq : hybrid_columns(g, p.o, nq);
+    if (E->hybrid && (E->cols == 0 || !g->dense_units)) {
+        a.hybrid = 0;  // no room (or no work units) for dense columns: sparse only
+        E->hybrid = false;
+        return GER_OK;
+    }
+    int rc = ensure_dense(g, E->cols, a.dense_width, fp64);
+    if (rc) return rc;
+    if (E->hybrid) {
+        if (nq > w.dmig_n) {
+            cudaFree(w.dmig);
+            w.dmig = nullptr;
+            w.dmig_n = 0;
+            if (alloc(&w.dmig, nq)) {
+                cudaGetLastError();
+                return fail(GER_ERR_OOM, "hybrid move list");
+            }
+            w.dmig_n = nq;
+            ++w.gen;
+        }
+        a.hybrid = 1;
+        a.dense_cap = (int32_t)E->cols;
+        a.migrate_at = p.o.dense_switch > 0 ? p.o.dense_switch : std::max<int64_t>(g->nnz / 16, 1);
+        a.dense_block_q = w.dblock_q;
+        a.mig_list = w.dmig;
+    }
+    a.dense_X[0] = w.dX[0];
+    a.dense_X[1] = w.dX[1];
+    E->d = make_dense_args(g, q0, E->cols, a.dense_width, fp64);
+    return GER_OK;
+}
+
+// Iteration 0 of the SMM phase (everything before the first advance).
+static void issue_smm_start(ger_graph* g, Engine& E, bool fp64, cudaStream_t st) {
+    if (E.dense) {
+        launch_smm_setup(E.a, st);
+        launch_smm_alloc(E.a, st);
+        issue_dense_start(g, E.d, fp64, E.cols, st);
+        launch_smm_decide(E.a, st);
+    } else {
+        if (E.hybrid) cudaMemsetAsync(g->ws.dblock_q, 0xff, E.d.nblocks * (size_t)(E.d.width / 2) * sizeof(int32_t), st);
+        launch_smm_start(fp64, E.a, E.grid, st);
+        if (E.hybrid) launch_dense_migrate(fp64, E.d, E.a, st);
+    }
+}
+
+// One further SMM iteration (everything before its advance).
+static void issue_smm_iteration(Engine& E, bool fp64, cudaStream_t st) {
+    if (E.dense) {
+        launch_smm_alloc(E.a, st);
+        launch_dense_iteration(fp64, E.d, st);
+        launch_smm_decide(E.a, st);
+    } else if (E.hybrid) {
+        launch_smm_body(fp64, E.a, E.grid, st);
+        launch_dense_iteration(fp64, E.d, st);
+        launch_smm_decide(E.a, st);
+        launch_dense_migrate(fp64, E.d, E.a, st);
+    } else {
+        launch_smm_iteration(fp64, E.a, E.grid, st);
+    }
+}
+
 // The GEER launch sequence for queries [q0, q0 + nq), stream-ordered, with
 // one host round trip per SMM iteration to learn whether any query
 // continues.
 static int run_queries(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool fp64) {
     Workspace& w = g->ws;
-    SmmArgs a;
-    AmcArgs m;
-    make_args(g, p, q0, nq, fp64, &a, &m);
-    const int grid = g->sm_count * 8;
-    const bool dense = a.dense_engine != 0;
-    DenseArgs d{};
-    if (dense) {
-        int rc = ensure_dense(g, nq, a.dense_width, fp64);
-        if (rc) return rc;
-        a.dense_X[0] = w.dX[0];
-        a.dense_X[1] = w.dX[1];
-        d = make_dense_args(g, q0, nq, a.dense_width);
-        launch_smm_setup(a, p.st);
-        launch_smm_alloc(a, p.st);
-        issue_dense_start(g, d, fp64, nq, p.st);
-        launch_smm_decide(a, p.st);
-    } else {
-        launch_smm_start(fp64, a, grid, p.st);
-    }
-    launch_smm_advance(a, 0, false, p.st);
+    Engine E;
+    int rc = prepare_engine(g, p, q0, nq, fp64, &E);
+    if (rc) return rc;
+    issue_smm_start(g, E, fp64, p.st);
+    launch_smm_advance(E.a, 0, false, p.st);
     int32_t* n_want = reinterpret_cast<int32_t*>(w.host_rb + 2);
     for (int iter = 1; iter < 100000; ++iter) {
         GER_CUDA(cudaMemcpyAsync(n_want, &w.ctl->n_want, sizeof(int32_t), cudaMemcpyDeviceToHost, p.st));
         GER_CUDA(cudaStreamSynchronize(p.st));
         if (*n_want == 0) break;
-        if (dense) {
-            launch_smm_alloc(a, p.st);
-            launch_dense_iteration(fp64, d, p.st);
-            launch_smm_decide(a, p.st);
-        } else {
-            launch_smm_iteration(fp64, a, grid, p.st);
-        }
-        launch_smm_advance(a, 0, false, p.st);
+        issue_smm_iteration(E, fp64, p.st);
+        launch_smm_advance(E.a, 0, false, p.st);
     }
-    issue_amc(g, m, nq, p.st);
+    issue_amc(g, E.m, nq, p.st);
     return GER_OK;
 }
 
@@ -669,6 +755,7 @@ static bool same_key(const BatchGraph& bg, const Plan& p, bool fp64, const ger_g
     return bg.valid && bg.nq == p.q && bg.fp64 == fp64 && std::memcmp(&bg.o, &p.o, sizeof(ger_options)) == 0 &&
            bg.lambda == g->lambda && bg.pool == g->ws.ent && bg.state == g->ws.st && bg.prof == g_prof_on &&
            bg.dense == g->ws.dX[0] && bg.dense_w == (p.o.smm_engine ? dense_width_for(const_cast<ger_graph*>(g), p.o) : 0) &&
+           bg.dense_dev == g->ws.dblock_q && bg.mig == g->ws.dmig && bg.gen == g->ws.gen &&
            bg.mlp == (g->mlp_w != nullptr);
 }
 
@@ -683,19 +770,12 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
     destroy_graph(bg);
     Workspace& w = g->ws;
     cudaStream_t st = g->stream, st2 = g->stream2;
-    SmmArgs a;
-    AmcArgs m;
-    make_args(g, p, 0, p.q, fp64, &a, &m);
-    const int grid = g->sm_count * 8;
-    const bool dense = a.dense_engine != 0;
-    DenseArgs d{};
-    if (dense) {
-        int rc = ensure_dense(g, p.q, a.dense_width, fp64);
-        if (rc) return rc;
-        a.dense_X[0] = w.dX[0];
-        a.dense_X[1] = w.dX[1];
-        d = make_dense_args(g, 0, p.q, a.dense_width);
-    }
+    Engine E;
+    int rc = prepare_engine(g, p, 0, p.q, fp64, &E);
+    if (rc) return rc;
+    SmmArgs& a = E.a;
+    AmcArgs& m = E.m;
+    const bool dense = E.dense || E.hybrid;
     cudaGraph_t graph = nullptr;
     GER_CUDA(cudaGraphCreate(&graph, 0));
     cudaGraphConditionalHandle handle;
@@ -712,14 +792,7 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
     if (e == cudaSuccess) {
         cudaMemsetAsync(w.counters, 0, 4 * sizeof(int), st);
         cudaMemsetAsync(w.ctl, 0, sizeof(SmmCtl), st);
-        if (dense) {
-            launch_smm_setup(a, st);
-            launch_smm_alloc(a, st);
-            issue_dense_start(g, d, fp64, p.q, st);
-            launch_smm_decide(a, st);
-        } else {
-            launch_smm_start(fp64, a, grid, st);
-        }
+        issue_smm_start(g, E, fp64, st);
         launch_smm_advance(a, handle, true, st);
         cudaStreamCaptureStatus cs;
         const cudaGraphNode_t* deps = nullptr;
@@ -743,13 +816,7 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
             if (e == cudaSuccess) {
                 g_prof_suspend = true;  // no event records inside a conditional body
                 const int64_t before = g_captured;
-                if (dense) {
-                    launch_smm_alloc(a, st2);
-                    launch_dense_iteration(fp64, d, st2);
-                    launch_smm_decide(a, st2);
-                } else {
-                    launch_smm_iteration(fp64, a, grid, st2);
-                }
+                issue_smm_iteration(E, fp64, st2);
                 launch_smm_advance(a, handle, true, st2);
                 body_launches = g_captured - before;
                 g_captured = before;
@@ -787,6 +854,10 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
     bg.state = w.st;
     bg.dense = w.dX[0];
     bg.dense_w = dense ? a.dense_width : 0;
+    bg.dense_cols = E.cols;
+    bg.dense_dev = w.dblock_q;
+    bg.mig = w.dmig;
+    bg.gen = w.gen;
     bg.prof = g_prof_on;
     bg.launches = g_captured;  // kernels outside the while body, once per replay
     bg.body_launches = body_launches;
@@ -906,6 +977,8 @@ void ger_default_options(ger_options* o) {
     o->sparse_cap = 0;
     o->smm_engine = GER_ENGINE_SPARSE;
     o->dense_width = 0;
+    o->dense_switch = 0;
+    o->dense_budget_mb = 0;
 }
 
 const char* ger_last_error(void) { return g_err; }
@@ -1059,10 +1132,11 @@ static int check_opts(const ger_options* opt, ger_options* o) {
         o->switch_policy != GER_SWITCH_MLP)
         return fail(GER_ERR_INVALID, "bad switch policy");
     if (o->ell_formula != GER_ELL_REFINED && o->ell_formula != GER_ELL_PENG) return fail(GER_ERR_INVALID, "bad ell formula");
-    if (o->smm_engine != GER_ENGINE_SPARSE && o->smm_engine != GER_ENGINE_DENSE)
+    if (o->smm_engine != GER_ENGINE_SPARSE && o->smm_engine != GER_ENGINE_DENSE && o->smm_engine != GER_ENGINE_HYBRID)
         return fail(GER_ERR_INVALID, "bad smm engine");
     if (o->dense_width != 0 && !dense_width_ok(o->dense_width, o->precision == GER_FP64))
         return fail(GER_ERR_INVALID, "dense_width must be 32, 64 or 128 (FP32) or 32 or 64 (FP64)");
+    if (o->dense_switch < 0 || o->dense_budget_mb < 0) return fail(GER_ERR_INVALID, "negative dense option");
     return GER_OK;
 }
 

@@ -548,9 +548,59 @@ __global__ void dense_block_flags_kernel(DenseArgs d) {
     }
 }
 
+// Hybrid engine: blocks that received their first column in this decision
+// start as zeros in both buffers (columns are handed out in order, so the
+// new blocks are [dense_open, ceil(used / (width/2)))).
+__global__ void dense_open_kernel(DenseArgs d, int cap) {
+    const int qpb = d.width / 2;
+    const int b0 = d.ctl->dense_open;
+    const int b1 = (min(d.ctl->dense_next, cap) + qpb - 1) / qpb;
+    if (b1 <= b0) return;
+    const size_t esz = d.fp64 ? 8 : 4;
+    const int64_t per = d.g.n * (int64_t)d.width * (int64_t)esz / 16;  // uint4 per block and buffer
+    const int64_t total = (int64_t)(b1 - b0) * per;
+    for (int buf = 0; buf < 2; ++buf) {
+        uint4* X = reinterpret_cast<uint4*>(d.X[buf]) + (int64_t)b0 * per;
+        for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+             k += (int64_t)gridDim.x * blockDim.x)
+            X[k] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+// Hybrid engine: each query the last decision moved writes its frontier
+// table (F_l_b with s*, t* and the support bits of V_s, V_t) into its
+// column pair of the buffer the next SpMM reads. One CTA per moved query.
+template <typename T>
+__global__ void dense_migrate_kernel(DenseArgs d, SmmArgs a) {
+    const int nm = a.ctl->n_mig;
+    const int iter = a.ctl->iter;
+    T* X = reinterpret_cast<T*>(d.X[iter & 1]);
+    const T* ys = reinterpret_cast<const T*>(a.ys);
+    const T* yt = reinterpret_cast<const T*>(a.yt);
+    for (int k = blockIdx.x; k < nm; k += gridDim.x) {
+        const int q = a.mig_list[k];
+        const QSmm* M = a.sm + q;
+        const int64_t off = M->tab_off, cap = M->tab_cap;
+        T* col = X + (int64_t)M->dblock * d.g.n * d.width + 2 * M->dcol;
+        for (int64_t j = threadIdx.x; j < cap; j += blockDim.x) {
+            const GEntry e = a.ent[off + j];
+            if (e.v < 0) continue;
+            col[(int64_t)e.v * d.width] = with_support(ys[off + j], (e.bits & 1u) ? 0x80000000u : 0u);
+            col[(int64_t)e.v * d.width + 1] = with_support(yt[off + j], (e.bits & 2u) ? 0x80000000u : 0u);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+void launch_dense_migrate(bool fp64, const DenseArgs& d, const SmmArgs& a, cudaStream_t st) {
+    dense_open_kernel<<<1024, 256, 0, st>>>(d, a.dense_cap);
+    if (fp64) dense_migrate_kernel<double><<<256, 256, 0, st>>>(d, a);
+    else dense_migrate_kernel<float><<<256, 256, 0, st>>>(d, a);
+    note_launches(2);
+}
+
 bool dense_width_ok(int width, bool fp64) {
     return fp64 ? (width == 32 || width == 64) : (width == 32 || width == 64 || width == 128);
 }

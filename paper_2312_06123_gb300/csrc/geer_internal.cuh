@@ -82,6 +82,9 @@ struct SmmCtl {
     int32_t n_heavy;             // chunks of high-degree frontier nodes left to the heavy push
     int32_t iter;                // current SMM iteration (0: the initial frontier)
     int32_t pad;
+    // hybrid engine: dense columns handed out, queries moved by the last
+    // decision, dense blocks already zeroed
+    int32_t dense_next, n_mig, dense_open, pad2;
 };
 
 // Per-chunk partial sums of the walk kernel.

@@ -40,6 +40,13 @@ struct SmmArgs {
     void* dense_X[2];      // value buffers: block b at b * n * dense_width
     SmmCtl* ctl;
     int* err_flag;
+    // hybrid engine: a sparse query whose next push has >= migrate_at pairs
+    // moves to a free dense column (of dense_cap)
+    int32_t hybrid = 0;
+    int32_t dense_cap = 0;
+    int64_t migrate_at = 0;
+    int32_t* dense_block_q = nullptr;  // column -> query
+    int32_t* mig_list = nullptr;       // queries moved by the current decision
     // learned switch (policy 1): input normalisation (mean[6], std[6]) and FP16 weights
     const float* mlp_norm = nullptr;
     const unsigned short* mlp_w = nullptr;  // null: no network, the rule of Eq. (17) decides
@@ -79,6 +86,7 @@ struct DenseArgs {
     unsigned int* unit_ctr; // per block: next unit
     unsigned int* heavy_ctr;// per block and heavy row: pieces done (reset by the finishing warp)
     void* pieces;           // per block: nslots * width partial sums
+    int32_t fp64;           // element type of X
 };
 
 struct AmcArgs {
@@ -117,6 +125,8 @@ void launch_smm_mlp(const SmmArgs& a, cudaStream_t st);  // the learned switch's
 void launch_smm_advance(const SmmArgs& a, cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st);
 void launch_smm_start(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 void launch_smm_iteration(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
+// the sparse part of one iteration (alloc .. top2), without the decision
+void launch_smm_body(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 // the dense engine: iteration 0 and one pull-SpMM iteration (+ its epilogue)
 bool dense_width_ok(int width, bool fp64);
 int dense_prepare();  // cudaError_t of the shared-memory opt-in
@@ -125,6 +135,9 @@ void build_dense_units(int64_t n, const int64_t* row_ptr, std::vector<int4>* uni
 void launch_dense_map(const DenseArgs& d, int64_t nq, cudaStream_t st);
 void launch_dense_init(bool fp64, const DenseArgs& d, cudaStream_t st);
 void launch_dense_iteration(bool fp64, const DenseArgs& d, cudaStream_t st);
+// hybrid engine: zero newly used dense blocks, then scatter the frontier
+// tables of the queries the last decision moved into their dense columns
+void launch_dense_migrate(bool fp64, const DenseArgs& d, const SmmArgs& a, cudaStream_t st);
 void launch_amc_schedule(const AmcArgs& a, cudaStream_t st);
 void launch_amc_walk(const AmcArgs& a, int grid, cudaStream_t st);
 // batch statistics of batch a.batch; the last CTA schedules batch a.batch + 1

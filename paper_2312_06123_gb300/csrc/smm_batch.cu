@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(256) smm_push_kernel(SmmArgs a) {
         const GEntry e = a.ent[j];
         if (e.v < 0) continue;
         const int q = (int)(e.bits >> 2);
-        if (!a.sm[q].run) continue;
+        if (!a.sm[q].run || a.sm[q].dense) continue;  // dense queries iterate in the SpMM
         const int64_t rb = row_ptr[e.v], re = row_ptr[e.v + 1];
         if (re - rb > kLightMax) {
             // hand the node's neighbour list, in chunks, to the heavy push
@@ -337,6 +337,9 @@ __global__ void __launch_bounds__(256) smm_push_kernel(SmmArgs a) {
                 for (int c = lane; c < nch; c += 32) a.heavy[first + c] = (j << 20) | (int64_t)c;
                 continue;
             }
+            // the list is full: mark the reserved records that fit as empty, push here
+            for (int64_t c = (int64_t)first + lane; c < a.heavy_cap && c < (int64_t)first + nch; c += 32)
+                a.heavy[c] = -1;
         }
         push_range<T>(a, j, q, rb, re, lane, 32);
     }
@@ -350,6 +353,7 @@ __global__ void __launch_bounds__(256) smm_push_heavy_kernel(SmmArgs a) {
     const int64_t* row_ptr = a.g.row_ptr;
     for (int64_t c = blockIdx.x; c < nc; c += gridDim.x) {
         const int64_t rec = a.heavy[c];
+        if (rec < 0) continue;
         const int64_t j = rec >> 20, part = rec & 0xfffff;
         const GEntry e = a.ent[j];
         const int q = (int)(e.bits >> 2);
@@ -532,6 +536,23 @@ __global__ void smm_decide_kernel(SmmArgs a) {
             M->dgo = 1;
             atomicAdd(&a.ctl->n_want, 1);
         } else if (go) {
+            int col = -1;
+            if (a.hybrid && (int64_t)M->vol_union >= a.migrate_at) {
+                // hybrid engine: the next push is large; continue in a free dense column
+                col = atomicAdd(&a.ctl->dense_next, 1);
+                if (col >= a.dense_cap) col = -1;
+            }
+            if (col >= 0) {
+                const int qpb = a.dense_width / 2;
+                M->dense = 1;
+                M->dgo = 1;
+                M->dblock = col / qpb;
+                M->dcol = col % qpb;
+                a.dense_block_q[col] = q;
+                a.mig_list[atomicAdd(&a.ctl->n_mig, 1)] = q;
+                atomicAdd(&a.ctl->n_want, 1);
+                goto next_query;
+            }
             int64_t cap = 16;
             // the next frontier has at most min(push pairs, n) distinct nodes; load <= 1/2
             const int64_t most = min((int64_t)M->vol_union, (int64_t)a.g.n);
@@ -575,6 +596,7 @@ __global__ void smm_decide_kernel(SmmArgs a) {
                 Q->r = Q->r_b;
             }
         }
+    next_query:
         M->vol_paper = M->vol_union = M->count = 0;
         M->max1s = M->max1t = M->max2s = M->max2t = M->cnt1s = M->cnt1t = 0;
         M->sval[0] = M->sval[1] = M->sval[2] = M->sval[3] = 0.0;
@@ -586,6 +608,13 @@ __global__ void smm_decide_kernel(SmmArgs a) {
 __global__ void smm_advance_kernel(SmmArgs a, cudaGraphConditionalHandle h, int use_handle) {
     SmmCtl* C = a.ctl;
     C->iter += 1;
+    if (a.hybrid) {
+        // the moved queries' columns are filled; their blocks are zeroed
+        const int qpb = a.dense_width / 2;
+        const int used = min(C->dense_next, a.dense_cap);
+        C->dense_open = (used + qpb - 1) / qpb;
+        C->n_mig = 0;
+    }
     if (use_handle) cudaGraphSetConditional(h, C->n_want > 0 ? 1u : 0u);
 }
 
@@ -664,12 +693,16 @@ void launch_smm_advance(const SmmArgs& a, cudaGraphConditionalHandle h, bool use
     note_launches(1);
 }
 
-void launch_smm_iteration(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
+void launch_smm_body(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
     launch_smm_alloc(a, st);
     launch_smm_clear(a, grid, st);
     launch_smm_push(fp64, a, grid, st);
     launch_smm_finish(fp64, a, grid, st);
     launch_smm_top2(fp64, a, grid, st);
+}
+
+void launch_smm_iteration(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
+    launch_smm_body(fp64, a, grid, st);
     launch_smm_decide(a, st);
 }
 

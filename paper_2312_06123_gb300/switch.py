@@ -6,13 +6,15 @@ the same decision with a 6 -> 64 -> 64 -> 1 network fed the state after
 each iteration (log d(s), log d(t), l - l_b, log volume, log h(l - l_b),
 max_1(s*)/d(s) + max_1(t*)/d(t)); it predicts
 
-    log C(j + 1) - log C(j),   C(j) = kappa * sum_{i < j} push(i) + walks(j),
+    log C(j + 1) - log C(j),
+    C(j) = kappa * sum_{i < j} push(i) + walks(j) + mu * j,
 
 the change of the query's cost from one more iteration, where push(i) is
 the size of the push that computes iteration i + 1 (sum of d(v) over the
-union frontier V_s u V_t after iteration i) and walks(j) the AMC walk steps
-when the query switches after j iterations; kappa is the price of one push
-pair in walk steps. The query switches once the prediction is >= 0. The
+union frontier V_s u V_t after iteration i), walks(j) the AMC walk steps
+when the query switches after j iterations, kappa the price of one push
+pair and mu the share of one batched SMM iteration's fixed cost (its kernel
+launches) carried by one query, both in walk steps. The query switches once the prediction is >= 0. The
 truncation length l is not touched, so Theorem 2's guarantee holds whatever
 the network decides.
 
@@ -48,6 +50,8 @@ class CostLog:
     walks: np.ndarray          # [q][max_steps + 1] walks(j)
     ell: np.ndarray            # [q]
     kappa: float
+    mu: float = 0.0
+    inputs: np.ndarray | None = None  # [q][max_steps][6] raw inputs after each iteration
 
 
 @dataclass
@@ -56,6 +60,7 @@ class SwitchModel:
     weights: np.ndarray        # FP16 bit patterns (uint16[MLP_PARAMS])
     loss: np.ndarray = field(default_factory=lambda: np.zeros(0))
     kappa: float = 1.0
+    mu: float = 0.0
 
 
 def _with(o, **kw):
@@ -65,12 +70,13 @@ def _with(o, **kw):
     return o
 
 
-def cost_log(G, s, t, eps, degrees, options=None, max_steps: int = 12, kappa: float = 1.0,
+def cost_log(G, s, t, eps, degrees, options=None, max_steps: int = 12, kappa: float = 1.0, mu: float = 0.0,
              engine: int = GER_ENGINE_DENSE) -> CostLog:
     """Log the inputs after every SMM iteration j <= max_steps (one traced
     batch) and the walk steps of switching after j (one batch per j), and
-    turn them into training rows. The logging runs use `engine` (dense by
-    default: their SMM goes deep); the logged values do not depend on it."""
+    turn them into training rows priced with (kappa, mu). The logging runs
+    use `engine` (dense by default: their SMM goes deep); the logged values
+    do not depend on it."""
     options = _with(options, smm_engine=engine)
     s = np.asarray(s, np.int32)
     t = np.asarray(t, np.int32)
@@ -85,52 +91,79 @@ def cost_log(G, s, t, eps, degrees, options=None, max_steps: int = 12, kappa: fl
     for j in range(1, max_steps + 1):
         _, sj = G.query(s, t, eps, _with(options, switch_policy=GER_SWITCH_FIXED, fixed_ell_b=j), stats=True)
         walks[:, j] = sj["walk_steps"]
-    cost = np.full((q, max_steps + 1), np.nan)
+    return price(log[:, :, :MLP_INPUTS].copy(), push, walks, ell, kappa, mu)
+
+
+def price(inputs, push, walks, ell, kappa: float, mu: float) -> CostLog:
+    """Training rows of logged runs under the cost prices (kappa, mu)."""
+    q, steps = inputs.shape[0], inputs.shape[1]
+    cost = np.full((q, steps + 1), np.nan)
     cum = np.cumsum(push, axis=1)  # cum[:, j - 1] = sum_{i < j} push(i)
-    for j in range(1, max_steps + 1):
-        cost[:, j] = kappa * cum[:, j - 1] + walks[:, j]
+    for j in range(1, steps + 1):
+        cost[:, j] = kappa * cum[:, j - 1] + walks[:, j] + mu * j
     rows_f, rows_t, rows_q, rows_j = [], [], [], []
     for i in range(q):
-        top = int(min(ell[i], max_steps))
+        top = int(min(ell[i], steps))
         for j in range(1, top):
             c0, c1 = cost[i, j], cost[i, j + 1]
             if not (c0 > 0 and c1 > 0):
                 continue
-            rows_f.append(log[i, j - 1, :MLP_INPUTS])
+            rows_f.append(inputs[i, j - 1])
             rows_t.append(np.clip(np.log(c1) - np.log(c0), -TARGET_CLIP, TARGET_CLIP))
             rows_q.append(i)
             rows_j.append(j)
-    return CostLog(np.asarray(rows_f, np.float32).reshape(-1, MLP_INPUTS), np.asarray(rows_t, np.float32),
-                   np.asarray(rows_q, np.int64), np.asarray(rows_j, np.int64), cost, push, walks, ell, kappa)
+    out = CostLog(np.asarray(rows_f, np.float32).reshape(-1, MLP_INPUTS), np.asarray(rows_t, np.float32),
+                  np.asarray(rows_q, np.int64), np.asarray(rows_j, np.int64), cost, push, walks, ell, kappa, mu)
+    out.inputs = inputs
+    return out
 
 
-def calibrate_kappa(G, s, t, eps, push, options=None, lb: int = 2) -> float:
-    """Price of one push pair in walk steps, from the kernel time of a batch
-    switching after `lb` iterations: (SMM time / pushed pairs) / (AMC time /
-    walk steps), both measured with CUDA events around every launch."""
-    o = _with(options, switch_policy=GER_SWITCH_FIXED, fixed_ell_b=lb, per_query=0)
+def calibrate(G, s, t, eps, push, options=None, lb: int = 4) -> tuple[float, float]:
+    """(kappa, mu) from the kernel times of one batch switching after `lb`
+    iterations, measured with CUDA events around every launch: kappa =
+    (time per pushed pair) / (time per walk step); mu = (time of one SMM
+    iteration's launches beyond their work, i.e. the SMM time the push pairs
+    do not explain, per iteration and query) / (time per walk step). The SMM
+    time is split by a least-squares fit over iterations of
+    time_i = fixed + rate * pairs_i."""
     import os
+    q = len(s)
+    o = _with(options, switch_policy=GER_SWITCH_FIXED, fixed_ell_b=lb, per_query=0)
     prev = os.environ.get("GEER_NO_GRAPH")
     os.environ["GEER_NO_GRAPH"] = "1"  # per-launch events need the stream-ordered loop
     try:
         G.query(s, t, eps, o)
-        profile_enable(True)
-        _, st = G.query(s, t, eps, o, stats=True)
-        prof = profile_read()
-        profile_enable(False)
+        pts = []
+        amc_ms = steps = 0.0
+        for j in range(1, lb + 1):
+            profile_enable(True)
+            _, st = G.query(s, t, eps, _with(o, fixed_ell_b=j), stats=True)
+            prof = profile_read()
+            profile_enable(False)
+            smm = sum(v[1] for k, v in prof.items() if k.startswith("smm_") or k.startswith("dense_"))
+            lbq = np.minimum(st["ell_b"], j)
+            pairs_ = float(sum(push[i, :lbq[i]].sum() for i in range(q)))
+            pts.append((j, pairs_, smm))
+            amc_ms += sum(v[1] for k, v in prof.items() if k.startswith("amc_"))
+            steps += float(st["walk_steps"].sum())
     finally:
         if prev is None:
             del os.environ["GEER_NO_GRAPH"]
         else:
             os.environ["GEER_NO_GRAPH"] = prev
-    smm = sum(v[1] for k, v in prof.items() if k.startswith("smm_") or k.startswith("dense_"))
-    amc = sum(v[1] for k, v in prof.items() if k.startswith("amc_"))
-    lbq = np.minimum(st["ell_b"], lb)
-    pushed = float(sum(push[i, :lbq[i]].sum() for i in range(len(lbq))))
-    steps = float(st["walk_steps"].sum())
-    if pushed <= 0 or steps <= 0 or amc <= 0:
-        return 1.0
-    return float((smm / pushed) / (amc / steps))
+    if steps <= 0 or amc_ms <= 0:
+        return 1.0, 0.0
+    per_step = amc_ms / steps
+    it = np.array([p[0] for p in pts], float)
+    pr = np.array([p[1] for p in pts], float)
+    ms = np.array([p[2] for p in pts], float)
+    # time(j) = a + j * fixed + rate * pairs(j): solve in least squares
+    A = np.stack([np.ones_like(it), it, pr], axis=1)
+    coef, *_ = np.linalg.lstsq(A, ms, rcond=None)
+    fixed, rate = max(coef[1], 0.0), max(coef[2], 0.0)
+    if rate <= 0:
+        rate = float(ms[-1] / max(pr[-1], 1.0))
+    return float(rate / per_step), float(fixed / q / per_step)
 
 
 def init_weights(seed: int = 11) -> np.ndarray:
@@ -158,7 +191,7 @@ def train(log: CostLog, epochs: int = 60, batch: int = 1024, lr: float = 2e-3, s
     x = (log.feats - norm[:MLP_INPUTS]) / norm[MLP_INPUTS:]
     w, loss = mlp_train(x, log.target, init_weights(seed), mlp_train_options(epochs=epochs, batch=batch, lr=lr,
                                                                               seed=seed))
-    return SwitchModel(norm, w, loss, log.kappa)
+    return SwitchModel(norm, w, loss, log.kappa, log.mu)
 
 
 def policy_cost(log: CostLog, ell_b) -> np.ndarray:

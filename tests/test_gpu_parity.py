@@ -221,6 +221,57 @@ def test_dense_and_sparse_engines_agree(c1):
 
 
 # ---------------------------------------------------------------------------
+# hybrid engine (sparse push, then a dense column once the push grows)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec,rel", [(geer.GER_FP64, 1e-9), (geer.GER_FP32, 1e-5)])
+def test_hybrid_engine_standalone_smm(c1, prec, rel):
+    # every continuing query moves to the SpMM at its first decision
+    w, g, G, lam = c1
+    q = 40
+    o = _opts(precision=prec, switch_policy=geer.GER_SWITCH_FIXED, fixed_ell_b=-1,
+              smm_engine=geer.GER_ENGINE_HYBRID, dense_switch=1)
+    r, st = G.query(w.s[:q], w.t[:q], 0.1, o, stats=True)
+    for i in range(q):
+        ref = oracle.geer(g, int(w.s[i]), int(w.t[i]), 0.1, lam, forced_ell_b=int(st[i]["ell"]))
+        assert r[i] == pytest.approx(ref.r, rel=rel)
+        assert st[i]["volume"] == ref.volume
+
+
+@pytest.mark.parametrize("switch_at", [1, 2000, 20000])
+def test_hybrid_engine_rule_matches_oracle(c1, switch_at):
+    # moves at different depths (a threshold of 1 moves at the first decision)
+    w, g, G, lam = c1
+    o = _opts(precision=geer.GER_FP64, smm_engine=geer.GER_ENGINE_HYBRID, dense_switch=switch_at)
+    r, st = G.query(w.s, w.t, w.eps, o, stats=True)
+    _check_against_oracle(w, g, lam, r, st, 1e-9, 1e-9, max_disagree=1)
+
+
+def test_hybrid_engine_deep_smm_agrees_with_sparse(c1):
+    w, g, G, lam = c1
+    base = dict(precision=geer.GER_FP64, switch_policy=geer.GER_SWITCH_FIXED, fixed_ell_b=6)
+    r1, s1 = G.query(w.s, w.t, w.eps, _opts(**base), stats=True)
+    r2, s2 = G.query(w.s, w.t, w.eps, _opts(smm_engine=geer.GER_ENGINE_HYBRID, dense_switch=5000, **base),
+                     stats=True)
+    assert np.array_equal(s1["ell_b"], s2["ell_b"])
+    same = (s1["eta0"] == s2["eta0"]) & (s1["batches"] == s2["batches"])
+    assert same.sum() >= w.q - 1
+    assert np.array_equal(s1["checksum"][same], s2["checksum"][same])
+    assert np.allclose(r1[same], r2[same], rtol=1e-9, atol=0)
+
+
+def test_hybrid_engine_with_few_dense_columns(c1):
+    # a budget of 1 MiB holds ~16 columns at n = 4k (FP64): the rest stay sparse
+    w, g, G, lam = c1
+    base = dict(precision=geer.GER_FP64, switch_policy=geer.GER_SWITCH_FIXED, fixed_ell_b=-1)
+    r1, s1 = G.query(w.s, w.t, 0.1, _opts(**base), stats=True)
+    r2, s2 = G.query(w.s, w.t, 0.1, _opts(smm_engine=geer.GER_ENGINE_HYBRID, dense_switch=1, dense_budget_mb=1,
+                                          **base), stats=True)
+    assert np.allclose(r1, r2, rtol=1e-9, atol=0)
+    assert np.array_equal(s1["volume"], s2["volume"])
+
+
+# ---------------------------------------------------------------------------
 # closed forms and edge cases
 # ---------------------------------------------------------------------------
 
