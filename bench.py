@@ -29,7 +29,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 os.environ.setdefault("GEER_SYNTH_CACHE", "/tmp/geer_synth_cache")
 
-METRIC = "ER queries/s at eps=0.05 (batched FP32 GEER)"
+METRIC = "ER queries/s at eps=0.05 (batched FP32 GEER, learned switch)"
+TRAIN_PAIRS, TRAIN_SEED = 2000, 5  # cost-log pairs of the learned switch (the bench pairs use seed 2)
 WALK_STEP_BYTES = 20  # row_ptr pair 8 B + one col_idx 4 B + one (s*, t*) FP32 pair 8 B
 # DRAM bytes (read + write) per dense_spmm launch from the ncu capture of the
 # current kernel on this workload (profiles/dense_spmm_c2_w128.md), per width.
@@ -194,6 +195,7 @@ def _config(w):
     return {"workload": f"{g.name}, largest component (n={g.n}, m={g.m}); {w.q} uniform pairs, eps={w.eps[0]:g}",
             "graph": g.name, "n": g.n, "m": g.m, "queries": w.q, "eps": float(w.eps[0]), "delta": 0.01, "tau": 5,
             "smm_vectors": "fp32", "series_and_statistics": "fp64",
+            "switch": f"learned 6-64-64-1 network trained on cost logs of {TRAIN_PAIRS} other pairs (seed {TRAIN_SEED})",
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
@@ -242,9 +244,30 @@ def main():
     e_d = torch.from_numpy(w.eps.astype(np.float64)).to(dev)
     r_d = torch.empty(w.q, dtype=torch.float64, device=dev)
     st_d = torch.empty(w.q * geer.STATS_DTYPE.itemsize, dtype=torch.uint8, device=dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    opts = geer.default_options()
+    # the learned SMM -> AMC switch: cost logs on separate pairs, the push price
+    # chosen by measured batch time; Eq. (17)'s rule when no network beats it
+    from paper_2312_06123_gb300 import switch
+    from synth import pairs as synth_pairs
+    t_sw = time.perf_counter()
+    s_tr, t_tr = synth_pairs.uniform_pairs(g.n, TRAIN_PAIRS, TRAIN_SEED)
+    eps0 = float(w.eps[0])
+    clog = switch.cost_log(G, s_tr, t_tr, eps0, g.degrees(), max_steps=8)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def flush_l2():
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+
+    # selection under the timed region's conditions (L2 flushed before each batch)
+    model, fit_times = switch.fit(G, s_tr, t_tr, eps0, clog, before=flush_l2)
+    sw_seconds = time.perf_counter() - t_sw
+    if model is not None:
+        G.set_switch_mlp(model.norm, model.weights)
+        opts = geer.default_options(switch_policy=geer.GER_SWITCH_MLP)
+    else:
+        opts = geer.default_options()
+    rule_opts = geer.default_options()
 
     def step():
         G.query_dev(s_d, t_d, e_d, r_d, st_d, opts, stream=stream.cuda_stream)
@@ -254,7 +277,6 @@ def main():
     torch.cuda.synchronize()
 
     clocks = Clocks(local)
-    geer.profile_enable(True)
     launches0 = geer.launch_count()
     barrier()
     clocks.start()
@@ -272,9 +294,17 @@ def main():
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = geer.launch_count() - launches0
+    barrier()
+    # per-kernel times from the same batches run again with CUDA events
+    # around every launch (kept out of the timed region above)
+    geer.profile_enable(True)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        step()
+    torch.cuda.synchronize()
     prof = geer.profile_read()
     geer.profile_enable(False)
-    barrier()
     total_ms = float(sum(ms))
     if dist is not None:
         tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
@@ -283,8 +313,24 @@ def main():
     value = world * w.q * args.steps / (total_ms / 1000.0)
     stats = np.frombuffer(st_d.cpu().numpy().tobytes(), dtype=geer.STATS_DTYPE)
 
+    # the same batch under Eq. (17)'s rule
+    rule_ms = []
+    for _ in range(0 if args.no_extras else 3 + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        G.query_dev(s_d, t_d, e_d, r_d, None, rule_opts, stream=stream.cuda_stream)
+        b.record(stream)
+        b.synchronize()
+        rule_ms.append(a.elapsed_time(b))
+    rule_value = world * w.q / (float(np.median(rule_ms[3:])) / 1000.0) if rule_ms else None
+
     # e2e: host buffers through ger_query_batch_eps, copies inside the timed region
     e2e_t = []
+    if not args.no_extras:
+        G.query(w.s, w.t, w.eps, opts)  # warm-up: the batch graph for these options
     for _ in range(0 if args.no_extras else args.steps):
         flush.fill_(1.0)
         torch.cuda.synchronize()
@@ -351,6 +397,12 @@ def main():
         "plain_fp64_per_query": None if plain_value is None else {
             "value": plain_value, "unit": "queries/s", "ms_per_step": float(np.mean(pt)),
             "speedup_of_batched_fp32": value / world / plain_value},
+        "switch": {"policy": "learned" if model is not None else "rule (no network beat it)",
+                   "kappa": None if model is None else model.kappa, "train_pairs": TRAIN_PAIRS,
+                   "train_seed": TRAIN_SEED, "cost_log_rows": int(clog.feats.shape[0]),
+                   "setup_seconds": sw_seconds,
+                   "train_batch_ms": {k: v * 1e3 for k, v in fit_times.items()},
+                   "rule_value": rule_value},
         "preprocess": {"spectral_bound_ms": pre_ms, "lambda": lam, "lambda_2": l2, "lambda_n": ln},
         "kernels": {k: {"launches": v[0], "total_ms": v[1]} for k, v in prof.items()},
         "work": {"walk_steps_per_step": walk_steps, "walk_pairs_per_step": int(stats["walks"].sum()),

@@ -78,7 +78,7 @@ typedef struct ger_options {
     int32_t  smm_engine;    /* GER_ENGINE_SPARSE (default), GER_ENGINE_DENSE or GER_ENGINE_HYBRID */
     int32_t  dense_width;   /* dense engine: columns per block (2 per query); 0: autotuned per graph */
     int64_t  dense_switch;  /* hybrid engine: push pairs at which a query moves to the SpMM; 0: nnz / 16 */
-    int32_t  dense_budget_mb; /* hybrid engine: device memory for dense columns (MiB); 0: 8192 */
+    int32_t  dense_budget_mb; /* hybrid engine: device memory for dense columns (MiB); 0: half the free memory */
     int32_t  reserved0;
 } ger_options;
 

@@ -633,7 +633,16 @@ static void issue_amc(ger_graph* g, AmcArgs m, int64_t nq, cudaStream_t st) {
 // Dense columns of the hybrid engine for a batch of nq queries: as many as
 // the memory budget holds (two buffers of n values per column), at most nq.
 static int64_t hybrid_columns(const ger_graph* g, const ger_options& o, int64_t nq) {
-    const int64_t budget = (int64_t)(o.dense_budget_mb > 0 ? o.dense_budget_mb : 8192) << 20;
+    int64_t budget = (int64_t)o.dense_budget_mb << 20;
+    if (budget <= 0) {
+        // default: half of the free device memory (dense buffers already held count as free)
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            fr = 0;
+        }
+        budget = ((int64_t)fr + 2 * (int64_t)g->ws.dX_bytes) / 2;
+    }
     const int64_t per = 2 * g->n * (o.precision == GER_FP64 ? 8 : 4);
     return std::min<int64_t>(nq, budget / std::max<int64_t>(per, 1));
 }
@@ -695,7 +704,7 @@ static void issue_smm_start(ger_graph* g, Engine& E, bool fp64, cudaStream_t st)
         launch_smm_setup(E.a, st);
         launch_smm_alloc(E.a, st);
         issue_dense_start(g, E.d, fp64, E.cols, st);
-        launch_smm_decide(E.a, st);
+        launch_smm_decide(E.a, st, true);
     } else {
         if (E.hybrid) cudaMemsetAsync(g->ws.dblock_q, 0xff, E.d.nblocks * (size_t)(E.d.width / 2) * sizeof(int32_t), st);
         launch_smm_start(fp64, E.a, E.grid, st);

@@ -120,7 +120,7 @@ void launch_smm_seed(const SmmArgs& a, cudaStream_t st);
 void launch_smm_push(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 void launch_smm_finish(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 void launch_smm_top2(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
-void launch_smm_decide(const SmmArgs& a, cudaStream_t st);
+void launch_smm_decide(const SmmArgs& a, cudaStream_t st, bool first = false);
 void launch_smm_mlp(const SmmArgs& a, cudaStream_t st);  // the learned switch's call per query
 void launch_smm_advance(const SmmArgs& a, cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st);
 void launch_smm_start(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);

@@ -679,9 +679,10 @@ void launch_smm_top2(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
     note_launches(1);
 }
 
-void launch_smm_decide(const SmmArgs& a, cudaStream_t st) {
+void launch_smm_decide(const SmmArgs& a, cudaStream_t st, bool first) {
     const int grid = (int)std::min<int64_t>((a.nq + 255) / 256, 1024);
-    if (a.policy == 1 && a.mlp_w != nullptr) launch_smm_mlp(a, st);
+    // the first decision (l_b = 0) is the rule's "run at least once"
+    if (!first && a.policy == 1 && a.mlp_w != nullptr) launch_smm_mlp(a, st);
     prof_begin(FAM_SMM_DECIDE, st);
     smm_decide_kernel<<<grid, 256, 0, st>>>(a);
     prof_end(FAM_SMM_DECIDE, st);
@@ -713,7 +714,7 @@ void launch_smm_start(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
     launch_smm_seed(a, st);
     launch_smm_finish(fp64, a, grid, st);
     launch_smm_top2(fp64, a, grid, st);
-    launch_smm_decide(a, st);
+    launch_smm_decide(a, st, true);
 }
 
 }  // namespace geer

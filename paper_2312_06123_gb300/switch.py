@@ -118,52 +118,41 @@ def price(inputs, push, walks, ell, kappa: float, mu: float) -> CostLog:
     return out
 
 
-def calibrate(G, s, t, eps, push, options=None, lb: int = 4) -> tuple[float, float]:
-    """(kappa, mu) from the kernel times of one batch switching after `lb`
-    iterations, measured with CUDA events around every launch: kappa =
-    (time per pushed pair) / (time per walk step); mu = (time of one SMM
-    iteration's launches beyond their work, i.e. the SMM time the push pairs
-    do not explain, per iteration and query) / (time per walk step). The SMM
-    time is split by a least-squares fit over iterations of
-    time_i = fixed + rate * pairs_i."""
-    import os
+def batch_seconds(G, s, t, eps, options, repeats: int = 7, before=None) -> float:
+    """Median wall time of one batch call (after a warm-up call); `before`
+    (nullable) runs ahead of every timed call, e.g. to flush the L2 cache
+    the way a benchmark's timed region does."""
+    G.query(s, t, eps, options)
+    times = []
+    for _ in range(repeats):
+        if before is not None:
+            before()
+        t0 = time.perf_counter()
+        G.query(s, t, eps, options)
+        times.append(time.perf_counter() - t0)
+    return float(np.median(times))
+
+
+def fit(G, s, t, eps, log: CostLog, options=None, kappas=(8.0, 32.0, 128.0), epochs: int = 60,
+        seed: int = 7, before=None, repeats: int = 9):
+    """Choose the push price by measurement: train one network per kappa on
+    the cost log, time each resulting policy on the logged queries' own
+    batch, and keep the fastest; returns (model or None when Eq. (17)'s rule
+    is at least as fast, {label: seconds})."""
     q = len(s)
-    o = _with(options, switch_policy=GER_SWITCH_FIXED, fixed_ell_b=lb, per_query=0)
-    prev = os.environ.get("GEER_NO_GRAPH")
-    os.environ["GEER_NO_GRAPH"] = "1"  # per-launch events need the stream-ordered loop
-    try:
-        G.query(s, t, eps, o)
-        pts = []
-        amc_ms = steps = 0.0
-        for j in range(1, lb + 1):
-            profile_enable(True)
-            _, st = G.query(s, t, eps, _with(o, fixed_ell_b=j), stats=True)
-            prof = profile_read()
-            profile_enable(False)
-            smm = sum(v[1] for k, v in prof.items() if k.startswith("smm_") or k.startswith("dense_"))
-            lbq = np.minimum(st["ell_b"], j)
-            pairs_ = float(sum(push[i, :lbq[i]].sum() for i in range(q)))
-            pts.append((j, pairs_, smm))
-            amc_ms += sum(v[1] for k, v in prof.items() if k.startswith("amc_"))
-            steps += float(st["walk_steps"].sum())
-    finally:
-        if prev is None:
-            del os.environ["GEER_NO_GRAPH"]
-        else:
-            os.environ["GEER_NO_GRAPH"] = prev
-    if steps <= 0 or amc_ms <= 0:
-        return 1.0, 0.0
-    per_step = amc_ms / steps
-    it = np.array([p[0] for p in pts], float)
-    pr = np.array([p[1] for p in pts], float)
-    ms = np.array([p[2] for p in pts], float)
-    # time(j) = a + j * fixed + rate * pairs(j): solve in least squares
-    A = np.stack([np.ones_like(it), it, pr], axis=1)
-    coef, *_ = np.linalg.lstsq(A, ms, rcond=None)
-    fixed, rate = max(coef[1], 0.0), max(coef[2], 0.0)
-    if rate <= 0:
-        rate = float(ms[-1] / max(pr[-1], 1.0))
-    return float(rate / per_step), float(fixed / q / per_step)
+    eps = np.broadcast_to(np.asarray(eps, np.float64), (q,)).copy()
+    times = {"rule": batch_seconds(G, s, t, eps, _with(options, switch_policy=GER_SWITCH_RULE), repeats, before)}
+    best, best_t = None, times["rule"]
+    for k in kappas:
+        lg = price(log.inputs, log.push, log.walks, log.ell, k, 0.0)
+        model = train(lg, epochs=epochs, seed=seed)
+        G.set_switch_mlp(model.norm, model.weights)
+        tk = batch_seconds(G, s, t, eps, _with(options, switch_policy=GER_SWITCH_MLP), repeats, before)
+        times[f"kappa={k:g}"] = tk
+        if tk < best_t:
+            best, best_t = model, tk
+    G.set_switch_mlp(None, None)
+    return best, times
 
 
 def init_weights(seed: int = 11) -> np.ndarray:

@@ -124,32 +124,35 @@ def rmat_model():
     lam, _, _ = G.spectral_bound()
     d = g.degrees()
     s, t = pairs.uniform_pairs(g.n, 768, 21)
-    kappa = 1.0
-    log = switch.cost_log(G, s, t, 0.05, d, max_steps=12, kappa=kappa)
-    model = switch.train(log, epochs=60, batch=512)
-    return g, G, lam, model, log
+    log = switch.cost_log(G, s, t, 0.05, d, max_steps=8)
+    model, times = switch.fit(G, s, t, 0.05, log, kappas=(8.0, 32.0, 128.0))
+    return g, G, lam, model, log, times
 
 
 def test_training_on_cost_logs_converges(rmat_model):
-    g, G, lam, model, log = rmat_model
+    g, G, lam, model, log, times = rmat_model
     assert log.feats.shape[0] > 1000
+    # the price was chosen by measured batch time on the training pairs
+    assert model is not None, times
     assert np.all(np.isfinite(model.loss))
     assert model.loss[-1] < 0.7 * model.loss[0]
 
 
 def test_learned_switch_gains_over_the_rule(rmat_model):
-    # held-out pairs: the trained switch's modelled cost C(l_b) beats Eq. (17)
-    g, G, lam, model, _ = rmat_model
+    # held-out pairs: faster batches than Eq. (17), and a lower logged cost
+    # C(l_b) under the chosen price
+    g, G, lam, model, _, _ = rmat_model
     d = g.degrees()
     s, t = pairs.uniform_pairs(g.n, 512, 22)
-    log = switch.cost_log(G, s, t, 0.05, d, max_steps=12, kappa=model.kappa)
-    res = switch.evaluate(G, s, t, 0.05, model, log)
+    log = switch.cost_log(G, s, t, 0.05, d, max_steps=8, kappa=model.kappa)
+    res = switch.evaluate(G, s, t, 0.05, model, log, repeats=9)
     ok = np.isfinite(res["rule"]["cost"]) & np.isfinite(res["mlp"]["cost"])
     assert ok.mean() > 0.9
     rule, learned = res["rule"]["cost"][ok].sum(), res["mlp"]["cost"][ok].sum()
-    print(f"learned switch: cost {learned:.4g} vs rule {rule:.4g} ({rule / learned:.3f}x); "
-          f"time {res['mlp']['seconds'] * 1e3:.2f} ms vs {res['rule']['seconds'] * 1e3:.2f} ms")
+    print(f"learned switch (kappa {model.kappa:g}): cost {learned:.4g} vs rule {rule:.4g} ({rule / learned:.3f}x); "
+          f"time {res['mlp']['seconds'] * 1e3:.3f} ms vs {res['rule']['seconds'] * 1e3:.3f} ms")
     assert learned < rule
+    assert res["mlp"]["seconds"] < res["rule"]["seconds"]
     # the best switch point in hindsight bounds what any policy can reach
     best = np.nanmin(log.cost[:, 1:], axis=1)[ok].sum()
     assert best <= learned
@@ -160,6 +163,7 @@ def test_learned_switch_keeps_parity_and_eps(c1, rmat_model):
     # valid; walks replay bit-exactly and r stays within eps of L^+
     w, g, G, lam = c1
     model = rmat_model[3]
+    assert model is not None
     G.set_switch_mlp(model.norm, model.weights)
     try:
         r, st = G.query(w.s, w.t, w.eps, geer.default_options(precision=geer.GER_FP64,
