@@ -71,27 +71,35 @@ def _with(o, **kw):
 
 
 def cost_log(G, s, t, eps, degrees, options=None, max_steps: int = 12, kappa: float = 1.0, mu: float = 0.0,
-             engine: int = GER_ENGINE_DENSE) -> CostLog:
+             engine: int = GER_ENGINE_DENSE, chunk: int = 512) -> CostLog:
     """Log the inputs after every SMM iteration j <= max_steps (one traced
     batch) and the walk steps of switching after j (one batch per j), and
     turn them into training rows priced with (kappa, mu). The logging runs
-    use `engine` (dense by default: their SMM goes deep); the logged values
-    do not depend on it."""
+    use `engine` (dense by default: their SMM goes deep), `chunk` queries at
+    a time; the logged values do not depend on either. A query's walks
+    depend on its index in the submitted batch (the walk RNG key), so the
+    log describes the chunked indexing."""
     options = _with(options, smm_engine=engine)
     s = np.asarray(s, np.int32)
     t = np.asarray(t, np.int32)
     q = len(s)
     eps = np.broadcast_to(np.asarray(eps, np.float64), (q,)).copy()
-    log, st = G.smm_trace(s, t, eps, options, max_steps)
-    ell = st["ell"].astype(np.int64)
+    inputs = np.zeros((q, max_steps, MLP_INPUTS), np.float32)
     push = np.zeros((q, max_steps + 1))
-    push[:, 0] = degrees[s].astype(np.float64) + degrees[t]
-    push[:, 1:] = log[:, :, 6]
     walks = np.full((q, max_steps + 1), np.nan)
-    for j in range(1, max_steps + 1):
-        _, sj = G.query(s, t, eps, _with(options, switch_policy=GER_SWITCH_FIXED, fixed_ell_b=j), stats=True)
-        walks[:, j] = sj["walk_steps"]
-    return price(log[:, :, :MLP_INPUTS].copy(), push, walks, ell, kappa, mu)
+    ell = np.zeros(q, np.int64)
+    for a in range(0, q, chunk):
+        b = min(q, a + chunk)
+        log, st = G.smm_trace(s[a:b], t[a:b], eps[a:b], options, max_steps)
+        ell[a:b] = st["ell"]
+        inputs[a:b] = log[:, :, :MLP_INPUTS]
+        push[a:b, 0] = degrees[s[a:b]].astype(np.float64) + degrees[t[a:b]]
+        push[a:b, 1:] = log[:, :, 6]
+        for j in range(1, max_steps + 1):
+            _, sj = G.query(s[a:b], t[a:b], eps[a:b], _with(options, switch_policy=GER_SWITCH_FIXED, fixed_ell_b=j),
+                            stats=True)
+            walks[a:b, j] = sj["walk_steps"]
+    return price(inputs, push, walks, ell, kappa, mu)
 
 
 def price(inputs, push, walks, ell, kappa: float, mu: float) -> CostLog:
