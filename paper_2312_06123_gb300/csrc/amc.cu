@@ -30,6 +30,19 @@ namespace {
 
 }  // namespace
 
+// Row start and degree of node w.
+__device__ __forceinline__ uint2 node_row(const DevGraph& g, int32_t w) {
+    if (g.node_info) return __ldg(g.node_info + w);
+    const int64_t rs = __ldg(g.row_ptr + w);
+    return make_uint2((uint32_t)rs, (uint32_t)(__ldg(g.row_ptr + w + 1) - rs));
+}
+
+__device__ __forceinline__ const int32_t* row_base(const DevGraph& g, int32_t w, uint2 info) {
+    // node_info holds the low 32 bits of the row start (nnz < 2^32); otherwise
+    // re-read the full 64-bit start
+    return g.node_info ? g.col_idx + info.x : g.col_idx + __ldg(g.row_ptr + w);
+}
+
 // Chunk layout of the next batch for every query still in AMC, by one CTA:
 // per query ppc (walk pairs per chunk) and its chunk count, and their prefix
 // in chunk_begin. Reads the query
@@ -54,6 +67,9 @@ __device__ void schedule_cta(const AmcArgs& a) {
                 const int64_t ppc = unit * ((units + c - 1) / c);
                 nch = (eta + ppc - 1) / ppc;
                 Q->ppc = ppc;
+                // the rest of the walk record was packed when the query entered AMC
+                a.wq[q].eta = eta;
+                a.wq[q].ppc = ppc;
             }
             Q->nchunks = nch;
         }
@@ -64,23 +80,13 @@ __device__ void schedule_cta(const AmcArgs& a) {
         if (tid == 0) carry += tot;
         __syncthreads();
     }
-    if (tid == 0) a.chunk_begin[a.nq] = carry;
+    if (tid == 0) {
+        a.chunk_begin[a.nq] = carry;
+        *a.walk_ctr = 0ull;
+    }
 }
 
 __global__ void __launch_bounds__(kCta) amc_schedule_kernel(AmcArgs a) { schedule_cta(a); }
-
-// Row start and degree of node w.
-__device__ __forceinline__ uint2 node_row(const DevGraph& g, int32_t w) {
-    if (g.node_info) return __ldg(g.node_info + w);
-    const int64_t rs = __ldg(g.row_ptr + w);
-    return make_uint2((uint32_t)rs, (uint32_t)(__ldg(g.row_ptr + w + 1) - rs));
-}
-
-__device__ __forceinline__ const int32_t* row_base(const DevGraph& g, int32_t w, uint2 info) {
-    // node_info holds the low 32 bits of the row start (nnz < 2^32); otherwise
-    // re-read the full 64-bit start
-    return g.node_info ? g.col_idx + info.x : g.col_idx + __ldg(g.row_ptr + w);
-}
 
 // g of a node whose first probe `p` (slot h) is already loaded
 __device__ __forceinline__ double resolve_g(const GEntry* tab, int32_t mask, int32_t v, int4 p, uint32_t h) {
@@ -98,7 +104,7 @@ __device__ __forceinline__ double resolve_g(const GEntry* tab, int32_t mask, int
 // row record and its first lookup probe together.
 constexpr int kSmemChunkBegin = 2048;  // chunk_begin entries staged in shared memory
 #ifndef GEER_WALK_MINB
-#define GEER_WALK_MINB 5
+#define GEER_WALK_MINB 4
 #endif
 
 template <int W>
@@ -111,30 +117,34 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
     const int64_t* cb_arr = staged ? cbeg : a.chunk_begin;
     const int lane = threadIdx.x & 31;
     const int sigma = lane & 1;
-    const int64_t total = a.chunk_begin[a.nq];
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t total = cb_arr[a.nq];
     const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
     const DevGraph g = a.g;
     const uint32_t lane_ctr = (uint32_t)(2 * (a.batch - 1) + sigma);
-    for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < total; c += nw) {
+    for (;;) {
+        // chunks are handed out in order by a ticket counter
+        unsigned long long ticket = 0;
+        if (lane == 0) ticket = atomicAdd(a.walk_ctr, 1ull);
+        const int64_t c = (int64_t)__shfl_sync(0xffffffffu, ticket, 0);
+        if (c >= total) break;
         // owning query: last q with chunk_begin[q] <= c
         int lo = 0, hi = a.nq + 1;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
             if (cb_arr[mid] <= c) lo = mid + 1; else hi = mid;
         }
-        const QState* Q = a.st + (lo - 1);
+        const WalkQ* WQ = a.wq + (lo - 1);
         const int64_t cb = cb_arr[lo - 1];
-        const int64_t eta = Q->eta, ppc = Q->ppc;
-        const int32_t lf = Q->lf, qidx = Q->qidx;
-        const int32_t start = sigma ? Q->t : Q->s;
-        const GEntry* tab = a.pool + Q->table_off;
-        const int32_t mask = Q->table_mask;
+        const int64_t eta = WQ->eta, ppc = WQ->ppc;
+        const int32_t lf = WQ->lf, qidx = WQ->qidx;
+        const int32_t start = sigma ? WQ->t : WQ->s;
+        const GEntry* tab = a.pool + WQ->table_off;
+        const int32_t mask = WQ->mask;
         // dense-engine queries: (s*, t*) read directly from their block column
-        const char* dvals = reinterpret_cast<const char*>(Q->dense_vals);
-        const int64_t dstride = Q->dense_stride;
-        const double inv_ds = 1.0 / (double)Q->ds, inv_dt = 1.0 / (double)Q->dt;
-        const uint2 start_info = node_row(g, start);
+        const char* dvals = reinterpret_cast<const char*>(WQ->dvals);
+        const int64_t dstride = WQ->dstride;
+        const double inv_ds = WQ->inv_ds, inv_dt = WQ->inv_dt;
+        const uint2 start_info = sigma ? WQ->t_info : WQ->s_info;
         const int64_t k_lo = (c - cb) * ppc;
         const int64_t k_hi = min(k_lo + ppc, eta);
         double sz = 0.0, sz2 = 0.0;
@@ -155,7 +165,52 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
                 inf[i] = start_info;
                 r[i] = make_uint4(0, 0, 0, 0);
             }
-            if (act[0]) {
+            if (act[0] && g.edge_rec && mask >= 0) {
+                // one dependent load per step: the edge record of the chosen
+                // neighbour carries that neighbour's row; the lookup probe of
+                // step j is resolved during step j + 1's load. The W walks of
+                // the lane advance together so that their loads overlap.
+                uint2 cur[W];
+                int32_t pnx[W];
+                uint32_t phh[W];
+                int4 ppr[W];
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    cur[i] = start_info;
+                    pnx[i] = start;
+                    phh[i] = 0;
+                    ppr[i] = make_int4(0, 0, 0, 0);
+                }
+                for (int j = 1; j <= lf; ++j) {
+                    const int sub = (j - 1) & 3;
+                    uint4 rec[W];
+#pragma unroll
+                    for (int i = 0; i < W; ++i) {
+                        if (sub == 0)
+                            r[i] = philox4x32_10(
+                                make_uint4((uint32_t)k[i], lane_ctr, (uint32_t)qidx, (uint32_t)((j - 1) >> 2)), key);
+                        const uint32_t d = sub == 0 ? r[i].x : (sub == 1 ? r[i].y : (sub == 2 ? r[i].z : r[i].w));
+                        rec[i] = act[i] ? __ldg(g.edge_rec + cur[i].x + __umulhi(d, cur[i].y))
+                                        : make_uint4((uint32_t)start, start_info.x, start_info.y, 0u);
+                    }
+#pragma unroll
+                    for (int i = 0; i < W; ++i)
+                        if (j > 1 && act[i]) z[i] += resolve_g(tab, mask, pnx[i], ppr[i], phh[i]);
+#pragma unroll
+                    for (int i = 0; i < W; ++i) {
+                        pnx[i] = (int32_t)rec[i].x;
+                        cur[i] = make_uint2(rec[i].y, rec[i].z);
+                        phh[i] = hash32(rec[i].x) & (uint32_t)mask;
+                        ppr[i] = __ldg(reinterpret_cast<const int4*>(tab + phh[i]));
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    if (lf > 0 && act[i]) z[i] += resolve_g(tab, mask, pnx[i], ppr[i], phh[i]);
+                    w[i] = pnx[i];
+                    if (act[i]) cs += walk_hash(w[i], k[i], sigma, a.batch);
+                }
+            } else if (act[0]) {
                 for (int j = 1; j <= lf; ++j) {
                     const int sub = (j - 1) & 3;
                     int32_t nx[W];
@@ -292,9 +347,34 @@ void launch_amc_schedule(const AmcArgs& a, cudaStream_t st) {
     prof_end(FAM_AMC_SCHEDULE, st);
 }
 
-void launch_amc_walk(const AmcArgs& a, int grid, cudaStream_t st) {
+__global__ void edge_records_kernel(const int32_t* col_idx, const uint2* node_info, int64_t nnz, uint4* out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = col_idx[e];
+        const uint2 inf = node_info[v];
+        out[e] = make_uint4((uint32_t)v, inf.x, inf.y, 0u);
+    }
+}
+
+void launch_edge_records(const int32_t* col_idx, const uint2* node_info, int64_t nnz, uint4* out, cudaStream_t st) {
+    if (nnz <= 0) return;
+    edge_records_kernel<<<(int)std::min<int64_t>((nnz + 255) / 256, 152 * 32), 256, 0, st>>>(col_idx, node_info, nnz,
+                                                                                           out);
+    note_launches(1);
+}
+
+void launch_amc_walk(const AmcArgs& a, int sm_count, cudaStream_t st) {
+    static int per_sm = 0;  // resident CTAs per SM of the walk kernel
+    if (per_sm == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, amc_walk_kernel<kWalksPerLane>, 256, 0) != cudaSuccess ||
+            b < 1) {
+            cudaGetLastError();
+            b = 1;
+        }
+        per_sm = b;
+    }
     prof_begin(FAM_AMC_WALK, st);
-    amc_walk_kernel<kWalksPerLane><<<grid, 256, 0, st>>>(a);
+    amc_walk_kernel<kWalksPerLane><<<sm_count * per_sm, 256, 0, st>>>(a);
     prof_end(FAM_AMC_WALK, st);
 }
 

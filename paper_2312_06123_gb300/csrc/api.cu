@@ -139,6 +139,7 @@ struct Workspace {
     double* r = nullptr;
     ger_query_stats* stats = nullptr;
     int64_t* chunk_begin = nullptr;
+    WalkQ* wq = nullptr;
     Partial* partial = nullptr;
     int64_t partial_cap = 0;
     // SMM phase
@@ -207,6 +208,7 @@ struct ger_graph {
     int64_t* row_ptr = nullptr;
     int32_t* col_idx = nullptr;
     uint2* node_info = nullptr;  // {first edge, degree} per node when nnz < 2^32
+    uint4* edge_rec = nullptr;   // {neighbour, its first edge, its degree, 0} per edge (walks)
     bool has_lambda = false;
     double lambda = 0, lam2 = 0, lamn = 0;
     cudaStream_t stream = nullptr;
@@ -228,6 +230,7 @@ namespace geer {
 static void free_ws(Workspace& w) {
     cudaFree(w.st); cudaFree(w.s); cudaFree(w.t); cudaFree(w.eps); cudaFree(w.r); cudaFree(w.stats);
     cudaFree(w.chunk_begin); cudaFree(w.partial); cudaFree(w.qsmm); cudaFree(w.seg_q); cudaFree(w.seg_off);
+    cudaFree(w.wq);
     cudaFree(w.ctl); cudaFree(w.ent); cudaFree(w.sums); cudaFree(w.yvals); cudaFree(w.counters);
     cudaFree(w.heavy);
     cudaFree(w.dX[0]); cudaFree(w.dX[1]);
@@ -246,7 +249,7 @@ static cudaError_t alloc(T** p, size_t count) {
 static int ensure_ws(ger_graph* g, int64_t q, int64_t pool_cap) {
     Workspace& w = g->ws;
     if (!w.counters) {
-        GER_CUDA(alloc(&w.counters, 4));
+        GER_CUDA(alloc(&w.counters, 8));  // [1] error flag, [2] reduce CTA counter, [4..5] walk ticket
         GER_CUDA(alloc(&w.ctl, 1));
         GER_CUDA(alloc(&w.heavy, kHeavyCap));
         GER_CUDA(cudaMallocHost(reinterpret_cast<void**>(&w.host_rb), 4 * sizeof(int64_t)));
@@ -254,14 +257,16 @@ static int ensure_ws(ger_graph* g, int64_t q, int64_t pool_cap) {
     if (q > w.q_cap) {
         cudaFree(w.st); cudaFree(w.s); cudaFree(w.t); cudaFree(w.eps); cudaFree(w.r); cudaFree(w.stats);
         cudaFree(w.chunk_begin); cudaFree(w.partial); cudaFree(w.qsmm); cudaFree(w.seg_q); cudaFree(w.seg_off);
+        cudaFree(w.wq);
         w.st = nullptr; w.s = nullptr; w.t = nullptr; w.eps = nullptr; w.r = nullptr; w.stats = nullptr;
         w.chunk_begin = nullptr; w.partial = nullptr; w.qsmm = nullptr; w.seg_q = nullptr; w.seg_off = nullptr;
+        w.wq = nullptr;
         w.q_cap = 0;
         const int64_t qc = std::max<int64_t>(q, 64);
         const int64_t pc = qc * kMaxChunksPerQuery;
         if (alloc(&w.st, qc) || alloc(&w.s, qc) || alloc(&w.t, qc) || alloc(&w.eps, qc) || alloc(&w.r, qc) ||
             alloc(&w.stats, qc) || alloc(&w.chunk_begin, qc + 1) || alloc(&w.partial, pc) ||
-            alloc(&w.qsmm, qc) || alloc(&w.seg_q, 2 * qc) || alloc(&w.seg_off, 2 * (qc + 1))) {
+            alloc(&w.qsmm, qc) || alloc(&w.seg_q, 2 * qc) || alloc(&w.seg_off, 2 * (qc + 1)) || alloc(&w.wq, qc)) {
             cudaGetLastError();
             return fail(GER_ERR_OOM, "workspace for %lld queries", (long long)q);
         }
@@ -371,7 +376,7 @@ static int validate_csr(int64_t n, const int64_t* rp, const int32_t* ci) {
 
 static int ensure_lambda(ger_graph* g) {
     if (g->has_lambda) return GER_OK;
-    DevGraph dg{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info};
+    DevGraph dg{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info, g->edge_rec};
     double l2 = 0, ln = 0;
     int steps = 0;
     const int rc = lanczos_spectral_bound(dg, 300, 1e-13, g->stream, &l2, &ln, &steps);
@@ -514,7 +519,7 @@ static int ensure_dense(ger_graph* g, int64_t nq, int width, bool fp64) {
 static DenseArgs make_dense_args(ger_graph* g, int64_t q0, int64_t nq, int width, bool fp64) {
     Workspace& w = g->ws;
     DenseArgs d;
-    d.g = DevGraph{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info};
+    d.g = DevGraph{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info, g->edge_rec};
     d.width = width;
     d.nblocks = (int32_t)((nq + width / 2 - 1) / (width / 2));
     d.X[0] = w.dX[0];
@@ -554,7 +559,7 @@ static void issue_dense_start(ger_graph* g, const DenseArgs& d, bool fp64, int64
 // Launch arguments of the SMM and AMC phases for queries [q0, q0 + nq).
 static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool fp64, SmmArgs* pa, AmcArgs* pm) {
     Workspace& w = g->ws;
-    DevGraph dg{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info};
+    DevGraph dg{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info, g->edge_rec};
     SmmArgs& a = *pa;
     a.g = dg;
     a.nq = (int32_t)nq;
@@ -597,6 +602,7 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
     a.dense_X[1] = w.dX[1];
     a.ctl = w.ctl;
     a.err_flag = w.counters + 1;
+    a.wq = w.wq + q0;
     a.mlp_norm = g->mlp_norm;
     a.mlp_w = p.o.switch_policy == GER_SWITCH_MLP ? g->mlp_w : nullptr;
     a.trace = p.trace ? p.trace + q0 * (int64_t)p.trace_steps * kTraceWidth : nullptr;
@@ -606,6 +612,8 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
     m.nq = (int32_t)nq;
     m.st = w.st + q0;
     m.chunk_begin = w.chunk_begin;
+    m.wq = w.wq + q0;
+    m.walk_ctr = reinterpret_cast<unsigned long long*>(w.counters + 4);
     m.done = reinterpret_cast<unsigned int*>(w.counters + 2);
     m.partial = w.partial;
     m.partial_cap = w.partial_cap;
@@ -619,12 +627,12 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
 
 // The tau AMC rounds (schedule -> walks -> batch statistics).
 static void issue_amc(ger_graph* g, AmcArgs m, int64_t nq, cudaStream_t st) {
-    const int walk_grid = nq == 1 ? g->sm_count * 2 : g->sm_count * 8;
+
     m.batch = 1;
     launch_amc_schedule(m, st);
     for (int b = 1; b <= m.tau; ++b) {
         m.batch = b;
-        launch_amc_walk(m, walk_grid, st);
+        launch_amc_walk(m, g->sm_count, st);
         launch_amc_reduce(m, st);  // its last CTA lays out batch b + 1
     }
     note_launches(1 + 2 * m.tau);
@@ -949,7 +957,7 @@ static int run_batch(ger_graph* g, Plan& p) {
 // translation units.
 int graph_view(const ger_graph* g, DevGraph* dg, double* lambda, bool* has_lambda, int* device, int* sm_count) {
     if (!g) return fail(GER_ERR_INVALID, "null graph");
-    *dg = DevGraph{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info};
+    *dg = DevGraph{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info, g->edge_rec};
     *lambda = g->lambda;
     *has_lambda = g->has_lambda;
     *device = g->device;
@@ -1064,6 +1072,28 @@ int ger_load_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int 
             ger_free(g);
             return fail(GER_ERR_OOM, "device copy of the node records");
         }
+        // the walks' edge records: 16 B per stored edge; without them the
+        // walks take two dependent loads per step instead of one
+        // when col_idx and the node records fit in L2 they serve the walk's two
+        // dependent loads from L2, faster than one DRAM load of an edge record
+        int l2 = 0;
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
+        const char* rec_env = std::getenv("GEER_EDGE_RECORDS");  // 0 / 1 override the size rule
+        bool want_rec = 4 * g->nnz + 8 * n > (int64_t)l2;
+        if (rec_env && rec_env[0]) want_rec = rec_env[0] != '0';
+        if (!want_rec) {
+            g->edge_rec = nullptr;
+        } else if (cudaMalloc(&g->edge_rec, (size_t)std::max<int64_t>(g->nnz, 1) * sizeof(uint4)) == cudaSuccess) {
+            launch_edge_records(g->col_idx, g->node_info, g->nnz, g->edge_rec, g->stream);
+            if (cudaStreamSynchronize(g->stream) != cudaSuccess) {
+                cudaGetLastError();
+                ger_free(g);
+                return fail(GER_ERR_CUDA, "building the edge records");
+            }
+        } else {
+            cudaGetLastError();
+            g->edge_rec = nullptr;
+        }
         if (n < INT32_MAX) {
             std::vector<int4> units, heavy;
             int32_t nslots = 0;
@@ -1096,6 +1126,7 @@ void ger_free(ger_graph* g) {
     cudaFree(g->row_ptr);
     cudaFree(g->col_idx);
     cudaFree(g->node_info);
+    cudaFree(g->edge_rec);
     cudaFree(g->dense_units);
     cudaFree(g->dense_heavy);
     cudaFree(g->mlp_w);

@@ -87,6 +87,20 @@ struct SmmCtl {
     int32_t dense_next, n_mig, dense_open, pad2;
 };
 
+// What a walk chunk needs of its query, packed by the batch schedule (one
+// record per query in AMC).
+struct __align__(16) WalkQ {
+    int32_t s, t;
+    uint2 s_info, t_info;     // {first edge, degree} of s and t
+    int32_t lf, qidx;
+    int64_t eta, ppc;         // walk pairs of this batch, pairs per chunk
+    int64_t table_off;        // lookup table (mask >= 0) ...
+    int32_t mask, dstride;
+    const void* dvals;        // ... or the query's dense column (mask < 0)
+    double inv_ds, inv_dt;
+    int64_t pad;
+};
+
 // Per-chunk partial sums of the walk kernel.
 struct Partial {
     double sz, sz2;
@@ -99,6 +113,9 @@ struct DevGraph {
     const int64_t* row_ptr;
     const int32_t* col_idx;
     const uint2* node_info;  // per node {first edge, degree} when nnz < 2^32, else null
+    // per edge e = (u, v): {v, first edge of v, degree of v, 0} (null when absent): a walk
+    // step's one load brings the next step's row as well
+    const uint4* edge_rec = nullptr;
 };
 
 // ---------------------------------------------------------------------------

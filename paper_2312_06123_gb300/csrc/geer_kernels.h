@@ -53,6 +53,7 @@ struct SmmArgs {
     // cost log: per query and SMM iteration 1..trace_steps, kTraceWidth floats
     float* trace = nullptr;
     int32_t trace_steps = 0;
+    WalkQ* wq = nullptr;  // walk records, packed for the queries that enter AMC
 };
 
 // Columns of one cost-log row: the six switch inputs, the union frontier's
@@ -94,6 +95,8 @@ struct AmcArgs {
     int32_t nq;
     QState* st;
     int64_t* chunk_begin;  // nq + 1
+    WalkQ* wq;             // nq walk records, packed by the schedule
+    unsigned long long* walk_ctr;  // next chunk of the batch (reset by the schedule)
     unsigned int* done;    // CTA counter of the fused reduce (last CTA schedules)
     Partial* partial;
     int64_t partial_cap;
@@ -139,7 +142,10 @@ void launch_dense_iteration(bool fp64, const DenseArgs& d, cudaStream_t st);
 // tables of the queries the last decision moved into their dense columns
 void launch_dense_migrate(bool fp64, const DenseArgs& d, const SmmArgs& a, cudaStream_t st);
 void launch_amc_schedule(const AmcArgs& a, cudaStream_t st);
-void launch_amc_walk(const AmcArgs& a, int grid, cudaStream_t st);
+// edge e -> {col_idx[e], node_info[col_idx[e]], 0}
+void launch_edge_records(const int32_t* col_idx, const uint2* node_info, int64_t nnz, uint4* out, cudaStream_t st);
+// one persistent grid (as many CTAs as fit on the GPU) over the batch's chunks
+void launch_amc_walk(const AmcArgs& a, int sm_count, cudaStream_t st);
 // batch statistics of batch a.batch; the last CTA schedules batch a.batch + 1
 void launch_amc_reduce(const AmcArgs& a, cudaStream_t st);
 

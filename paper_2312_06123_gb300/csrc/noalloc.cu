@@ -41,7 +41,8 @@ constexpr size_t kOffSegOff = align256(kOffSegQ + sizeof(int32_t) * 2 * kNoAlloc
 constexpr int64_t kNoAllocHeavy = 4096;
 constexpr size_t kOffHeavy = align256(kOffSegOff + sizeof(int64_t) * 2 * (kNoAllocMaxQueries + 1));
 constexpr size_t kOffChunk = align256(kOffHeavy + sizeof(int64_t) * kNoAllocHeavy);
-constexpr size_t kOffPartial = align256(kOffChunk + sizeof(int64_t) * (kNoAllocMaxQueries + 1));
+constexpr size_t kOffWalkQ = align256(kOffChunk + sizeof(int64_t) * (kNoAllocMaxQueries + 1));
+constexpr size_t kOffPartial = align256(kOffWalkQ + sizeof(WalkQ) * kNoAllocMaxQueries);
 constexpr size_t kOffEnt = align256(kOffPartial + sizeof(Partial) * kNoAllocMaxQueries * kMaxChunksPerQuery);
 constexpr size_t kOffSums = align256(kOffEnt + sizeof(GEntry) * kNoAllocPool);
 constexpr size_t kOffY = align256(kOffSums + sizeof(uint64_t) * 2 * kNoAllocPool);
@@ -171,6 +172,7 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     a.heavy_cap = kNoAllocHeavy;
     a.ctl = ctl;
     a.err_flag = counters + 1;
+    a.wq = reinterpret_cast<WalkQ*>(base + kOffWalkQ);
     const int grid = sm_count * 8;
     launch_smm_start(fp64, a, grid, st);
     launch_smm_advance(a, 0, false, st);
@@ -187,6 +189,8 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     m.nq = (int32_t)q;
     m.st = qs;
     m.chunk_begin = reinterpret_cast<int64_t*>(base + kOffChunk);
+    m.wq = reinterpret_cast<WalkQ*>(base + kOffWalkQ);
+    m.walk_ctr = reinterpret_cast<unsigned long long*>(counters + 4);  // inside the 64-byte counter region
     m.done = reinterpret_cast<unsigned int*>(counters + 2);
     m.partial = reinterpret_cast<Partial*>(base + kOffPartial);
     m.partial_cap = kNoAllocMaxQueries * kMaxChunksPerQuery;
@@ -200,7 +204,7 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     launch_amc_schedule(m, st);
     for (int b = 1; b <= o.tau; ++b) {
         m.batch = b;
-        launch_amc_walk(m, sm_count * 8, st);
+        launch_amc_walk(m, sm_count, st);
         launch_amc_reduce(m, st);  // its last CTA lays out batch b + 1
     }
     launch_finalize(qs, q, r_dev, stats_dev, st);

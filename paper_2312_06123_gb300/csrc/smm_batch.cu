@@ -591,6 +591,26 @@ __global__ void smm_decide_kernel(SmmArgs a) {
             }
             if (lf > 0) {
                 Q->status = ST_AMC;
+                // the static part of the query's walk record
+                WalkQ* wr = a.wq + q;
+                wr->s = Q->s;
+                wr->t = Q->t;
+                if (a.g.node_info) {
+                    wr->s_info = a.g.node_info[Q->s];
+                    wr->t_info = a.g.node_info[Q->t];
+                } else {
+                    const int64_t rs = a.g.row_ptr[Q->s], rt = a.g.row_ptr[Q->t];
+                    wr->s_info = make_uint2((uint32_t)rs, (uint32_t)Q->ds);
+                    wr->t_info = make_uint2((uint32_t)rt, (uint32_t)Q->dt);
+                }
+                wr->lf = (int32_t)lf;
+                wr->qidx = Q->qidx;
+                wr->table_off = Q->table_off;
+                wr->mask = Q->table_mask;
+                wr->dstride = Q->dense_stride;
+                wr->dvals = Q->dense_vals;
+                wr->inv_ds = 1.0 / ds;
+                wr->inv_dt = 1.0 / dt;
             } else {
                 Q->status = ST_DONE;
                 Q->r = Q->r_b;
