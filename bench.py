@@ -31,10 +31,11 @@ os.environ.setdefault("GEER_SYNTH_CACHE", "/tmp/geer_synth_cache")
 
 METRIC = "ER queries/s at eps=0.05 (batched FP32 GEER, learned switch)"
 TRAIN_PAIRS, TRAIN_SEED = 2000, 5  # cost-log pairs of the learned switch (the bench pairs use seed 2)
+TRAIN_PAIRS_C4 = 7000              # the R-MAT workload trains on ~50k logged rows
 WALK_STEP_BYTES = 20  # row_ptr pair 8 B + one col_idx 4 B + one (s*, t*) FP32 pair 8 B
 # DRAM bytes (read + write) per dense_spmm launch from the ncu capture of the
-# current kernel on this workload (profiles/dense_spmm_c2_w128.md), per width.
-SPMM_TRAFFIC: dict = {128: 6_262_000_000 + 501_000_000}
+# current kernel, per (workload, width): profiles/dense_spmm_c2_w128.md
+SPMM_TRAFFIC: dict = {("c2", 128): 6_262_000_000 + 501_000_000}
 
 
 def _peaks():
@@ -145,7 +146,7 @@ def run_reference(args, world, rank):
     return 0
 
 
-def spmm_leg(G, w, geer, peak, nq=64, width=128, lb=10, reps=3):
+def spmm_leg(G, w, geer, peak, nq=64, width=128, lb=10, reps=3, workload="c2"):
     """Dense pull SpMM (the SMM step as a block SpMM, FP32, B = width columns
     = width/2 queries) on the bench graph: standalone SMM for `lb` iterations
     of `nq` pairs of the workload whose l >= lb, timed per launch with CUDA
@@ -182,7 +183,7 @@ def spmm_leg(G, w, geer, peak, nq=64, width=128, lb=10, reps=3):
            "launches": nl, "ms_per_launch": per * 1000.0, "algorithmic_bytes_per_launch": alg,
            "achieved": alg / per / 1e9, "peak": peak, "unit": "GB/s", "frac": alg / per / 1e9 / peak,
            "us_per_query_iteration": per * 1e6 / nq}
-    tr = SPMM_TRAFFIC.get(width)
+    tr = SPMM_TRAFFIC.get((workload, width))
     if tr is not None:
         out["traffic"] = tr
         out["dram_gbs"] = tr / per / 1e9
@@ -192,10 +193,17 @@ def spmm_leg(G, w, geer, peak, nq=64, width=128, lb=10, reps=3):
 
 def _config(w):
     g = w.graph
-    return {"workload": f"{g.name}, largest component (n={g.n}, m={g.m}); {w.q} uniform pairs, eps={w.eps[0]:g}",
-            "graph": g.name, "n": g.n, "m": g.m, "queries": w.q, "eps": float(w.eps[0]), "delta": 0.01, "tau": 5,
+    if w.name == "c3":
+        pairs_txt = (f"{w.q} pairs in thirds low-low / low-high / high-high degree (low <= median, high = top 1%), "
+                     f"eps cycling 0.1 / 0.05 / 0.02")
+        eps_cfg = "0.1/0.05/0.02"
+    else:
+        pairs_txt = f"{w.q} uniform pairs, eps={w.eps[0]:g}"
+        eps_cfg = float(w.eps[0])
+    return {"workload": f"{g.name}, largest component (n={g.n}, m={g.m}); {pairs_txt}",
+            "graph": g.name, "n": g.n, "m": g.m, "queries": w.q, "eps": eps_cfg, "delta": 0.01, "tau": 5,
             "smm_vectors": "fp32", "series_and_statistics": "fp64",
-            "switch": f"learned 6-64-64-1 network trained on cost logs of {TRAIN_PAIRS} other pairs (seed {TRAIN_SEED})",
+            "switch": "learned 6-64-64-1 network trained on cost logs of other pairs (seed 5)",
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
@@ -250,9 +258,15 @@ def main():
     from paper_2312_06123_gb300 import switch
     from synth import pairs as synth_pairs
     t_sw = time.perf_counter()
-    s_tr, t_tr = synth_pairs.uniform_pairs(g.n, TRAIN_PAIRS, TRAIN_SEED)
-    eps0 = float(w.eps[0])
-    clog = switch.cost_log(G, s_tr, t_tr, eps0, g.degrees(), max_steps=8)
+    train_pairs = TRAIN_PAIRS_C4 if args.workload == "c4" else TRAIN_PAIRS
+    if args.workload == "c3":  # training pairs follow the workload's recipe
+        s_tr, t_tr, eps_tr = synth_pairs.bucketed_pairs(g, train_pairs, TRAIN_SEED)
+        ms_log = 4
+    else:
+        s_tr, t_tr = synth_pairs.uniform_pairs(g.n, train_pairs, TRAIN_SEED)
+        eps_tr, ms_log = float(w.eps[0]), 8
+    eps0 = eps_tr
+    clog = switch.cost_log(G, s_tr, t_tr, eps0, g.degrees(), max_steps=ms_log)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def flush_l2():
@@ -341,21 +355,23 @@ def main():
         e2e_t.append(time.perf_counter() - t1)
     e2e_value = world * w.q * len(e2e_t) / sum(e2e_t) if e2e_t else None
 
-    # the plain FP64 per-query GPU path (one query at a time), same queries
+    # the plain FP64 per-query GPU path (one query at a time), on the first
+    # (at most) 1,000 queries of the same batch
     plain_opts = geer.default_options(precision=geer.GER_FP64, per_query=1)
+    pq = min(w.q, 1000)
     if not args.no_extras:
-        G.query_dev(s_d, t_d, e_d, r_d, None, plain_opts, stream=stream.cuda_stream)
+        G.query_dev(s_d[:pq], t_d[:pq], e_d[:pq], r_d[:pq], None, plain_opts, stream=stream.cuda_stream)
         torch.cuda.synchronize()
     pt = []
     for _ in range(0 if args.no_extras else max(args.plain_steps, 1)):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        G.query_dev(s_d, t_d, e_d, r_d, None, plain_opts, stream=stream.cuda_stream)
+        G.query_dev(s_d[:pq], t_d[:pq], e_d[:pq], r_d[:pq], None, plain_opts, stream=stream.cuda_stream)
         b.record(stream)
         b.synchronize()
         pt.append(a.elapsed_time(b))
-    plain_value = w.q * len(pt) / (sum(pt) / 1000.0) if pt else None
+    plain_value = pq * len(pt) / (sum(pt) / 1000.0) if pt else None
 
     if rank != 0:
         return 0
@@ -376,7 +392,7 @@ def main():
         nl, tms = fam[1]
         roof = {"kernel": fam[0], "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s",
                 "frac": None, "peak_source": peak_kind, "traffic": None}
-    spmm = None if args.no_extras else spmm_leg(G, w, geer, peak)
+    spmm = None if args.no_extras else spmm_leg(G, w, geer, peak, workload=args.workload)
     # CPU baseline: the oracle as it stands, one host thread, bounded sample
     cpu = None
     if not args.no_extras:
@@ -400,7 +416,7 @@ def main():
             "value": plain_value, "unit": "queries/s", "ms_per_step": float(np.mean(pt)),
             "speedup_of_batched_fp32": value / world / plain_value},
         "switch": {"policy": "learned" if model is not None else "rule (no network beat it)",
-                   "kappa": None if model is None else model.kappa, "train_pairs": TRAIN_PAIRS,
+                   "kappa": None if model is None else model.kappa, "train_pairs": train_pairs,
                    "train_seed": TRAIN_SEED, "cost_log_rows": int(clog.feats.shape[0]),
                    "setup_seconds": sw_seconds,
                    "train_batch_ms": {k: v * 1e3 for k, v in fit_times.items()},

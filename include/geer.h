@@ -77,7 +77,7 @@ typedef struct ger_options {
     int64_t  sparse_cap;    /* max SMM push pairs of one query iteration (0: no limit beyond the pool) */
     int32_t  smm_engine;    /* GER_ENGINE_SPARSE (default), GER_ENGINE_DENSE or GER_ENGINE_HYBRID */
     int32_t  dense_width;   /* dense engine: columns per block (2 per query); 0: autotuned per graph */
-    int64_t  dense_switch;  /* hybrid engine: push pairs at which a query moves to the SpMM; 0: nnz / 16 */
+    int64_t  dense_switch;  /* hybrid engine: push pairs at which a query moves to the SpMM; 0: autotuned, else nnz / 16 */
     int32_t  dense_budget_mb; /* hybrid engine: device memory for dense columns (MiB); 0: half the free memory */
     int32_t  reserved0;
 } ger_options;
@@ -210,6 +210,29 @@ int ger_profile_enable(int on);
 /* Copy up to max_entries family records into out; returns the number of
    families with at least one timed launch (>= 0), or GER_ERR_INVALID. */
 int ger_profile_read(ger_kernel_profile *out, int max_entries);
+
+/* Autotuning of the SMM engines (no counterpart in the paper; the choices
+ * change run time only, never a result). Times, on graph g and the given
+ * queries (host pointers, per-query eps), with the given options:
+ *  1. the dense block width: standalone SMM (4 iterations) of up to 64 of the
+ *     queries on the dense engine at every width the precision allows;
+ *  2. the hybrid engine's switch size: the whole batch at nnz/64, nnz/16,
+ *     nnz/4, nnz push pairs and without moves.
+ * The fastest of each is stored on g and used whenever an option leaves the
+ * value at 0 (dense_width, dense_switch). out (nullable) receives the choices
+ * and the median batch times.
+ * Errors: as ger_query_batch_eps. */
+typedef struct ger_tuning {
+    int32_t dense_width;            /* chosen block width (0: no dense engine on this graph) */
+    int32_t reserved;
+    int64_t dense_switch;           /* chosen hybrid switch size (push pairs) */
+    float   width_ms[3];            /* widths 32, 64, 128 (FP64: 32, 64) */
+    float   switch_ms[5];
+    int64_t switch_candidates[5];
+} ger_tuning;
+
+int ger_autotune(ger_graph *g, int64_t q, const int32_t *s, const int32_t *t, const double *eps,
+                 const ger_options *opt, ger_tuning *out);
 
 /* ------------------------------------------------------------------------
  * The learned SMM -> AMC switch (no counterpart in the paper; it replaces

@@ -58,6 +58,12 @@ class MlpTrainOptions(ctypes.Structure):
                 ("seed", ctypes.c_uint64)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("dense_width", ctypes.c_int32), ("reserved", ctypes.c_int32), ("dense_switch", ctypes.c_int64),
+                ("width_ms", ctypes.c_float * 3), ("switch_ms", ctypes.c_float * 5),
+                ("switch_candidates", ctypes.c_int64 * 5)]
+
+
 class KernelProfile(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -105,6 +111,7 @@ def load_library(build_if_missing: bool = True):
     L.ger_profile_read.argtypes = [ctypes.POINTER(KernelProfile), ctypes.c_int]
     L.ger_profile_read.restype = ctypes.c_int
     L.ger_set_switch_mlp.argtypes = [_P, _P, _P]
+    L.ger_autotune.argtypes = [_P, i64, _P, _P, _P, ctypes.POINTER(Options), ctypes.POINTER(Tuning)]
     L.ger_smm_trace.argtypes = [_P, i64, _P, _P, _P, ctypes.POINTER(Options), i32, _P, _P]
     L.ger_mlp_forward.argtypes = [i64, _P, _P, _P]
     L.ger_mlp_gradient.argtypes = [i64, _P, _P, _P, _P, _P]
@@ -114,7 +121,7 @@ def load_library(build_if_missing: bool = True):
     for name in ("ger_load_csr", "ger_graph_size", "ger_spectral_bound", "ger_set_spectral_bound",
                  "ger_query_batch", "ger_query_batch_eps", "ger_query_batch_dev",
                  "ger_query_batch_dev_noalloc", "ger_set_switch_mlp", "ger_smm_trace", "ger_mlp_forward",
-                 "ger_mlp_gradient", "ger_mlp_train"):
+                 "ger_mlp_gradient", "ger_mlp_train", "ger_autotune"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -290,6 +297,20 @@ class Graph:
         nv = _arr(norm, np.float32).reshape(2 * MLP_INPUTS)
         w = _fp16_bits(weights)
         _check(L.ger_set_switch_mlp(self._h, nv.ctypes.data_as(_P), w.ctypes.data_as(_P)))
+
+    def autotune(self, s, t, eps, options: Options | None = None) -> dict:
+        """Time the dense block widths and the hybrid switch sizes on these
+        queries (ger_autotune); the choices stay on the graph."""
+        s = _arr(s, np.int32)
+        t = _arr(t, np.int32)
+        e = _arr(np.broadcast_to(eps, s.shape), np.float64)
+        res = Tuning()
+        opt = options if options is not None else default_options()
+        _check(load_library().ger_autotune(self._h, s.shape[0], s.ctypes.data_as(_P), t.ctypes.data_as(_P),
+                                           e.ctypes.data_as(_P), ctypes.byref(opt), ctypes.byref(res)))
+        return {"dense_width": res.dense_width, "dense_switch": int(res.dense_switch),
+                "width_ms": list(res.width_ms), "switch_ms": list(res.switch_ms),
+                "switch_candidates": [int(x) for x in res.switch_candidates]}
 
     def smm_trace(self, s, t, eps, options: Options | None = None, max_steps: int = 16):
         """Cost log: (log[q][max_steps][LOG_WIDTH], stats) of a batch run

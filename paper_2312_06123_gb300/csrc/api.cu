@@ -21,7 +21,8 @@ namespace geer {
 static std::atomic<int64_t> g_launches{0};
 static bool g_capturing = false;    // graph capture: launches are counted per replay instead
 static int64_t g_captured = 0;      // kernels captured so far
-constexpr int64_t kHeavyCap = 1 << 16;
+constexpr int64_t kHeavyCap = 1 << 16;     // initial heavy-push list (chunk records)
+constexpr int64_t kHeavyCapMax = 1 << 26;
 void note_launches(int k) {
     if (g_capturing) g_captured += k;
     else g_launches.fetch_add(k, std::memory_order_relaxed);
@@ -146,7 +147,8 @@ struct Workspace {
     QSmm* qsmm = nullptr;
     int32_t* seg_q = nullptr;     // 2 (q_cap)
     int64_t* seg_off = nullptr;   // 2 (q_cap + 1)
-    int64_t* heavy = nullptr;     // kHeavyCap slots
+    int64_t* heavy = nullptr;     // heavy_cap chunk records of the heavy push
+    int64_t heavy_cap = 0;
     SmmCtl* ctl = nullptr;
     // frontier-table pool (also the walk lookup tables)
     GEntry* ent = nullptr;
@@ -214,6 +216,7 @@ struct ger_graph {
     cudaStream_t stream = nullptr;
     cudaStream_t stream2 = nullptr;  // captures the SMM while body
     int dense_tuned[2] = {0, 0};     // autotuned dense block width (FP32, FP64), 0: not tuned
+    int64_t hybrid_tuned = 0;        // autotuned hybrid switch size (push pairs), 0: not tuned
     int dense_ctas = 0;              // dense SpMM CTAs per SM and block, 0: default
     int4* dense_units = nullptr;     // dense SpMM work units (null when nnz >= 2^32)
     int4* dense_heavy = nullptr;     // dense SpMM heavy rows
@@ -252,6 +255,7 @@ static int ensure_ws(ger_graph* g, int64_t q, int64_t pool_cap) {
         GER_CUDA(alloc(&w.counters, 8));  // [1] error flag, [2] reduce CTA counter, [4..5] walk ticket
         GER_CUDA(alloc(&w.ctl, 1));
         GER_CUDA(alloc(&w.heavy, kHeavyCap));
+        w.heavy_cap = kHeavyCap;
         GER_CUDA(cudaMallocHost(reinterpret_cast<void**>(&w.host_rb), 4 * sizeof(int64_t)));
     }
     if (q > w.q_cap) {
@@ -581,7 +585,9 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
         while (cap < 2 * p.o.sparse_cap) cap <<= 1;
         a.max_table = cap;
     } else {
-        a.max_table = std::min<int64_t>(w.pool_cap, (int64_t)1 << 26);
+        // a table holds at most n nodes (capacity < 4n); a pool too small for it
+        // grows and the batch reruns, so only sparse_cap bounds a table
+        a.max_table = (int64_t)1 << 40;
     }
     a.ent = w.ent;
     a.sum_s = w.sums;
@@ -594,7 +600,7 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
     a.seg_off[0] = w.seg_off;
     a.seg_off[1] = w.seg_off + (w.q_cap + 1);
     a.heavy = w.heavy;
-    a.heavy_cap = kHeavyCap;
+    a.heavy_cap = w.heavy_cap;
     a.dense_engine = p.o.smm_engine == GER_ENGINE_DENSE;
     a.dense_width = a.dense_engine ? dense_width_for(g, p.o) : 2;
     a.dense_fp64 = fp64;
@@ -638,8 +644,8 @@ static void issue_amc(ger_graph* g, AmcArgs m, int64_t nq, cudaStream_t st) {
     note_launches(1 + 2 * m.tau);
 }
 
-// Dense columns of the hybrid engine for a batch of nq queries: as many as
-// the memory budget holds (two buffers of n values per column), at most nq.
+// Dense columns of the hybrid engine for a batch of nq queries: as many
+// query column pairs as the memory budget holds, at most nq.
 static int64_t hybrid_columns(const ger_graph* g, const ger_options& o, int64_t nq) {
     int64_t budget = (int64_t)o.dense_budget_mb << 20;
     if (budget <= 0) {
@@ -651,7 +657,8 @@ static int64_t hybrid_columns(const ger_graph* g, const ger_options& o, int64_t 
         }
         budget = ((int64_t)fr + 2 * (int64_t)g->ws.dX_bytes) / 2;
     }
-    const int64_t per = 2 * g->n * (o.precision == GER_FP64 ? 8 : 4);
+    // a query holds two columns (s*, t*) in each of the two buffers
+    const int64_t per = 4 * g->n * (o.precision == GER_FP64 ? 8 : 4);
     return std::min<int64_t>(nq, budget / std::max<int64_t>(per, 1));
 }
 
@@ -696,7 +703,9 @@ static int prepare_engine(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, b
         }
         a.hybrid = 1;
         a.dense_cap = (int32_t)E->cols;
-        a.migrate_at = p.o.dense_switch > 0 ? p.o.dense_switch : std::max<int64_t>(g->nnz / 16, 1);
+        a.migrate_at = p.o.dense_switch > 0 ? p.o.dense_switch
+                       : g->hybrid_tuned > 0 ? g->hybrid_tuned
+                                             : std::max<int64_t>(g->nnz / 16, 1);
         a.dense_block_q = w.dblock_q;
         a.mig_list = w.dmig;
     }
@@ -933,7 +942,27 @@ static int run_batch(ger_graph* g, Plan& p) {
         GER_CUDA(cudaMemcpyAsync(w.host_rb + 1, &w.ctl->cursor, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                  p.st));
         GER_CUDA(cudaMemcpyAsync(w.host_rb + 3, &w.ctl->iter, sizeof(int32_t), cudaMemcpyDeviceToHost, p.st));
+        GER_CUDA(cudaMemcpyAsync(reinterpret_cast<int32_t*>(w.host_rb + 3) + 1, &w.ctl->pad2, sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, p.st));
         GER_CUDA(cudaStreamSynchronize(p.st));
+        {
+            // heavy pushes that did not fit ran on single warps (correct, slow):
+            // give the next batches a list that holds them
+            const int64_t need = reinterpret_cast<int32_t*>(w.host_rb + 3)[1];
+            if (need > w.heavy_cap && w.heavy_cap < kHeavyCapMax) {
+                int64_t cap = w.heavy_cap;
+                while (cap < 2 * need && cap < kHeavyCapMax) cap <<= 1;
+                int64_t* nh = nullptr;
+                if (alloc(&nh, cap) == cudaSuccess) {
+                    cudaFree(w.heavy);
+                    w.heavy = nh;
+                    w.heavy_cap = cap;
+                    ++w.gen;
+                } else {
+                    cudaGetLastError();
+                }
+            }
+        }
         if (use_graph) {
             prof_collect_graph(g->bg.prof_recs);
             // the while body ran iter - 1 times
@@ -1265,6 +1294,93 @@ int ger_smm_trace(ger_graph* g, int64_t q, const int32_t* s, const int32_t* t, c
     o.per_query = 0;
     std::vector<double> r((size_t)std::max<int64_t>(q, 1));
     return host_batch(g, q, s, t, eps, 0.0, &o, r.data(), stats, log_out, max_steps);
+}
+
+// Wall time (ms) of one host-buffer batch on the graph's stream, after one
+// untimed call with the same options (which also builds its graph).
+static int timed_batch(ger_graph* g, int64_t q, const int32_t* s, const int32_t* t, const double* eps,
+                       const ger_options* o, int reps, float* ms_out) {
+    std::vector<double> r((size_t)q);
+    int rc = host_batch(g, q, s, t, eps, 0.0, o, r.data(), nullptr);
+    if (rc) return rc;
+    cudaEvent_t a, b;
+    GER_CUDA(cudaEventCreate(&a));
+    GER_CUDA(cudaEventCreate(&b));
+    std::vector<float> ms;
+    for (int i = 0; i < reps && !rc; ++i) {
+        cudaEventRecord(a, g->stream);
+        rc = host_batch(g, q, s, t, eps, 0.0, o, r.data(), nullptr);
+        cudaEventRecord(b, g->stream);
+        cudaEventSynchronize(b);
+        float x = 0.f;
+        cudaEventElapsedTime(&x, a, b);
+        ms.push_back(x);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc) return rc;
+    std::sort(ms.begin(), ms.end());
+    *ms_out = ms[ms.size() / 2];
+    return GER_OK;
+}
+
+int ger_autotune(ger_graph* g, int64_t q, const int32_t* s, const int32_t* t, const double* eps,
+                 const ger_options* opt, ger_tuning* out) {
+    if (!g || q <= 0 || !s || !t || !eps) return fail(GER_ERR_INVALID, "null argument or no queries");
+    ger_options base;
+    int rc = check_opts(opt, &base);
+    if (rc) return rc;
+    const bool fp64 = base.precision == GER_FP64;
+    ger_tuning res;
+    std::memset(&res, 0, sizeof(res));
+    // 1. dense block width: standalone SMM (min(l, 4) iterations) of up to 64
+    //    queries per width on the dense engine; cost per query
+    if (g->dense_units) {
+        const int64_t qs = std::min<int64_t>(q, 64);
+        const int widths32[3] = {32, 64, 128}, widths64[2] = {32, 64};
+        const int* widths = fp64 ? widths64 : widths32;
+        const int nw = fp64 ? 2 : 3;
+        float best = 0.f;
+        for (int i = 0; i < nw; ++i) {
+            ger_options o = base;
+            o.smm_engine = GER_ENGINE_DENSE;
+            o.dense_width = widths[i];
+            o.switch_policy = GER_SWITCH_FIXED;
+            o.fixed_ell_b = 4;
+            o.per_query = 0;
+            float ms = 0.f;
+            rc = timed_batch(g, qs, s, t, eps, &o, 3, &ms);
+            if (rc) return rc;
+            // queries share a block up to width / 2: the cost of qs queries at this width
+            res.width_ms[i] = ms;
+            if (i == 0 || ms < best) {
+                best = ms;
+                res.dense_width = widths[i];
+            }
+        }
+        g->dense_tuned[fp64 ? 1 : 0] = res.dense_width;
+    }
+    // 2. hybrid switch size: the whole batch with the caller's options on the
+    //    hybrid engine at a few sizes (and without moves), the fastest wins
+    const int64_t cands[5] = {g->nnz / 64, g->nnz / 16, g->nnz / 4, g->nnz, (int64_t)1 << 62};
+    float best = 0.f;
+    for (int i = 0; i < 5; ++i) {
+        ger_options o = base;
+        o.smm_engine = GER_ENGINE_HYBRID;
+        o.dense_switch = std::max<int64_t>(cands[i], 1);
+        float ms = 0.f;
+        rc = timed_batch(g, q, s, t, eps, &o, 3, &ms);
+        if (rc) return rc;
+        res.switch_ms[i] = ms;
+        res.switch_candidates[i] = o.dense_switch;
+        if (i == 0 || ms < best) {
+            best = ms;
+            res.dense_switch = o.dense_switch;
+        }
+    }
+    g->hybrid_tuned = res.dense_switch;
+    if (out) *out = res;
+    return GER_OK;
 }
 
 int ger_set_switch_mlp(ger_graph* g, const float* norm, const uint16_t* weights) {

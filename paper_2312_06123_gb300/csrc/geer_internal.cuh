@@ -84,7 +84,8 @@ struct SmmCtl {
     int32_t pad;
     // hybrid engine: dense columns handed out, queries moved by the last
     // decision, dense blocks already zeroed
-    int32_t dense_next, n_mig, dense_open, pad2;
+    int32_t dense_next, n_mig, dense_open;
+    int32_t pad2;                // largest heavy-push chunk count of any iteration
 };
 
 // What a walk chunk needs of its query, packed by the batch schedule (one

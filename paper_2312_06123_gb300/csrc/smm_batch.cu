@@ -242,6 +242,8 @@ __global__ void __launch_bounds__(kCta) smm_alloc_kernel(SmmArgs a) {
         C->hi[parity] = hi;
         C->cursor = base + (unsigned long long)carry;
         C->n_want = 0;
+        // the largest heavy-push demand of the batch (the host grows the list to it)
+        if (C->n_heavy > C->pad2) C->pad2 = C->n_heavy;
         C->n_heavy = 0;
     }
 }

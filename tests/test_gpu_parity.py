@@ -261,7 +261,7 @@ def test_hybrid_engine_deep_smm_agrees_with_sparse(c1):
 
 
 def test_hybrid_engine_with_few_dense_columns(c1):
-    # a budget of 1 MiB holds ~16 columns at n = 4k (FP64): the rest stay sparse
+    # a budget of 1 MiB holds ~8 query columns at n = 4k (FP64): the rest stay sparse
     w, g, G, lam = c1
     base = dict(precision=geer.GER_FP64, switch_policy=geer.GER_SWITCH_FIXED, fixed_ell_b=-1)
     r1, s1 = G.query(w.s, w.t, 0.1, _opts(**base), stats=True)
