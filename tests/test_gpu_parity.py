@@ -369,3 +369,35 @@ def test_c2_within_eps_of_reference(c2):
         L = oracle.ell(d[s], d[t], 1e-4, lam)
         ref = oracle.smm_terms(g, s, t, L).sum()
         assert abs(r[i] - ref) <= 0.05 + 1e-4
+
+
+def test_c2_learned_switch_sampled_parity(c2):
+    # the benchmark's configuration: a network trained on other pairs' cost logs
+    from paper_2312_06123_gb300 import switch
+    from synth import pairs
+    w, g, G, lam = c2
+    s_tr, t_tr = pairs.uniform_pairs(g.n, 512, 5)
+    log = switch.cost_log(G, s_tr, t_tr, 0.05, g.degrees(), max_steps=4)
+    model = switch.train(switch.price(log.inputs, log.push, log.walks, log.ell, 32.0, 0.0))
+    G.set_switch_mlp(model.norm, model.weights)
+    try:
+        r, st = G.query(w.s, w.t, w.eps, _opts(switch_policy=geer.GER_SWITCH_MLP), stats=True)
+    finally:
+        G.set_switch_mlp(None, None)
+    assert np.isfinite(r).all()
+    rng = np.random.default_rng(1)
+    for i in sorted(rng.choice(w.q, 10, replace=False)):
+        ref = replay(g, w.s[i], w.t[i], w.eps[i], lam, st[i], i)
+        compare(r[i], st[i], ref, 1e-5, 1e-5)
+
+
+def test_c2_hybrid_sampled_parity(c2):
+    # queries whose next push reaches nnz / 64 pairs continue on the SpMM
+    w, g, G, lam = c2
+    o = _opts(smm_engine=geer.GER_ENGINE_HYBRID, dense_switch=int(g.row_ptr[-1]) // 64,
+              switch_policy=geer.GER_SWITCH_FIXED, fixed_ell_b=3)
+    r, st = G.query(w.s[:64], w.t[:64], w.eps[:64], o, stats=True)
+    rng = np.random.default_rng(2)
+    for i in sorted(rng.choice(64, 6, replace=False)):
+        ref = replay(g, w.s[i], w.t[i], w.eps[i], lam, st[i], i)
+        compare(r[i], st[i], ref, 1e-5, 1e-5)
