@@ -35,7 +35,10 @@ TRAIN_PAIRS_C4 = 7000              # the R-MAT workload trains on ~50k logged ro
 WALK_STEP_BYTES = 20  # row_ptr pair 8 B + one col_idx 4 B + one (s*, t*) FP32 pair 8 B
 # DRAM bytes (read + write) per dense_spmm launch from the ncu capture of the
 # current kernel, per (workload, width): profiles/dense_spmm_c2_w128.md
-SPMM_TRAFFIC: dict = {("c2", 128): 6_262_000_000 + 501_000_000}
+SPMM_TRAFFIC: dict = {("c2", 128): 6_261_000_000 + 501_000_000}
+# DRAM bytes per walk step of amc_walk (ncu, all 5 AMC launches of the workload's batch):
+# profiles/amc_walk_c2_bench.md
+WALK_TRAFFIC_PER_STEP: dict = {"c2": (697_000_000 + 16_600_000) / 18_505_638}
 
 
 def _peaks():
@@ -191,6 +194,30 @@ def spmm_leg(G, w, geer, peak, nq=64, width=128, lb=10, reps=3, workload="c2"):
     return out
 
 
+def run_case(args):
+    """One kernel's launches for a profiler (no timing, no JSON line)."""
+    import synth
+    import paper_2312_06123_gb300 as geer
+    os.environ["GEER_NO_GRAPH"] = "1"  # profilers cannot time kernel nodes of the conditional graph
+    w = synth.workload(args.workload)
+    G = geer.Graph.from_csr(w.graph)
+    G.spectral_bound()
+    if args.case == "spmm":
+        _, st = G.query(w.s, w.t, w.eps, geer.default_options(), stats=True)
+        sel = np.nonzero(st["ell"] >= 10)[0][:64]
+        o = geer.default_options(precision=geer.GER_FP32, switch_policy=geer.GER_SWITCH_FIXED, fixed_ell_b=10,
+                                 smm_engine=geer.GER_ENGINE_DENSE, dense_width=128)
+        for _ in range(2):
+            G.query(w.s[sel], w.t[sel], w.eps[sel], o)
+    else:
+        o = (geer.default_options() if args.case == "walk"
+             else geer.default_options(switch_policy=geer.GER_SWITCH_FIXED, fixed_ell_b=1))
+        for _ in range(2):
+            G.query(w.s, w.t, w.eps, o)
+    print("ok")
+    return 0
+
+
 def _config(w):
     g = w.graph
     if w.name == "c3":
@@ -219,10 +246,17 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 per-query path")
     ap.add_argument("--no-extras", action="store_true",
                     help="profiling runs: skip the e2e, plain-FP64 and CPU-baseline legs (timed region unchanged)")
+    ap.add_argument("--case", choices=["spmm", "walk", "walk-fixed1"],
+                    help="profiling runs: only the launches of one kernel's case, stream-ordered, twice "
+                         "(spmm: 64 pairs with l >= 10, FP32 block of 128, standalone SMM for 10 iterations; "
+                         "walk: the workload's batch under Eq. (17); walk-fixed1: the batch switching after "
+                         "one iteration); prints nothing but 'ok'")
     args = ap.parse_args()
     world, rank, local = _dist()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.case:
+        return run_case(args)
 
     import torch
     import synth
@@ -385,8 +419,11 @@ def main():
         nl, tms = prof["amc_walk"]
         per_launch_bytes = WALK_STEP_BYTES * walk_steps / (nl / args.steps)
         achieved = per_launch_bytes / (tms / nl / 1000.0) / 1e9
+        tps = WALK_TRAFFIC_PER_STEP.get(args.workload)
         roof = {"kernel": "amc_walk", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": None if tps is None else tps * walk_steps / (nl / args.steps),
+                "traffic_note": "ncu DRAM bytes per walk step x this run's walk steps per launch",
                 "algorithmic_bytes_per_launch": per_launch_bytes}
     else:
         nl, tms = fam[1]

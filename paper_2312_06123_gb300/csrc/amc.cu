@@ -107,7 +107,7 @@ constexpr int kSmemChunkBegin = 2048;  // chunk_begin entries staged in shared m
 #define GEER_WALK_MINB 4
 #endif
 
-template <int W>
+template <int W, bool REC>
 __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a) {
     __shared__ int64_t cbeg[kSmemChunkBegin];
     const bool staged = a.nq + 1 <= kSmemChunkBegin;
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
                 inf[i] = start_info;
                 r[i] = make_uint4(0, 0, 0, 0);
             }
-            if (act[0] && g.edge_rec && mask >= 0) {
+            if (REC && act[0] && mask >= 0) {
                 // one dependent load per step: the edge record of the chosen
                 // neighbour carries that neighbour's row; the lookup probe of
                 // step j is resolved during step j + 1's load. The W walks of
@@ -363,18 +363,22 @@ void launch_edge_records(const int32_t* col_idx, const uint2* node_info, int64_t
 }
 
 void launch_amc_walk(const AmcArgs& a, int sm_count, cudaStream_t st) {
-    static int per_sm = 0;  // resident CTAs per SM of the walk kernel
-    if (per_sm == 0) {
+    static int per_sm[2] = {0, 0};  // resident CTAs per SM of the two walk kernels
+    const bool rec = a.g.edge_rec != nullptr;
+    if (per_sm[rec] == 0) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, amc_walk_kernel<kWalksPerLane>, 256, 0) != cudaSuccess ||
-            b < 1) {
+        const cudaError_t e =
+            rec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, amc_walk_kernel<kWalksPerLane, true>, 256, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, amc_walk_kernel<kWalksPerLane, false>, 256, 0);
+        if (e != cudaSuccess || b < 1) {
             cudaGetLastError();
             b = 1;
         }
-        per_sm = b;
+        per_sm[rec] = b;
     }
     prof_begin(FAM_AMC_WALK, st);
-    amc_walk_kernel<kWalksPerLane><<<sm_count * per_sm, 256, 0, st>>>(a);
+    if (rec) amc_walk_kernel<kWalksPerLane, true><<<sm_count * per_sm[1], 256, 0, st>>>(a);
+    else amc_walk_kernel<kWalksPerLane, false><<<sm_count * per_sm[0], 256, 0, st>>>(a);
     prof_end(FAM_AMC_WALK, st);
 }
 

@@ -1103,13 +1103,12 @@ int ger_load_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int 
         }
         // the walks' edge records: 16 B per stored edge; without them the
         // walks take two dependent loads per step instead of one
-        // when col_idx and the node records fit in L2 they serve the walk's two
-        // dependent loads from L2, faster than one DRAM load of an edge record
-        int l2 = 0;
-        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, device);
-        const char* rec_env = std::getenv("GEER_EDGE_RECORDS");  // 0 / 1 override the size rule
-        bool want_rec = 4 * g->nnz + 8 * n > (int64_t)l2;
-        if (rec_env && rec_env[0]) want_rec = rec_env[0] != '0';
+        // opt-in (GEER_EDGE_RECORDS=1): a walk reads edges uniformly and node
+        // records in proportion to degree, so col_idx plus the node records
+        // hit L2 more often than one edge-record array; measured slower on the
+        // 1M- and 4M-node power-law graphs
+        const char* rec_env = std::getenv("GEER_EDGE_RECORDS");
+        const bool want_rec = rec_env && rec_env[0] && rec_env[0] != '0';
         if (!want_rec) {
             g->edge_rec = nullptr;
         } else if (cudaMalloc(&g->edge_rec, (size_t)std::max<int64_t>(g->nnz, 1) * sizeof(uint4)) == cudaSuccess) {
