@@ -99,6 +99,19 @@ class Clocks:
                 "samples": len(rows), "reasons": sorted(reasons)}
 
 
+def replica_value(total_ms: float, queries: int, steps: int, world: int, dist=None, device=None):
+    """Whole-job throughput of N replicas (no data exchange between them:
+    each rank runs its own batch): the slowest rank's timed milliseconds
+    (max over ranks) set the job time; returns (value, job_ms)."""
+    import torch
+    job_ms = float(total_ms)
+    if dist is not None and world > 1:
+        tt = torch.tensor([job_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        job_ms = float(tt.item())
+    return world * queries * steps / (job_ms / 1000.0), job_ms
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -355,12 +368,7 @@ def main():
     torch.cuda.synchronize()
     prof = geer.profile_read()
     geer.profile_enable(False)
-    total_ms = float(sum(ms))
-    if dist is not None:
-        tt = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    value = world * w.q * args.steps / (total_ms / 1000.0)
+    value, total_ms = replica_value(float(sum(ms)), w.q, args.steps, world, dist, dev)
     stats = np.frombuffer(st_d.cpu().numpy().tobytes(), dtype=geer.STATS_DTYPE)
 
     # the same batch under Eq. (17)'s rule
