@@ -43,16 +43,28 @@ __device__ __forceinline__ const int32_t* row_base(const DevGraph& g, int32_t w,
     return g.node_info ? g.col_idx + info.x : g.col_idx + __ldg(g.row_ptr + w);
 }
 
-// Chunk layout of the next batch for every query still in AMC, by one CTA:
-// per query ppc (walk pairs per chunk) and its chunk count, and their prefix
-// in chunk_begin. Reads the query
-// state through the L2 (it was written by other CTAs of the same kernel).
-__device__ void schedule_cta(const AmcArgs& a) {
+// Walk pairs per chunk and chunk count of a batch of eta walk pairs, at
+// most maxc chunks (a chunk is a whole number of warp rounds).
+__device__ __forceinline__ void chunk_layout(int64_t eta, int64_t maxc, int64_t* ppc, int64_t* nch) {
+    const int64_t unit = kWalksPerLane * kPairsPerWarpRound;
+    const int64_t units = (eta + unit - 1) / unit;
+    const int64_t c = units < maxc ? units : maxc;
+    *ppc = unit * ((units + c - 1) / c);
+    *nch = (eta + *ppc - 1) / *ppc;
+}
+
+// Chunk layout of the next walk launch (batches b .. b + nb - 1, batch i of
+// a query having eta * 2^(i - b) pairs) for every query still in AMC, by one
+// CTA: per query its chunk count over the launch's batches, and their prefix
+// in chunk_begin. Reads the query state through the L2 (it was written by
+// other CTAs of the same kernel).
+__device__ void schedule_cta(const AmcArgs& a, int nb) {
     __shared__ int64_t scan[kWarps + 1];
     __shared__ int64_t carry;
     const int tid = threadIdx.x;
     if (tid == 0) carry = 0;
     __syncthreads();
+    const int64_t maxc = kMaxChunksPerQuery / nb;
     for (int64_t tile = 0; tile < a.nq; tile += kCta) {
         const int64_t q = tile + tid;
         int64_t nch = 0;
@@ -60,16 +72,14 @@ __device__ void schedule_cta(const AmcArgs& a) {
             QState* Q = a.st + q;
             if (__ldcg(&Q->status) == ST_AMC) {
                 const int64_t eta = __ldcg(&Q->eta);
-                // a warp round walks kWalksPerLane * kPairsPerWarpRound pairs
-                const int64_t unit = kWalksPerLane * kPairsPerWarpRound;
-                const int64_t units = (eta + unit - 1) / unit;
-                int64_t c = units < kMaxChunksPerQuery ? units : kMaxChunksPerQuery;
-                const int64_t ppc = unit * ((units + c - 1) / c);
-                nch = (eta + ppc - 1) / ppc;
-                Q->ppc = ppc;
+                for (int i = 0; i < nb; ++i) {
+                    int64_t ppc, n;
+                    chunk_layout(eta << i, maxc, &ppc, &n);
+                    if (i == 0) Q->ppc = ppc;
+                    nch += n;
+                }
                 // the rest of the walk record was packed when the query entered AMC
                 a.wq[q].eta = eta;
-                a.wq[q].ppc = ppc;
             }
             Q->nchunks = nch;
         }
@@ -86,7 +96,33 @@ __device__ void schedule_cta(const AmcArgs& a) {
     }
 }
 
-__global__ void __launch_bounds__(kCta) amc_schedule_kernel(AmcArgs a) { schedule_cta(a); }
+// Batches walked together at the start (when cheap), and the walk steps
+// below which they are: the speculative batches cost at most this much, the
+// launches they save are latency-bound.
+constexpr int kAmcGroup = 3;
+constexpr int64_t kAmcGroupSteps = (int64_t)1 << 25;
+
+// First layout of a batch's AMC: walk batches 1..kAmcGroup in one launch
+// when their walk steps (if no query stopped early) stay below
+// kAmcGroupSteps -- most queries need several batches, so little is wasted
+// and two latency-bound launch pairs are saved; else batch 1 alone. The
+// choice goes to *a.group for the launches that follow.
+__global__ void __launch_bounds__(kCta) amc_schedule_kernel(AmcArgs a) {
+    __shared__ unsigned long long tot;
+    if (threadIdx.x == 0) tot = 0ull;
+    __syncthreads();
+    const int nb = a.tau < kAmcGroup ? a.tau : kAmcGroup;
+    unsigned long long mine = 0ull;
+    for (int64_t q = threadIdx.x; q < a.nq; q += blockDim.x) {
+        const QState* Q = a.st + q;
+        if (Q->status == ST_AMC) mine += (unsigned long long)(((1ll << nb) - 1) * Q->eta * 2 * (int64_t)Q->lf);
+    }
+    atomicAdd(&tot, mine);
+    __syncthreads();
+    const int group = tot <= (unsigned long long)kAmcGroupSteps ? nb : 1;
+    if (threadIdx.x == 0) *a.group = group;
+    schedule_cta(a, group);
+}
 
 // g of a node whose first probe `p` (slot h) is already loaded
 __device__ __forceinline__ double resolve_g(const GEntry* tab, int32_t mask, int32_t v, int4 p, uint32_t h) {
@@ -120,7 +156,12 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
     const int64_t total = cb_arr[a.nq];
     const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
     const DevGraph g = a.g;
-    const uint32_t lane_ctr = (uint32_t)(2 * (a.batch - 1) + sigma);
+    // batches of this launch: the first launch walks *a.group batches, the
+    // launches of batches it covered have nothing to do
+    const int group = *a.group;
+    if (a.batch > 1 && a.batch <= group) return;
+    const int nbatch = a.batch == 1 ? group : 1;
+    const int64_t maxc = kMaxChunksPerQuery / nbatch;
     for (;;) {
         // chunks are handed out in order by a ticket counter
         unsigned long long ticket = 0;
@@ -135,7 +176,18 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
         }
         const WalkQ* WQ = a.wq + (lo - 1);
         const int64_t cb = cb_arr[lo - 1];
-        const int64_t eta = WQ->eta, ppc = WQ->ppc;
+        // which of the launch's batches this chunk belongs to, and its place in it
+        int64_t L = c - cb, eta = WQ->eta, ppc, nchb;
+        int bi = 0;
+        for (;;) {
+            chunk_layout(eta, maxc, &ppc, &nchb);
+            if (L < nchb || bi == nbatch - 1) break;
+            L -= nchb;
+            eta <<= 1;
+            ++bi;
+        }
+        const int batch = a.batch + bi;
+        const uint32_t lane_ctr = (uint32_t)(2 * (batch - 1) + sigma);
         const int32_t lf = WQ->lf, qidx = WQ->qidx;
         const int32_t start = sigma ? WQ->t : WQ->s;
         const GEntry* tab = a.pool + WQ->table_off;
@@ -145,7 +197,7 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
         const int64_t dstride = WQ->dstride;
         const double inv_ds = WQ->inv_ds, inv_dt = WQ->inv_dt;
         const uint2 start_info = sigma ? WQ->t_info : WQ->s_info;
-        const int64_t k_lo = (c - cb) * ppc;
+        const int64_t k_lo = L * ppc;
         const int64_t k_hi = min(k_lo + ppc, eta);
         double sz = 0.0, sz2 = 0.0;
         uint64_t cs = 0;
@@ -208,7 +260,7 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
                 for (int i = 0; i < W; ++i) {
                     if (lf > 0 && act[i]) z[i] += resolve_g(tab, mask, pnx[i], ppr[i], phh[i]);
                     w[i] = pnx[i];
-                    if (act[i]) cs += walk_hash(w[i], k[i], sigma, a.batch);
+                    if (act[i]) cs += walk_hash(w[i], k[i], sigma, batch);
                 }
             } else if (act[0]) {
                 for (int j = 1; j <= lf; ++j) {
@@ -260,7 +312,7 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
                 }
 #pragma unroll
                 for (int i = 0; i < W; ++i)
-                    if (act[i]) cs += walk_hash(w[i], k[i], sigma, a.batch);
+                    if (act[i]) cs += walk_hash(w[i], k[i], sigma, batch);
             }
 #pragma unroll
             for (int i = 0; i < W; ++i) {
@@ -286,58 +338,75 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
 }
 
 // One warp per query: batch statistics (Algorithm 1: Z, the empirical
-// variance, f of Eq. (7) at delta/tau) and the stop / doubling decision.
-// The last CTA to finish lays out the next batch (schedule_cta).
+// variance, f of Eq. (7) at delta/tau) and the stop / doubling decision for
+// each batch of the launch in order, until the query stops (the walks of
+// later batches of the launch are then not used). The last CTA to finish
+// lays out the next launch (one batch).
 __global__ void __launch_bounds__(kCta) amc_reduce_kernel(AmcArgs a) {
     __shared__ bool last;
+    const int group = *a.group;
+    if (a.batch > 1 && a.batch <= group) return;  // walked and evaluated with batch 1
+    const int nbatch = a.batch == 1 ? group : 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t q = (int64_t)blockIdx.x * kWarps + warp;
+    const int64_t maxc = kMaxChunksPerQuery / nbatch;
     if (q < a.nq) {
         QState* Q = a.st + q;
         if (Q->status == ST_AMC) {  // uniform across the warp
-            const int64_t nch = Q->nchunks, begin = a.chunk_begin[q];
-            double sz = 0.0, sz2 = 0.0;
-            uint64_t cs = 0;
-            for (int64_t i = lane; i < nch; i += 32) {
-                const Partial p = a.partial[begin + i];
-                sz += p.sz;
-                sz2 += p.sz2;
-                cs += p.cs;
-            }
-            sz = warp_sum(sz);
-            sz2 = warp_sum(sz2);
-            cs = warp_sum(cs);
-            if (lane == 0) {
-                const int64_t eta = Q->eta;
-                const double Z = sz / (double)eta;
-                double var = sz2 / (double)eta - Z * Z;
-                if (var < 0.0) var = 0.0;
-                const double delta_b = a.delta / (double)a.tau;
-                const double L = log(3.0 / delta_b);
-                const double f = sqrt(2.0 * var * L / (double)eta) + 3.0 * Q->psi * L / (double)eta;
-                Q->walks += eta;
-                Q->walk_steps += 2 * eta * (int64_t)Q->lf;
-                Q->checksum += cs;
-                Q->batch = a.batch;
-                Q->f_last = f;
-                if (f <= Q->eps / 2.0 || a.batch >= a.tau) {
-                    Q->r_f = Z;
-                    Q->r = Q->r_b + Z;
-                    Q->status = ST_DONE;
-                } else {
-                    Q->eta = 2 * eta;
+            int64_t begin = a.chunk_begin[q];
+            int64_t eta = Q->eta;
+            for (int bi = 0; bi < nbatch; ++bi) {
+                const int batch = a.batch + bi;
+                int64_t ppc, nch;
+                chunk_layout(eta, maxc, &ppc, &nch);
+                double sz = 0.0, sz2 = 0.0;
+                uint64_t cs = 0;
+                for (int64_t i = lane; i < nch; i += 32) {
+                    const Partial p = a.partial[begin + i];
+                    sz += p.sz;
+                    sz2 += p.sz2;
+                    cs += p.cs;
                 }
+                sz = warp_sum(sz);
+                sz2 = warp_sum(sz2);
+                cs = warp_sum(cs);
+                int stop = 0;
+                if (lane == 0) {
+                    const double Z = sz / (double)eta;
+                    double var = sz2 / (double)eta - Z * Z;
+                    if (var < 0.0) var = 0.0;
+                    const double delta_b = a.delta / (double)a.tau;
+                    const double L = log(3.0 / delta_b);
+                    const double f = sqrt(2.0 * var * L / (double)eta) + 3.0 * Q->psi * L / (double)eta;
+                    Q->walks += eta;
+                    Q->walk_steps += 2 * eta * (int64_t)Q->lf;
+                    Q->checksum += cs;
+                    Q->batch = batch;
+                    Q->f_last = f;
+                    if (f <= Q->eps / 2.0 || batch >= a.tau) {
+                        Q->r_f = Z;
+                        Q->r = Q->r_b + Z;
+                        Q->status = ST_DONE;
+                        stop = 1;
+                    } else {
+                        Q->eta = 2 * eta;
+                    }
+                }
+                if (__shfl_sync(0xffffffffu, stop, 0)) break;
+                begin += nch;
+                eta *= 2;
             }
         }
     }
-    if (a.batch >= a.tau) return;  // no next batch to lay out
+    const int next = a.batch + nbatch;
+    if (next > a.tau) return;  // no next batch to lay out
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(a.done, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!last) return;
     __threadfence();
-    schedule_cta(a);
+    schedule_cta(a, 1);
     if (threadIdx.x == 0) *a.done = 0u;
 }
 

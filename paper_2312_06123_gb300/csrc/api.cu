@@ -252,7 +252,7 @@ static cudaError_t alloc(T** p, size_t count) {
 static int ensure_ws(ger_graph* g, int64_t q, int64_t pool_cap) {
     Workspace& w = g->ws;
     if (!w.counters) {
-        GER_CUDA(alloc(&w.counters, 8));  // [1] error flag, [2] reduce CTA counter, [4..5] walk ticket
+        GER_CUDA(alloc(&w.counters, 8));  // [1] error flag, [2] reduce CTA counter, [4..5] walk ticket, [6] AMC group
         GER_CUDA(alloc(&w.ctl, 1));
         GER_CUDA(alloc(&w.heavy, kHeavyCap));
         w.heavy_cap = kHeavyCap;
@@ -620,6 +620,7 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
     m.chunk_begin = w.chunk_begin;
     m.wq = w.wq + q0;
     m.walk_ctr = reinterpret_cast<unsigned long long*>(w.counters + 4);
+    m.group = w.counters + 6;
     m.done = reinterpret_cast<unsigned int*>(w.counters + 2);
     m.partial = w.partial;
     m.partial_cap = w.partial_cap;
@@ -632,14 +633,16 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
 }
 
 // The tau AMC rounds (schedule -> walks -> batch statistics).
+// The AMC rounds: one walk launch and one statistics launch per batch; the
+// first schedule may fold the first batches into the first launch (the later
+// launches of those batches then return at once).
 static void issue_amc(ger_graph* g, AmcArgs m, int64_t nq, cudaStream_t st) {
-
     m.batch = 1;
     launch_amc_schedule(m, st);
     for (int b = 1; b <= m.tau; ++b) {
         m.batch = b;
         launch_amc_walk(m, g->sm_count, st);
-        launch_amc_reduce(m, st);  // its last CTA lays out batch b + 1
+        launch_amc_reduce(m, st);  // its last CTA lays out the next launch
     }
     note_launches(1 + 2 * m.tau);
 }

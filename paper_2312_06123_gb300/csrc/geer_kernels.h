@@ -103,7 +103,8 @@ struct AmcArgs {
     const GEntry* pool;
     uint64_t seed;
     int32_t tau;
-    int32_t batch;         // 1-based batch index b
+    int32_t batch;         // 1-based index b of the launch's first batch
+    int32_t* group;        // batches walked by the first launch (set by the first schedule)
     int32_t dense_fp64;    // element type of dense-engine values
     double delta;
     int* err_flag;

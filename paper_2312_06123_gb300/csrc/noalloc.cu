@@ -200,12 +200,13 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     m.delta = o.delta;
     m.dense_fp64 = fp64;
     m.err_flag = counters + 1;
+    m.group = counters + 6;  // inside the 64-byte counter region
     m.batch = 1;
     launch_amc_schedule(m, st);
     for (int b = 1; b <= o.tau; ++b) {
         m.batch = b;
         launch_amc_walk(m, sm_count, st);
-        launch_amc_reduce(m, st);  // its last CTA lays out batch b + 1
+        launch_amc_reduce(m, st);  // its last CTA lays out the next launch
     }
     launch_finalize(qs, q, r_dev, stats_dev, st);
     note_launches(2 + 2 * o.tau);
