@@ -32,6 +32,7 @@ os.environ.setdefault("GEER_SYNTH_CACHE", "/tmp/geer_synth_cache")
 METRIC = "ER queries/s at eps=0.05 (batched FP32 GEER, learned switch)"
 TRAIN_PAIRS, TRAIN_SEED = 2000, 5  # cost-log pairs of the learned switch (the bench pairs use seed 2)
 TRAIN_PAIRS_C4 = 7000              # the R-MAT workload trains on ~50k logged rows
+TRAIN_PAIRS_C5 = 256               # the 1B-edge workload logs few pairs (dense columns are 256 MB each)
 WALK_STEP_BYTES = 20  # row_ptr pair 8 B + one col_idx 4 B + one (s*, t*) FP32 pair 8 B
 # DRAM bytes (read + write) per dense_spmm launch from the ncu capture of the
 # current kernel, per (workload, width): profiles/dense_spmm_c2_w128.md
@@ -254,7 +255,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
     ap.add_argument("--ref-seconds", type=float, default=10.0, help="oracle seconds per reference step")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle seconds for cpu_baseline")
     ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 per-query path")
@@ -306,15 +307,19 @@ def main():
     from paper_2312_06123_gb300 import switch
     from synth import pairs as synth_pairs
     t_sw = time.perf_counter()
-    train_pairs = TRAIN_PAIRS_C4 if args.workload == "c4" else TRAIN_PAIRS
+    train_pairs = {"c4": TRAIN_PAIRS_C4, "c5": TRAIN_PAIRS_C5}.get(args.workload, TRAIN_PAIRS)
+    log_chunk = 512
     if args.workload == "c3":  # training pairs follow the workload's recipe
         s_tr, t_tr, eps_tr = synth_pairs.bucketed_pairs(g, train_pairs, TRAIN_SEED)
         ms_log = 4
+    elif args.workload == "c5":  # dense columns of a 32M-node graph: 256 MB per query
+        s_tr, t_tr = synth_pairs.uniform_pairs(g.n, train_pairs, TRAIN_SEED)
+        eps_tr, ms_log, log_chunk = float(w.eps[0]), 3, 64
     else:
         s_tr, t_tr = synth_pairs.uniform_pairs(g.n, train_pairs, TRAIN_SEED)
         eps_tr, ms_log = float(w.eps[0]), 8
     eps0 = eps_tr
-    clog = switch.cost_log(G, s_tr, t_tr, eps0, g.degrees(), max_steps=ms_log)
+    clog = switch.cost_log(G, s_tr, t_tr, eps0, g.degrees(), max_steps=ms_log, chunk=log_chunk)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def flush_l2():

@@ -12,7 +12,8 @@ Workloads (graph seed 1, pair seed 2, walk seed 3):
   * ``workload("c4")``: R-MAT scale 22, edge factor 16, (0.57, 0.19, 0.19);
     4,096 uniform pairs, eps 0.05.
   * ``workload("c5")``: Chung-Lu n=32M, mean degree 62.5 (~1B edges),
-    exponent 2.3; 2,048 uniform pairs, eps 0.05.
+    exponent 2.3; 2,048 uniform pairs, eps 0.05 (drawn by the GPU generator
+    of ``gpu_graphs`` when a GPU is present).
 """
 from __future__ import annotations
 
@@ -55,14 +56,23 @@ def _graph(name: str, scale: float = 1.0) -> CSRGraph:
     if name == "c4":
         return graphs.rmat(22, 16, 0.57, 0.19, 0.19, GRAPH_SEED, "rmat scale=22 ef=16")
     if name == "c5":
-        return graphs.chung_lu(int(32_000_000 * scale), 62.5, 2.3, GRAPH_SEED,
-                               f"chung-lu n={int(32_000_000 * scale)} d=62.5 b=2.3")
+        # ~1B edges: drawn on the GPU when there is one (see gpu_graphs)
+        n5 = int(32_000_000 * scale)
+        try:
+            import torch
+            on_gpu = torch.cuda.is_available()
+        except ImportError:
+            on_gpu = False
+        if on_gpu:
+            from .gpu_graphs import chung_lu_gpu
+            return chung_lu_gpu(n5, 62.5, 2.3, GRAPH_SEED, f"chung-lu n={n5} d=62.5 b=2.3 (device draw)")
+        return graphs.chung_lu(n5, 62.5, 2.3, GRAPH_SEED, f"chung-lu n={n5} d=62.5 b=2.3")
     raise KeyError(name)
 
 
 def workload(name: str, scale: float = 1.0, q: int | None = None) -> Workload:
     """Build (or load from the cache directory $GEER_SYNTH_CACHE) a workload."""
-    cache = os.environ.get("GEER_SYNTH_CACHE")
+    cache = os.environ.get("GEER_SYNTH_CACHE") if name != "c5" else None  # c5's CSR is ~8 GB
     path = None
     if cache:
         path = os.path.join(cache, f"{name}_{scale:g}.npz")

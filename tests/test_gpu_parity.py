@@ -303,6 +303,29 @@ def test_self_pair_and_zero_length(c1):
     assert st[0]["ell"] == 0 and r[0] == 1 / 19 + 1 / 19
 
 
+@pytest.mark.parametrize("engine", [geer.GER_ENGINE_DENSE, geer.GER_ENGINE_HYBRID])
+def test_engines_on_degenerate_queries(c1, engine):
+    # a batch mixing s = t, an l = 0 pair and ordinary pairs; then one query at
+    # a time (a dense block with a single live column)
+    w, g, G, lam = c1
+    o = _opts(precision=geer.GER_FP64, smm_engine=engine, dense_switch=1)
+    s = np.array([5, int(w.s[0]), int(w.s[1]), 9], dtype=np.int32)
+    t = np.array([5, int(w.t[0]), int(w.t[1]), 9], dtype=np.int32)
+    r, st = G.query(s, t, 0.1, o, stats=True)
+    assert r[0] == 0.0 and r[3] == 0.0 and st[0]["walks"] == 0
+    ref, sref = G.query(s, t, 0.1, _opts(precision=geer.GER_FP64), stats=True)
+    assert np.allclose(r, ref, rtol=1e-9, atol=0) and np.array_equal(st["checksum"], sref["checksum"])
+    r1, s1 = G.query(s[1:2], t[1:2], 0.1, _opts(precision=geer.GER_FP64, smm_engine=engine, dense_switch=1,
+                                                per_query=1), stats=True)
+    ref1 = replay(g, s[1], t[1], 0.1, lam, s1[0], 0)
+    compare(r1[0], s1[0], ref1, 1e-9, 1e-9)
+    K = graphs.complete(20)
+    GK = geer.Graph.from_csr(K)
+    GK.set_spectral_bound(1 / 19)
+    rk, sk = GK.query([0, 3], [7, 3], 0.5, o, stats=True)
+    assert sk[0]["ell"] == 0 and rk[0] == 1 / 19 + 1 / 19 and rk[1] == 0.0
+
+
 def test_invalid_queries(c1):
     w, g, G, lam = c1
     with pytest.raises(geer.GeerError) as e:
