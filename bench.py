@@ -163,13 +163,15 @@ def run_reference(args, world, rank):
     return 0
 
 
-def spmm_leg(G, w, geer, peak, nq=64, width=128, lb=10, reps=3, workload="c2"):
+def spmm_leg(G, w, geer, peak, nq=64, width=128, lb=10, reps=3, workload="c2", base=None):
     """Dense pull SpMM (the SMM step as a block SpMM, FP32, B = width columns
     = width/2 queries) on the bench graph: standalone SMM for `lb` iterations
     of `nq` pairs of the workload whose l >= lb, timed per launch with CUDA
     events on the launching stream (host-driven loop, no graph capture)."""
     g = w.graph
-    r, st = G.query(w.s, w.t, w.eps, geer.default_options(), stats=True)
+    # l of every pair (a batch switching after one SMM iteration reports it)
+    r, st = G.query(w.s, w.t, w.eps, geer.default_options(switch_policy=geer.GER_SWITCH_FIXED, fixed_ell_b=1,
+                                                          **(base or {})), stats=True)
     sel = np.nonzero(st["ell"] >= lb)[0][:nq]
     if len(sel) < nq:
         return None
@@ -302,6 +304,11 @@ def main():
     r_d = torch.empty(w.q, dtype=torch.float64, device=dev)
     st_d = torch.empty(w.q * geer.STATS_DTYPE.itemsize, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
+    # the 1B-edge graph's hubs make sparse tables of deep queries too large:
+    # pushes of >= nnz/64 pairs continue on the SpMM (hybrid engine)
+    base = {}
+    if args.workload == "c5":
+        base = {"smm_engine": geer.GER_ENGINE_HYBRID, "dense_switch": int(g.row_ptr[-1]) // 64}
     # the learned SMM -> AMC switch: cost logs on separate pairs, the push price
     # chosen by measured batch time; Eq. (17)'s rule when no network beats it
     from paper_2312_06123_gb300 import switch
@@ -327,14 +334,15 @@ def main():
         torch.cuda.synchronize()
 
     # selection under the timed region's conditions (L2 flushed before each batch)
-    model, fit_times = switch.fit(G, s_tr, t_tr, eps0, clog, before=flush_l2)
+    model, fit_times = switch.fit(G, s_tr, t_tr, eps0, clog, options=geer.default_options(**base),
+                                  before=flush_l2)
     sw_seconds = time.perf_counter() - t_sw
     if model is not None:
         G.set_switch_mlp(model.norm, model.weights)
-        opts = geer.default_options(switch_policy=geer.GER_SWITCH_MLP)
+        opts = geer.default_options(switch_policy=geer.GER_SWITCH_MLP, **base)
     else:
-        opts = geer.default_options()
-    rule_opts = geer.default_options()
+        opts = geer.default_options(**base)
+    rule_opts = geer.default_options(**base)
 
     def step():
         G.query_dev(s_d, t_d, e_d, r_d, st_d, opts, stream=stream.cuda_stream)
@@ -411,7 +419,7 @@ def main():
 
     # the plain FP64 per-query GPU path (one query at a time), on the first
     # (at most) 1,000 queries of the same batch
-    plain_opts = geer.default_options(precision=geer.GER_FP64, per_query=1)
+    plain_opts = geer.default_options(precision=geer.GER_FP64, per_query=1, **base)
     pq = min(w.q, 1000)
     if not args.no_extras:
         G.query_dev(s_d[:pq], t_d[:pq], e_d[:pq], r_d[:pq], None, plain_opts, stream=stream.cuda_stream)
@@ -449,7 +457,7 @@ def main():
         nl, tms = fam[1]
         roof = {"kernel": fam[0], "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s",
                 "frac": None, "peak_source": peak_kind, "traffic": None}
-    spmm = None if args.no_extras else spmm_leg(G, w, geer, peak, workload=args.workload)
+    spmm = None if args.no_extras else spmm_leg(G, w, geer, peak, workload=args.workload, base=base)
     # CPU baseline: the oracle as it stands, one host thread, bounded sample
     cpu = None
     if not args.no_extras:
