@@ -142,7 +142,7 @@ def batch_seconds(G, s, t, eps, options, repeats: int = 7, before=None) -> float
 
 
 def fit(G, s, t, eps, log: CostLog, options=None, kappas=(8.0, 32.0, 128.0), epochs: int = 60,
-        seed: int = 7, before=None, repeats: int = 9):
+        seed: int = 7, before=None, repeats: int = 9, min_rows: int = 64):
     """Choose the push price by measurement: train one network per kappa on
     the cost log, time each resulting policy on the logged queries' own
     batch, and keep the fastest; returns (model or None when Eq. (17)'s rule
@@ -151,6 +151,9 @@ def fit(G, s, t, eps, log: CostLog, options=None, kappas=(8.0, 32.0, 128.0), epo
     eps = np.broadcast_to(np.asarray(eps, np.float64), (q,)).copy()
     times = {"rule": batch_seconds(G, s, t, eps, _with(options, switch_policy=GER_SWITCH_RULE), repeats, before)}
     best, best_t = None, times["rule"]
+    if log.feats.shape[0] < min_rows:
+        # (almost) no query has a decision to make (l <= 1): the rule stays
+        return None, times
     for k in kappas:
         lg = price(log.inputs, log.push, log.walks, log.ell, k, 0.0)
         model = train(lg, epochs=epochs, seed=seed)
