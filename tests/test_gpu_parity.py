@@ -424,3 +424,36 @@ def test_c2_hybrid_sampled_parity(c2):
     for i in sorted(rng.choice(64, 6, replace=False)):
         ref = replay(g, w.s[i], w.t[i], w.eps[i], lam, st[i], i)
         compare(r[i], st[i], ref, 1e-5, 1e-5)
+
+
+# ---------------------------------------------------------------------------
+# full size: 4M-node Chung-Lu (beta 2.2), 8,192 bucketed pairs, per-query eps
+# ---------------------------------------------------------------------------
+
+def test_c3_sampled_parity():
+    w = synth.workload("c3")
+    g = w.graph
+    G = geer.Graph.from_csr(g)
+    lam, _, _ = G.spectral_bound()
+    r, st = G.query(w.s, w.t, w.eps, _opts(), stats=True)
+    assert np.isfinite(r).all()
+    # high-high pairs at eps 0.1 (cheap for the oracle), and the s = t-free rest is finite
+    cand = [i for i in range(2 * w.q // 3, w.q) if w.eps[i] == 0.1 and st[i]["walks"] < 200000]
+    rng = np.random.default_rng(3)
+    for i in sorted(rng.choice(cand, 4, replace=False)):
+        ref = replay(g, w.s[i], w.t[i], w.eps[i], lam, st[i], i)
+        compare(r[i], st[i], ref, 1e-5, 1e-5)
+    G.close()
+
+
+def test_autotune_changes_run_time_only(c1):
+    w, g, G, lam = c1
+    o = _opts(precision=geer.GER_FP64)
+    r0, s0 = G.query(w.s, w.t, w.eps, _opts(precision=geer.GER_FP64, smm_engine=geer.GER_ENGINE_HYBRID), stats=True)
+    tune = G.autotune(w.s, w.t, w.eps, o)
+    assert tune["dense_width"] in (32, 64) and tune["dense_switch"] in tune["switch_candidates"]
+    assert all(x > 0 for x in tune["switch_ms"])
+    r1, s1 = G.query(w.s, w.t, w.eps, _opts(precision=geer.GER_FP64, smm_engine=geer.GER_ENGINE_HYBRID), stats=True)
+    same = s0["ell_b"] == s1["ell_b"]
+    assert np.array_equal(s0["checksum"][same], s1["checksum"][same])
+    assert np.allclose(r0[same], r1[same], rtol=1e-9, atol=0)
