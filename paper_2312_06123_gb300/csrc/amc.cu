@@ -15,7 +15,10 @@
 // g(v) = s*(v)/d(s) - t*(v)/d(t) read from the query's lookup table (Eq. 11;
 // the start node w_0 is not counted, as E[Z_k] = q(s,t) of Eqs. 12-13 requires).
 // Per-chunk sums go to a partial array; the reduce kernel adds a query's
-// chunks in a fixed order, so results do not depend on scheduling.
+// chunks in a fixed order, so results do not depend on scheduling. When the
+// first three batches' walks are few, they share the first launch (the
+// chunks of a query are its batch-1, then batch-2, then batch-3 chunks) and
+// the reduce evaluates them in order, ignoring batches after a stop.
 #include "geer_internal.cuh"
 #include "geer_kernels.h"
 

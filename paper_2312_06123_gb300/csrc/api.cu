@@ -1,7 +1,10 @@
 // api.cu -- the C ABI of include/geer.h: graph loading and validation,
 // workspace management, and the launch sequence of a GEER query batch
-// (Algorithm 3): sparse SMM with the greedy switch, then tau AMC rounds of
-// schedule -> walks -> batch statistics, then the per-query outputs.
+// (Algorithm 3): SMM iterations on the sparse push, dense pull SpMM or hybrid
+// engine with the switch of Eq. (17) (or the learned switch), then the AMC
+// rounds of schedule -> walks -> batch statistics, then the per-query
+// outputs; one batch shape is captured once as a CUDA graph. Also the
+// autotuner and the learned switch's installation and cost log.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
