@@ -146,6 +146,175 @@ constexpr int kSmemChunkBegin = 2048;  // chunk_begin entries staged in shared m
 #define GEER_WALK_MINB 4
 #endif
 
+// Walks of chunk L of a work unit of query WQ: batches batch0 .. batch0 +
+// nbatch - 1 with eta pairs in batch0 (doubling), chunked by chunk_layout at
+// kMaxChunksPerQuery / nbatch chunks per batch. Returns the chunk's sums of
+// Z_k, Z_k^2 and the walk checksum, reduced over the warp.
+template <int W, bool REC>
+__device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, int64_t L, int64_t eta, int batch0,
+                                           int nbatch, int lane, double* out_sz, double* out_sz2, uint64_t* out_cs) {
+    const int sigma = lane & 1;
+    const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
+    const DevGraph g = a.g;
+    const int64_t maxc = kMaxChunksPerQuery / nbatch;
+    // which of the unit's batches this chunk belongs to, and its place in it
+    int64_t ppc, nchb;
+    int bi = 0;
+    for (;;) {
+        chunk_layout(eta, maxc, &ppc, &nchb);
+        if (L < nchb || bi == nbatch - 1) break;
+        L -= nchb;
+        eta <<= 1;
+        ++bi;
+    }
+    const int batch = batch0 + bi;
+    const uint32_t lane_ctr = (uint32_t)(2 * (batch - 1) + sigma);
+    const int32_t lf = WQ->lf, qidx = WQ->qidx;
+    const int32_t start = sigma ? WQ->t : WQ->s;
+    const GEntry* tab = a.pool + WQ->table_off;
+    const int32_t mask = WQ->mask;
+    // dense-engine queries: (s*, t*) read directly from their block column
+    const char* dvals = reinterpret_cast<const char*>(WQ->dvals);
+    const int64_t dstride = WQ->dstride;
+    const double inv_ds = WQ->inv_ds, inv_dt = WQ->inv_dt;
+    const uint2 start_info = sigma ? WQ->t_info : WQ->s_info;
+    const int64_t k_lo = L * ppc;
+    const int64_t k_hi = min(k_lo + ppc, eta);
+    double sz = 0.0, sz2 = 0.0;
+    uint64_t cs = 0;
+    for (int64_t k0 = k_lo; k0 < k_hi; k0 += W * kPairsPerWarpRound) {
+        int64_t k[W];
+        bool act[W];
+        double z[W];
+        int32_t w[W];
+        uint2 inf[W];
+        uint4 r[W];
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            k[i] = k0 + (lane >> 1) + i * kPairsPerWarpRound;
+            act[i] = k[i] < k_hi;
+            z[i] = 0.0;
+            w[i] = start;
+            inf[i] = start_info;
+            r[i] = make_uint4(0, 0, 0, 0);
+        }
+        if (REC && act[0] && mask >= 0) {
+            // one dependent load per step: the edge record of the chosen
+            // neighbour carries that neighbour's row; the lookup probe of
+            // step j is resolved during step j + 1's load. The W walks of
+            // the lane advance together so that their loads overlap.
+            uint2 cur[W];
+            int32_t pnx[W];
+            uint32_t phh[W];
+            int4 ppr[W];
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                cur[i] = start_info;
+                pnx[i] = start;
+                phh[i] = 0;
+                ppr[i] = make_int4(0, 0, 0, 0);
+            }
+            for (int j = 1; j <= lf; ++j) {
+                const int sub = (j - 1) & 3;
+                uint4 rec[W];
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    if (sub == 0)
+                        r[i] = philox4x32_10(
+                            make_uint4((uint32_t)k[i], lane_ctr, (uint32_t)qidx, (uint32_t)((j - 1) >> 2)), key);
+                    const uint32_t d = sub == 0 ? r[i].x : (sub == 1 ? r[i].y : (sub == 2 ? r[i].z : r[i].w));
+                    rec[i] = act[i] ? __ldg(g.edge_rec + cur[i].x + __umulhi(d, cur[i].y))
+                                    : make_uint4((uint32_t)start, start_info.x, start_info.y, 0u);
+                }
+#pragma unroll
+                for (int i = 0; i < W; ++i)
+                    if (j > 1 && act[i]) z[i] += resolve_g(tab, mask, pnx[i], ppr[i], phh[i]);
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    pnx[i] = (int32_t)rec[i].x;
+                    cur[i] = make_uint2(rec[i].y, rec[i].z);
+                    phh[i] = hash32(rec[i].x) & (uint32_t)mask;
+                    ppr[i] = __ldg(reinterpret_cast<const int4*>(tab + phh[i]));
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                if (lf > 0 && act[i]) z[i] += resolve_g(tab, mask, pnx[i], ppr[i], phh[i]);
+                w[i] = pnx[i];
+                if (act[i]) cs += walk_hash(w[i], k[i], sigma, batch);
+            }
+        } else if (act[0]) {
+            for (int j = 1; j <= lf; ++j) {
+                const int sub = (j - 1) & 3;
+                int32_t nx[W];
+                uint32_t hh[W];
+                int4 pr[W];
+#pragma unroll
+                for (int i = 0; i < W; ++i) {
+                    if (sub == 0 && act[i])
+                        r[i] = philox4x32_10(
+                            make_uint4((uint32_t)k[i], lane_ctr, (uint32_t)qidx, (uint32_t)((j - 1) >> 2)), key);
+                    const uint32_t d = sub == 0 ? r[i].x : (sub == 1 ? r[i].y : (sub == 2 ? r[i].z : r[i].w));
+                    nx[i] = act[i] ? __ldg(row_base(g, w[i], inf[i]) + __umulhi(d, inf[i].y)) : start;
+                }
+                // next row records and first probes (or dense values), all independent
+                if (mask >= 0) {
+#pragma unroll
+                    for (int i = 0; i < W; ++i) {
+                        hh[i] = hash32((uint32_t)nx[i]) & (uint32_t)mask;
+                        pr[i] = __ldg(reinterpret_cast<const int4*>(tab + hh[i]));
+                        if (act[i]) inf[i] = node_row(g, nx[i]);
+                    }
+#pragma unroll
+                    for (int i = 0; i < W; ++i) {
+                        if (act[i]) z[i] += resolve_g(tab, mask, nx[i], pr[i], hh[i]);
+                        w[i] = nx[i];
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < W; ++i) {
+                        double xs, xt;
+                        if (a.dense_fp64) {
+                            const double2 p2 = __ldg(reinterpret_cast<const double2*>(dvals + (size_t)nx[i] * dstride * 8));
+                            xs = fabs(p2.x);  // the sign bit carries the support
+                            xt = fabs(p2.y);
+                        } else {
+                            const float2 p2 = __ldg(reinterpret_cast<const float2*>(dvals + (size_t)nx[i] * dstride * 4));
+                            xs = (double)fabsf(p2.x);
+                            xt = (double)fabsf(p2.y);
+                        }
+                        if (act[i]) {
+                            inf[i] = node_row(g, nx[i]);
+                            z[i] += xs * inv_ds - xt * inv_dt;
+                        }
+                        w[i] = nx[i];
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < W; ++i)
+                if (act[i]) cs += walk_hash(w[i], k[i], sigma, batch);
+        }
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            const double o = __shfl_xor_sync(0xffffffffu, z[i], 1);
+            if (sigma == 0 && act[i]) {
+                const double zk = z[i] - o;
+                sz += zk;
+                sz2 += zk * zk;
+            }
+        }
+    }
+    sz = warp_sum(sz);
+    sz2 = warp_sum(sz2);
+    cs = warp_sum(cs);
+    *out_sz = sz;
+    *out_sz2 = sz2;
+    *out_cs = cs;
+}
+
+// Launch-per-batch walks: a persistent grid whose warps take chunks of the
+// launch's layout (chunk_begin) from a ticket counter.
 template <int W, bool REC>
 __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a) {
     __shared__ int64_t cbeg[kSmemChunkBegin];
@@ -155,16 +324,12 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
     __syncthreads();
     const int64_t* cb_arr = staged ? cbeg : a.chunk_begin;
     const int lane = threadIdx.x & 31;
-    const int sigma = lane & 1;
     const int64_t total = cb_arr[a.nq];
-    const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
-    const DevGraph g = a.g;
     // batches of this launch: the first launch walks *a.group batches, the
     // launches of batches it covered have nothing to do
     const int group = *a.group;
     if (a.batch > 1 && a.batch <= group) return;
     const int nbatch = a.batch == 1 ? group : 1;
-    const int64_t maxc = kMaxChunksPerQuery / nbatch;
     for (;;) {
         // chunks are handed out in order by a ticket counter
         unsigned long long ticket = 0;
@@ -178,158 +343,9 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
             if (cb_arr[mid] <= c) lo = mid + 1; else hi = mid;
         }
         const WalkQ* WQ = a.wq + (lo - 1);
-        const int64_t cb = cb_arr[lo - 1];
-        // which of the launch's batches this chunk belongs to, and its place in it
-        int64_t L = c - cb, eta = WQ->eta, ppc, nchb;
-        int bi = 0;
-        for (;;) {
-            chunk_layout(eta, maxc, &ppc, &nchb);
-            if (L < nchb || bi == nbatch - 1) break;
-            L -= nchb;
-            eta <<= 1;
-            ++bi;
-        }
-        const int batch = a.batch + bi;
-        const uint32_t lane_ctr = (uint32_t)(2 * (batch - 1) + sigma);
-        const int32_t lf = WQ->lf, qidx = WQ->qidx;
-        const int32_t start = sigma ? WQ->t : WQ->s;
-        const GEntry* tab = a.pool + WQ->table_off;
-        const int32_t mask = WQ->mask;
-        // dense-engine queries: (s*, t*) read directly from their block column
-        const char* dvals = reinterpret_cast<const char*>(WQ->dvals);
-        const int64_t dstride = WQ->dstride;
-        const double inv_ds = WQ->inv_ds, inv_dt = WQ->inv_dt;
-        const uint2 start_info = sigma ? WQ->t_info : WQ->s_info;
-        const int64_t k_lo = L * ppc;
-        const int64_t k_hi = min(k_lo + ppc, eta);
-        double sz = 0.0, sz2 = 0.0;
-        uint64_t cs = 0;
-        for (int64_t k0 = k_lo; k0 < k_hi; k0 += W * kPairsPerWarpRound) {
-            int64_t k[W];
-            bool act[W];
-            double z[W];
-            int32_t w[W];
-            uint2 inf[W];
-            uint4 r[W];
-#pragma unroll
-            for (int i = 0; i < W; ++i) {
-                k[i] = k0 + (lane >> 1) + i * kPairsPerWarpRound;
-                act[i] = k[i] < k_hi;
-                z[i] = 0.0;
-                w[i] = start;
-                inf[i] = start_info;
-                r[i] = make_uint4(0, 0, 0, 0);
-            }
-            if (REC && act[0] && mask >= 0) {
-                // one dependent load per step: the edge record of the chosen
-                // neighbour carries that neighbour's row; the lookup probe of
-                // step j is resolved during step j + 1's load. The W walks of
-                // the lane advance together so that their loads overlap.
-                uint2 cur[W];
-                int32_t pnx[W];
-                uint32_t phh[W];
-                int4 ppr[W];
-#pragma unroll
-                for (int i = 0; i < W; ++i) {
-                    cur[i] = start_info;
-                    pnx[i] = start;
-                    phh[i] = 0;
-                    ppr[i] = make_int4(0, 0, 0, 0);
-                }
-                for (int j = 1; j <= lf; ++j) {
-                    const int sub = (j - 1) & 3;
-                    uint4 rec[W];
-#pragma unroll
-                    for (int i = 0; i < W; ++i) {
-                        if (sub == 0)
-                            r[i] = philox4x32_10(
-                                make_uint4((uint32_t)k[i], lane_ctr, (uint32_t)qidx, (uint32_t)((j - 1) >> 2)), key);
-                        const uint32_t d = sub == 0 ? r[i].x : (sub == 1 ? r[i].y : (sub == 2 ? r[i].z : r[i].w));
-                        rec[i] = act[i] ? __ldg(g.edge_rec + cur[i].x + __umulhi(d, cur[i].y))
-                                        : make_uint4((uint32_t)start, start_info.x, start_info.y, 0u);
-                    }
-#pragma unroll
-                    for (int i = 0; i < W; ++i)
-                        if (j > 1 && act[i]) z[i] += resolve_g(tab, mask, pnx[i], ppr[i], phh[i]);
-#pragma unroll
-                    for (int i = 0; i < W; ++i) {
-                        pnx[i] = (int32_t)rec[i].x;
-                        cur[i] = make_uint2(rec[i].y, rec[i].z);
-                        phh[i] = hash32(rec[i].x) & (uint32_t)mask;
-                        ppr[i] = __ldg(reinterpret_cast<const int4*>(tab + phh[i]));
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < W; ++i) {
-                    if (lf > 0 && act[i]) z[i] += resolve_g(tab, mask, pnx[i], ppr[i], phh[i]);
-                    w[i] = pnx[i];
-                    if (act[i]) cs += walk_hash(w[i], k[i], sigma, batch);
-                }
-            } else if (act[0]) {
-                for (int j = 1; j <= lf; ++j) {
-                    const int sub = (j - 1) & 3;
-                    int32_t nx[W];
-                    uint32_t hh[W];
-                    int4 pr[W];
-#pragma unroll
-                    for (int i = 0; i < W; ++i) {
-                        if (sub == 0 && act[i])
-                            r[i] = philox4x32_10(
-                                make_uint4((uint32_t)k[i], lane_ctr, (uint32_t)qidx, (uint32_t)((j - 1) >> 2)), key);
-                        const uint32_t d = sub == 0 ? r[i].x : (sub == 1 ? r[i].y : (sub == 2 ? r[i].z : r[i].w));
-                        nx[i] = act[i] ? __ldg(row_base(g, w[i], inf[i]) + __umulhi(d, inf[i].y)) : start;
-                    }
-                    // next row records and first probes (or dense values), all independent
-                    if (mask >= 0) {
-#pragma unroll
-                        for (int i = 0; i < W; ++i) {
-                            hh[i] = hash32((uint32_t)nx[i]) & (uint32_t)mask;
-                            pr[i] = __ldg(reinterpret_cast<const int4*>(tab + hh[i]));
-                            if (act[i]) inf[i] = node_row(g, nx[i]);
-                        }
-#pragma unroll
-                        for (int i = 0; i < W; ++i) {
-                            if (act[i]) z[i] += resolve_g(tab, mask, nx[i], pr[i], hh[i]);
-                            w[i] = nx[i];
-                        }
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < W; ++i) {
-                            double xs, xt;
-                            if (a.dense_fp64) {
-                                const double2 p2 = __ldg(reinterpret_cast<const double2*>(dvals + (size_t)nx[i] * dstride * 8));
-                                xs = fabs(p2.x);  // the sign bit carries the support
-                                xt = fabs(p2.y);
-                            } else {
-                                const float2 p2 = __ldg(reinterpret_cast<const float2*>(dvals + (size_t)nx[i] * dstride * 4));
-                                xs = (double)fabsf(p2.x);
-                                xt = (double)fabsf(p2.y);
-                            }
-                            if (act[i]) {
-                                inf[i] = node_row(g, nx[i]);
-                                z[i] += xs * inv_ds - xt * inv_dt;
-                            }
-                            w[i] = nx[i];
-                        }
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < W; ++i)
-                    if (act[i]) cs += walk_hash(w[i], k[i], sigma, batch);
-            }
-#pragma unroll
-            for (int i = 0; i < W; ++i) {
-                const double o = __shfl_xor_sync(0xffffffffu, z[i], 1);
-                if (sigma == 0 && act[i]) {
-                    const double zk = z[i] - o;
-                    sz += zk;
-                    sz2 += zk * zk;
-                }
-            }
-        }
-        sz = warp_sum(sz);
-        sz2 = warp_sum(sz2);
-        cs = warp_sum(cs);
+        double sz, sz2;
+        uint64_t cs;
+        walk_chunk<W, REC>(a, WQ, c - cb_arr[lo - 1], WQ->eta, a.batch, nbatch, lane, &sz, &sz2, &cs);
         if (lane == 0) {
             Partial p;
             p.sz = sz;
@@ -340,11 +356,81 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
     }
 }
 
-// One warp per query: batch statistics (Algorithm 1: Z, the empirical
-// variance, f of Eq. (7) at delta/tau) and the stop / doubling decision for
-// each batch of the launch in order, until the query stops (the walks of
-// later batches of the launch are then not used). The last CTA to finish
-// lays out the next launch (one batch).
+// Batch statistics (Algorithm 1: Z, the empirical variance, f of Eq. (7) at
+// delta/tau) and the stop / doubling decision of one query for its batches
+// batch0 .. batch0 + nbatch - 1 in order, from the chunk partials at
+// `begin`, until the query stops (the walks of later batches are then not
+// used). The whole warp calls it; lane 0 updates the query state. Reads and
+// writes go through L2, so that another SM's warp can take the query over.
+// Returns 1 (warp-uniform) when the query stopped.
+__device__ int evaluate_batches(const AmcArgs& a, QState* Q, int64_t begin, int64_t eta, int batch0, int nbatch,
+                                int lane) {
+    const int64_t maxc = kMaxChunksPerQuery / nbatch;
+    // the query's state, loaded once (independent loads, issued together)
+    double psi = 0.0, qeps = 0.0, r_b = 0.0;
+    int64_t walks = 0, steps = 0;
+    unsigned long long chk = 0;
+    int32_t lf = 0;
+    if (lane == 0) {
+        psi = __ldcg(&Q->psi);
+        qeps = __ldcg(&Q->eps);
+        r_b = __ldcg(&Q->r_b);
+        walks = __ldcg(reinterpret_cast<const long long*>(&Q->walks));
+        steps = __ldcg(reinterpret_cast<const long long*>(&Q->walk_steps));
+        chk = __ldcg(reinterpret_cast<const unsigned long long*>(&Q->checksum));
+        lf = __ldcg(&Q->lf);
+    }
+    const double delta_b = a.delta / (double)a.tau;
+    const double Lg = log(3.0 / delta_b);
+    for (int bi = 0; bi < nbatch; ++bi) {
+        const int batch = batch0 + bi;
+        int64_t ppc, nch;
+        chunk_layout(eta, maxc, &ppc, &nch);
+        double sz = 0.0, sz2 = 0.0;
+        uint64_t cs = 0;
+        for (int64_t i = lane; i < nch; i += 32) {
+            const Partial* p = a.partial + begin + i;
+            sz += __ldcg(&p->sz);
+            sz2 += __ldcg(&p->sz2);
+            cs += __ldcg(reinterpret_cast<const unsigned long long*>(&p->cs));
+        }
+        sz = warp_sum(sz);
+        sz2 = warp_sum(sz2);
+        cs = warp_sum(cs);
+        int stop = 0;
+        if (lane == 0) {
+            const double Z = sz / (double)eta;
+            double var = sz2 / (double)eta - Z * Z;
+            if (var < 0.0) var = 0.0;
+            const double f = sqrt(2.0 * var * Lg / (double)eta) + 3.0 * psi * Lg / (double)eta;
+            walks += eta;
+            steps += 2 * eta * (int64_t)lf;
+            chk += cs;
+            stop = f <= qeps / 2.0 || batch >= a.tau;
+            if (stop || bi == nbatch - 1) {
+                __stcg(reinterpret_cast<long long*>(&Q->walks), (long long)walks);
+                __stcg(reinterpret_cast<long long*>(&Q->walk_steps), (long long)steps);
+                __stcg(reinterpret_cast<unsigned long long*>(&Q->checksum), chk);
+                __stcg(&Q->batch, batch);
+                __stcg(&Q->f_last, f);
+                if (stop) {
+                    __stcg(&Q->r_f, Z);
+                    __stcg(&Q->r, r_b + Z);
+                    __stcg(&Q->status, (int32_t)ST_DONE);
+                } else {
+                    __stcg(reinterpret_cast<long long*>(&Q->eta), (long long)(2 * eta));
+                }
+            }
+        }
+        if (__shfl_sync(0xffffffffu, stop, 0)) return 1;
+        begin += nch;
+        eta *= 2;
+    }
+    return 0;
+}
+
+// Launch-per-batch statistics: one warp per query over the launch's batches;
+// the last CTA to finish lays out the next launch (one batch).
 __global__ void __launch_bounds__(kCta) amc_reduce_kernel(AmcArgs a) {
     __shared__ bool last;
     const int group = *a.group;
@@ -352,54 +438,10 @@ __global__ void __launch_bounds__(kCta) amc_reduce_kernel(AmcArgs a) {
     const int nbatch = a.batch == 1 ? group : 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t q = (int64_t)blockIdx.x * kWarps + warp;
-    const int64_t maxc = kMaxChunksPerQuery / nbatch;
     if (q < a.nq) {
         QState* Q = a.st + q;
-        if (Q->status == ST_AMC) {  // uniform across the warp
-            int64_t begin = a.chunk_begin[q];
-            int64_t eta = Q->eta;
-            for (int bi = 0; bi < nbatch; ++bi) {
-                const int batch = a.batch + bi;
-                int64_t ppc, nch;
-                chunk_layout(eta, maxc, &ppc, &nch);
-                double sz = 0.0, sz2 = 0.0;
-                uint64_t cs = 0;
-                for (int64_t i = lane; i < nch; i += 32) {
-                    const Partial p = a.partial[begin + i];
-                    sz += p.sz;
-                    sz2 += p.sz2;
-                    cs += p.cs;
-                }
-                sz = warp_sum(sz);
-                sz2 = warp_sum(sz2);
-                cs = warp_sum(cs);
-                int stop = 0;
-                if (lane == 0) {
-                    const double Z = sz / (double)eta;
-                    double var = sz2 / (double)eta - Z * Z;
-                    if (var < 0.0) var = 0.0;
-                    const double delta_b = a.delta / (double)a.tau;
-                    const double L = log(3.0 / delta_b);
-                    const double f = sqrt(2.0 * var * L / (double)eta) + 3.0 * Q->psi * L / (double)eta;
-                    Q->walks += eta;
-                    Q->walk_steps += 2 * eta * (int64_t)Q->lf;
-                    Q->checksum += cs;
-                    Q->batch = batch;
-                    Q->f_last = f;
-                    if (f <= Q->eps / 2.0 || batch >= a.tau) {
-                        Q->r_f = Z;
-                        Q->r = Q->r_b + Z;
-                        Q->status = ST_DONE;
-                        stop = 1;
-                    } else {
-                        Q->eta = 2 * eta;
-                    }
-                }
-                if (__shfl_sync(0xffffffffu, stop, 0)) break;
-                begin += nch;
-                eta *= 2;
-            }
-        }
+        if (Q->status == ST_AMC)  // uniform across the warp
+            evaluate_batches(a, Q, a.chunk_begin[q], Q->eta, a.batch, nbatch, lane);
     }
     const int next = a.batch + nbatch;
     if (next > a.tau) return;  // no next batch to lay out

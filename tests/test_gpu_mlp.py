@@ -113,7 +113,8 @@ def test_cost_log_matches_oracle_trace(c1, prec):
 
 
 def _small_rmat():
-    g = graphs.rmat(13, 16, 0.57, 0.19, 0.19, 1, "rmat scale=13 ef=16")
+    # large enough that a batch's time is its SMM and walk work, not its launches
+    g = graphs.rmat(15, 16, 0.57, 0.19, 0.19, 1, "rmat scale=15 ef=16")
     return g
 
 
@@ -123,7 +124,7 @@ def rmat_model():
     G = geer.Graph.from_csr(g)
     lam, _, _ = G.spectral_bound()
     d = g.degrees()
-    s, t = pairs.uniform_pairs(g.n, 768, 21)
+    s, t = pairs.uniform_pairs(g.n, 1024, 21)
     log = switch.cost_log(G, s, t, 0.05, d, max_steps=8)
     model, times = switch.fit(G, s, t, 0.05, log, kappas=(8.0, 32.0, 128.0))
     return g, G, lam, model, log, times
@@ -143,7 +144,7 @@ def test_learned_switch_gains_over_the_rule(rmat_model):
     # C(l_b) under the chosen price
     g, G, lam, model, _, _ = rmat_model
     d = g.degrees()
-    s, t = pairs.uniform_pairs(g.n, 512, 22)
+    s, t = pairs.uniform_pairs(g.n, 1024, 22)
     log = switch.cost_log(G, s, t, 0.05, d, max_steps=8, kappa=model.kappa)
     res = switch.evaluate(G, s, t, 0.05, model, log, repeats=9)
     ok = np.isfinite(res["rule"]["cost"]) & np.isfinite(res["mlp"]["cost"])
