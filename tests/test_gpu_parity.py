@@ -172,6 +172,50 @@ def test_standalone_amc_walks_bit_exact(c1, prec):
         compare(r[i], st[i], ref, 1e-9 if prec == geer.GER_FP64 else 1e-5, 1e-9)
 
 
+@pytest.mark.parametrize("tau,delta,seed", [(1, 0.01, 3), (2, 0.05, 3), (3, 0.01, 11), (7, 0.001, 3),
+                                             (5, 0.01, 0x5EEDF00D12345678)])
+def test_amc_options_replay_bit_exact(c1, tau, delta, seed):
+    # tau decides how many batches the first AMC launch folds (min(tau, 3)) and
+    # the chunk cap per batch; delta enters f through delta / tau; the seed's
+    # two halves are the Philox key
+    w, g, G, lam = c1
+    q = 48
+    s, t, eps = w.s[:q], w.t[:q], w.eps[:q]
+    for prec, rel in ((geer.GER_FP64, 1e-9), (geer.GER_FP32, 1e-5)):
+        r, st = G.query(s, t, eps, _opts(precision=prec, tau=tau, delta=delta, seed=seed), stats=True)
+        assert np.all(st["batches"] <= tau)
+        assert np.any(st["walks"] > 0)
+        for i in range(q):
+            ref = replay(g, s[i], t[i], eps[i], lam, st[i], i, seed=seed, tau=tau, delta=delta)
+            compare(r[i], st[i], ref, rel, rel)
+
+
+@pytest.mark.parametrize("heavy", [False, True])
+def test_amc_chunks_of_many_rounds_replay_bit_exact(c1, heavy):
+    # eps 0.02 and l_b = 1 on the lowest-degree pairs: batches of 1e4 - 2e5 walk
+    # pairs, past the per-query chunk cap, so one chunk holds several warp rounds.
+    # The three lighter pairs have their first three batches folded into one
+    # launch (cap 4096 / 3 chunks a batch); the heaviest is too heavy to fold.
+    w, g, G, lam = c1
+    d = g.degrees()
+    order = np.argsort(d[w.s] + d[w.t], kind="stable")
+    idx = order[:1] if heavy else order[1:4]
+    s, t = w.s[idx], w.t[idx]
+    eps = np.full(len(idx), 0.02)
+    o = _opts(precision=geer.GER_FP64, switch_policy=geer.GER_SWITCH_FIXED, fixed_ell_b=1)
+    r, st = G.query(s, t, eps, o, stats=True)
+    lf = st["ell"] - st["ell_b"]
+    folded = int((7 * st["eta0"] * 2 * lf).sum()) <= 1 << 25
+    assert folded != heavy
+    if heavy:
+        assert st["eta0"][0] > 16 * 4096
+    else:
+        assert (4 * st["eta0"]).max() > 16 * (4096 // 3)
+    for i in range(len(idx)):
+        ref = replay(g, s[i], t[i], eps[i], lam, st[i], i)
+        compare(r[i], st[i], ref, 1e-9, 1e-9)
+
+
 def test_peng_ell(c1):
     w, g, G, lam = c1
     r, st = G.query(w.s[:10], w.t[:10], 0.1, _opts(precision=geer.GER_FP64, ell_formula=geer.GER_ELL_PENG),
@@ -444,6 +488,35 @@ def test_c3_sampled_parity():
         ref = replay(g, w.s[i], w.t[i], w.eps[i], lam, st[i], i)
         compare(r[i], st[i], ref, 1e-5, 1e-5)
     G.close()
+
+
+def test_c5_sampled_parity():
+    # the 32M-node, ~1B-edge workload at full size in the bench's launch
+    # configuration (FP32, hybrid engine moving pushes of >= nnz/64 pairs to
+    # the SpMM): row starts past 2^30, hub rows of 10^5 edges
+    w = synth.workload("c5")
+    g = w.graph
+    nnz = int(g.row_ptr[-1])
+    assert nnz > 1 << 30
+    G = geer.Graph.from_csr(g)
+    lam, _, _ = G.spectral_bound()
+    o = _opts(smm_engine=geer.GER_ENGINE_HYBRID, dense_switch=nnz // 64)
+    r, st = G.query(w.s, w.t, w.eps, o, stats=True)
+    assert np.isfinite(r).all()
+    # the oracle's SMM passes over the whole CSR per iteration: one query of
+    # each kind -- SMM then walks (l >= 2, rare on this expander at eps 0.05),
+    # SMM only (l = 1), and Eq. (6)'s l = 0
+    rng = np.random.default_rng(5)
+    walked = np.flatnonzero(st["walks"] > 0)
+    smm_only = np.flatnonzero((st["ell_b"] >= 1) & (st["walks"] == 0))
+    flat = np.flatnonzero(st["ell"] == 0)
+    assert len(walked) >= 1 and len(smm_only) >= 1 and len(flat) >= 1
+    pick = [int(rng.choice(walked)), int(rng.choice(smm_only)), int(rng.choice(flat))]
+    for i in sorted(pick):
+        ref = replay(g, w.s[i], w.t[i], w.eps[i], lam, st[i], i)
+        compare(r[i], st[i], ref, 1e-5, 1e-5)
+    G.close()
+    del g, w
 
 
 def test_autotune_changes_run_time_only(c1):
