@@ -858,9 +858,9 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
         }
         if (e == cudaSuccess) {
             issue_amc(g, m, p.q, st);
-            const int fg = (int)std::min<int64_t>((p.q + 255) / 256, 4096);
+            const int fg = query_grid(p.q);
             prof_begin(FAM_FINALIZE, st);
-            finalize_kernel<<<fg, 256, 0, st>>>(w.st, p.q, p.r, p.stats);
+            finalize_kernel<<<fg, kQueryCta, 0, st>>>(w.st, p.q, p.r, p.stats);
             prof_end(FAM_FINALIZE, st);
             note_launches(1);
         }
@@ -937,9 +937,9 @@ static int run_batch(ger_graph* g, Plan& p) {
                 rc = run_queries(g, p, 0, p.q, fp64);
                 if (rc) return rc;
             }
-            const int fg = (int)std::min<int64_t>((p.q + 255) / 256, 4096);
+            const int fg = query_grid(p.q);
             prof_begin(FAM_FINALIZE, p.st);
-            finalize_kernel<<<fg, 256, 0, p.st>>>(w.st, p.q, p.r, p.stats);
+            finalize_kernel<<<fg, kQueryCta, 0, p.st>>>(w.st, p.q, p.r, p.stats);
             prof_end(FAM_FINALIZE, p.st);
             note_launches(1);
         }
@@ -1003,9 +1003,9 @@ int graph_view(const ger_graph* g, DevGraph* dg, double* lambda, bool* has_lambd
 int set_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
 void launch_finalize(const QState* st, int64_t nq, double* r, ger_query_stats* stats, cudaStream_t s) {
-    const int fg = (int)std::min<int64_t>((nq + 255) / 256, 4096);
+    const int fg = query_grid(nq);
     prof_begin(FAM_FINALIZE, s);
-    finalize_kernel<<<fg, 256, 0, s>>>(st, nq, r, stats);
+    finalize_kernel<<<fg, kQueryCta, 0, s>>>(st, nq, r, stats);
     prof_end(FAM_FINALIZE, s);
 }
 

@@ -10,6 +10,19 @@ namespace geer {
 
 constexpr int kCta = 256;          // threads per CTA of the SMM / reduction kernels
 constexpr int kWarps = kCta / 32;
+// CTA of the one-CTA table allocation, which walks every query in order:
+// one tile covers 1,024 queries, so their loads go out together and one scan
+// orders them. (Not for kernels with per-query FP64 work: the FP64 pipe of
+// one SM is narrow, so those spread their queries over many SMs.)
+constexpr int kSerialCta = 1024;
+constexpr int kSerialWarps = kSerialCta / 32;
+// CTA of the kernels with one thread per query (set-up, decision, outputs):
+// each thread writes its query's few hundred bytes of state with scattered
+// stores, so the queries are spread over many SMs
+constexpr int kQueryCta = 32;
+__host__ __device__ constexpr int query_grid(int64_t nq) {
+    return (int)((nq + kQueryCta - 1) / kQueryCta < 8192 ? (nq + kQueryCta - 1) / kQueryCta : 8192);
+}
 constexpr int kPairsPerWarpRound = 16;  // walk pairs per warp per round (2 lanes per pair)
 constexpr int kMaxChunksPerQuery = 4096;
 
@@ -182,22 +195,29 @@ __device__ __forceinline__ int64_t warp_incl_scan(int64_t x) {
 
 // Exclusive CTA scan of one value per thread; returns the prefix and writes
 // the CTA total to *total (all threads). smem: kWarps + 1 int64.
-__device__ __forceinline__ int64_t cta_excl_scan(int64_t x, int64_t* smem, int64_t* total) {
+// Exclusive scan over a CTA of NW warps (NW <= 32); smem holds NW + 1
+// values. Returns x's exclusive prefix and the CTA total.
+template <int NW>
+__device__ __forceinline__ int64_t cta_excl_scan_w(int64_t x, int64_t* smem, int64_t* total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     int64_t inc = warp_incl_scan(x);
     if (lane == 31) smem[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-        int64_t w = lane < kWarps ? smem[lane] : 0;
+        int64_t w = lane < NW ? smem[lane] : 0;
         int64_t wi = warp_incl_scan(w);
-        if (lane < kWarps) smem[lane] = wi - w;
-        if (lane == kWarps - 1) smem[kWarps] = wi;
+        if (lane < NW) smem[lane] = wi - w;
+        if (lane == NW - 1) smem[NW] = wi;
     }
     __syncthreads();
     int64_t r = smem[warp] + inc - x;
-    *total = smem[kWarps];
+    *total = smem[NW];
     __syncthreads();
     return r;
+}
+
+__device__ __forceinline__ int64_t cta_excl_scan(int64_t x, int64_t* smem, int64_t* total) {
+    return cta_excl_scan_w<kWarps>(x, smem, total);
 }
 
 template <typename T>

@@ -186,8 +186,8 @@ __global__ void smm_setup_kernel(SmmArgs a) {
 // ---------------------------------------------------------------------------
 // alloc (one CTA): tables for the queries that asked for one, in query order
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kCta) smm_alloc_kernel(SmmArgs a) {
-    __shared__ int64_t scan[kWarps + 1];
+__global__ void __launch_bounds__(kSerialCta) smm_alloc_kernel(SmmArgs a) {
+    __shared__ int64_t scan[kSerialWarps + 1];
     __shared__ int64_t carry, seg_carry;
     const int tid = threadIdx.x;
     SmmCtl* C = a.ctl;
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(kCta) smm_alloc_kernel(SmmArgs a) {
     __syncthreads();
     int32_t* seg_q = a.seg_q[parity];
     int64_t* seg_off = a.seg_off[parity];
-    for (int64_t tile = 0; tile < a.nq; tile += kCta) {
+    for (int64_t tile = 0; tile < a.nq; tile += kSerialCta) {
         const int64_t q = tile + tid;
         int64_t want = 0;
         if (q < a.nq) {
@@ -210,8 +210,8 @@ __global__ void __launch_bounds__(kCta) smm_alloc_kernel(SmmArgs a) {
             M->run = M->dense ? M->dgo : (want > 0);
         }
         int64_t tot, ntot;
-        const int64_t ex = cta_excl_scan(want, scan, &tot);
-        const int64_t sx = cta_excl_scan(want > 0 ? 1 : 0, scan, &ntot);
+        const int64_t ex = cta_excl_scan_w<kSerialWarps>(want, scan, &tot);
+        const int64_t sx = cta_excl_scan_w<kSerialWarps>(want > 0 ? 1 : 0, scan, &ntot);
         if (want > 0) {
             const int64_t off = (int64_t)base + carry + ex;
             QSmm* M = a.sm + q;
@@ -644,16 +644,16 @@ __global__ void smm_advance_kernel(SmmArgs a, cudaGraphConditionalHandle h, int 
 // launchers
 // ---------------------------------------------------------------------------
 void launch_smm_setup(const SmmArgs& a, cudaStream_t st) {
-    const int grid = (int)std::min<int64_t>((a.nq + 255) / 256, 1024);
+    const int grid = query_grid(a.nq);
     prof_begin(FAM_SMM_SETUP, st);
-    smm_setup_kernel<<<grid, 256, 0, st>>>(a);
+    smm_setup_kernel<<<grid, kQueryCta, 0, st>>>(a);
     prof_end(FAM_SMM_SETUP, st);
     note_launches(1);
 }
 
 void launch_smm_alloc(const SmmArgs& a, cudaStream_t st) {
     prof_begin(FAM_SMM_ALLOC, st);
-    smm_alloc_kernel<<<1, kCta, 0, st>>>(a);
+    smm_alloc_kernel<<<1, kSerialCta, 0, st>>>(a);
     prof_end(FAM_SMM_ALLOC, st);
     note_launches(1);
 }
@@ -666,9 +666,9 @@ void launch_smm_clear(const SmmArgs& a, int grid, cudaStream_t st) {
 }
 
 void launch_smm_seed(const SmmArgs& a, cudaStream_t st) {
-    const int grid = (int)std::min<int64_t>((a.nq + 255) / 256, 1024);
+    const int grid = query_grid(a.nq);
     prof_begin(FAM_SMM_PUSH, st);
-    smm_seed_kernel<<<grid, 256, 0, st>>>(a);
+    smm_seed_kernel<<<grid, kQueryCta, 0, st>>>(a);
     prof_end(FAM_SMM_PUSH, st);
     note_launches(1);
 }
@@ -702,11 +702,11 @@ void launch_smm_top2(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
 }
 
 void launch_smm_decide(const SmmArgs& a, cudaStream_t st, bool first) {
-    const int grid = (int)std::min<int64_t>((a.nq + 255) / 256, 1024);
+    const int grid = query_grid(a.nq);
     // the first decision (l_b = 0) is the rule's "run at least once"
     if (!first && a.policy == 1 && a.mlp_w != nullptr) launch_smm_mlp(a, st);
     prof_begin(FAM_SMM_DECIDE, st);
-    smm_decide_kernel<<<grid, 256, 0, st>>>(a);
+    smm_decide_kernel<<<grid, kQueryCta, 0, st>>>(a);
     prof_end(FAM_SMM_DECIDE, st);
     note_launches(1);
 }
