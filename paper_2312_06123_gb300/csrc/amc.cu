@@ -51,7 +51,12 @@ __device__ __forceinline__ const int32_t* row_base(const DevGraph& g, int32_t w,
 __device__ __forceinline__ void chunk_layout(int64_t eta, int64_t maxc, int64_t* ppc, int64_t* nch) {
     const int64_t unit = kWalksPerLane * kPairsPerWarpRound;
     const int64_t units = (eta + unit - 1) / unit;
-    const int64_t c = units < maxc ? units : maxc;
+    if (units <= maxc) {  // one warp round a chunk (the general case below, without its divisions)
+        *ppc = unit;
+        *nch = units;
+        return;
+    }
+    const int64_t c = maxc;
     *ppc = unit * ((units + c - 1) / c);
     *nch = (eta + *ppc - 1) / *ppc;
 }
@@ -99,6 +104,36 @@ __device__ void schedule_cta(const AmcArgs& a, int nb) {
     }
 }
 
+constexpr int kSmemChunkBegin = 2048;  // chunk prefix entries a walk CTA holds in shared memory
+
+// Chunk counts of the next walk launch, for batches whose prefix each walk
+// CTA builds itself (up to kSmemChunkBegin - 1 queries): the count of every
+// query in AMC over the launch's batches (nb of them), its walk record's
+// eta, and a fresh ticket counter.
+__device__ void count_cta(const AmcArgs& a, int nb) {
+    const int64_t maxc = kMaxChunksPerQuery / nb;
+    for (int64_t q = threadIdx.x; q < a.nq; q += blockDim.x) {
+        int32_t nch = 0;
+        const QState* Q = a.st + q;
+        if (Q->status == ST_AMC) {
+            const int64_t eta = Q->eta;
+            for (int i = 0; i < nb; ++i) {
+                int64_t ppc, n;
+                chunk_layout(eta << i, maxc, &ppc, &n);
+                nch += (int32_t)n;
+            }
+            a.wq[q].eta = eta;
+        }
+        a.chunk_count[q] = nch;
+    }
+    if (threadIdx.x == 0) *a.walk_ctr = 0ull;
+}
+
+__device__ void schedule_first(const AmcArgs& a, int nb) {
+    if (a.nq + 1 <= kSmemChunkBegin) count_cta(a, nb);
+    else schedule_cta(a, nb);
+}
+
 // Batches walked together at the start (when cheap), and the walk steps
 // below which they are: the speculative batches cost at most this much, the
 // launches they save are latency-bound.
@@ -124,7 +159,7 @@ __global__ void __launch_bounds__(kCta) amc_schedule_kernel(AmcArgs a) {
     __syncthreads();
     const int group = tot <= (unsigned long long)kAmcGroupSteps ? nb : 1;
     if (threadIdx.x == 0) *a.group = group;
-    schedule_cta(a, group);
+    schedule_first(a, group);
 }
 
 // g of a node whose first probe `p` (slot h) is already loaded
@@ -141,7 +176,6 @@ __device__ __forceinline__ double resolve_g(const GEntry* tab, int32_t mask, int
 // k0 + i + 16 w (w < W), from s and from t. The W walks of a lane advance in
 // lockstep so that their loads overlap; each step issues the next node's
 // row record and its first lookup probe together.
-constexpr int kSmemChunkBegin = 2048;  // chunk_begin entries staged in shared memory
 #ifndef GEER_WALK_MINB
 #define GEER_WALK_MINB 4
 #endif
@@ -318,18 +352,32 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
 template <int W, bool REC>
 __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a) {
     __shared__ int64_t cbeg[kSmemChunkBegin];
-    const bool staged = a.nq + 1 <= kSmemChunkBegin;
-    if (staged)
-        for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) cbeg[i] = a.chunk_begin[i];
-    __syncthreads();
-    const int64_t* cb_arr = staged ? cbeg : a.chunk_begin;
-    const int lane = threadIdx.x & 31;
-    const int64_t total = cb_arr[a.nq];
+    __shared__ int64_t scan[kWarps + 1];
     // batches of this launch: the first launch walks *a.group batches, the
     // launches of batches it covered have nothing to do
     const int group = *a.group;
     if (a.batch > 1 && a.batch <= group) return;
     const int nbatch = a.batch == 1 ? group : 1;
+    // chunk prefix over the queries: built here from the per-query counts
+    // (small batches), else laid out by the schedule
+    const bool staged = a.nq + 1 <= kSmemChunkBegin;
+    if (staged) {
+        int64_t carry = 0;
+        for (int64_t tile = 0; tile < a.nq; tile += kCta) {
+            const int64_t q = tile + threadIdx.x;
+            int64_t tot;
+            const int64_t ex = cta_excl_scan(q < a.nq ? (int64_t)a.chunk_count[q] : 0, scan, &tot);
+            if (q < a.nq) cbeg[q] = carry + ex;
+            carry += tot;
+        }
+        if (threadIdx.x == 0) cbeg[a.nq] = carry;
+        __syncthreads();
+        if (blockIdx.x == 0)  // for the statistics launch that follows
+            for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) a.chunk_begin[i] = cbeg[i];
+    }
+    const int64_t* cb_arr = staged ? cbeg : a.chunk_begin;
+    const int lane = threadIdx.x & 31;
+    const int64_t total = cb_arr[a.nq];
     for (;;) {
         // chunks are handed out in order by a ticket counter
         unsigned long long ticket = 0;
@@ -438,13 +486,31 @@ __global__ void __launch_bounds__(kCta) amc_reduce_kernel(AmcArgs a) {
     const int nbatch = a.batch == 1 ? group : 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t q = (int64_t)blockIdx.x * kWarps + warp;
+    const bool staged = a.nq + 1 <= kSmemChunkBegin;
     if (q < a.nq) {
         QState* Q = a.st + q;
-        if (Q->status == ST_AMC)  // uniform across the warp
-            evaluate_batches(a, Q, a.chunk_begin[q], Q->eta, a.batch, nbatch, lane);
+        if (Q->status == ST_AMC) {  // uniform across the warp
+            const int stop = evaluate_batches(a, Q, a.chunk_begin[q], Q->eta, a.batch, nbatch, lane);
+            if (staged && lane == 0 && a.batch + nbatch <= a.tau) {
+                // the next launch's chunks of the query (one batch)
+                int32_t nch = 0;
+                if (!stop) {
+                    const int64_t eta = __ldcg(reinterpret_cast<const long long*>(&Q->eta));
+                    int64_t ppc, n;
+                    chunk_layout(eta, kMaxChunksPerQuery, &ppc, &n);
+                    nch = (int32_t)n;
+                    a.wq[q].eta = eta;
+                }
+                a.chunk_count[q] = nch;
+            }
+        }
     }
     const int next = a.batch + nbatch;
     if (next > a.tau) return;  // no next batch to lay out
+    if (staged) {  // each walk CTA builds the prefix; only the ticket counter is reset here
+        if (blockIdx.x == 0 && threadIdx.x == 0) *a.walk_ctr = 0ull;
+        return;
+    }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(a.done, 1u) == gridDim.x - 1;

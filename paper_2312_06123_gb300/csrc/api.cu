@@ -143,6 +143,7 @@ struct Workspace {
     double* r = nullptr;
     ger_query_stats* stats = nullptr;
     int64_t* chunk_begin = nullptr;
+    int32_t* chunk_count = nullptr;
     WalkQ* wq = nullptr;
     Partial* partial = nullptr;
     int64_t partial_cap = 0;
@@ -236,7 +237,7 @@ namespace geer {
 static void free_ws(Workspace& w) {
     cudaFree(w.st); cudaFree(w.s); cudaFree(w.t); cudaFree(w.eps); cudaFree(w.r); cudaFree(w.stats);
     cudaFree(w.chunk_begin); cudaFree(w.partial); cudaFree(w.qsmm); cudaFree(w.seg_q); cudaFree(w.seg_off);
-    cudaFree(w.wq);
+    cudaFree(w.wq); cudaFree(w.chunk_count);
     cudaFree(w.ctl); cudaFree(w.ent); cudaFree(w.sums); cudaFree(w.yvals); cudaFree(w.counters);
     cudaFree(w.heavy);
     cudaFree(w.dX[0]); cudaFree(w.dX[1]);
@@ -264,16 +265,17 @@ static int ensure_ws(ger_graph* g, int64_t q, int64_t pool_cap) {
     if (q > w.q_cap) {
         cudaFree(w.st); cudaFree(w.s); cudaFree(w.t); cudaFree(w.eps); cudaFree(w.r); cudaFree(w.stats);
         cudaFree(w.chunk_begin); cudaFree(w.partial); cudaFree(w.qsmm); cudaFree(w.seg_q); cudaFree(w.seg_off);
-        cudaFree(w.wq);
+        cudaFree(w.wq); cudaFree(w.chunk_count);
         w.st = nullptr; w.s = nullptr; w.t = nullptr; w.eps = nullptr; w.r = nullptr; w.stats = nullptr;
         w.chunk_begin = nullptr; w.partial = nullptr; w.qsmm = nullptr; w.seg_q = nullptr; w.seg_off = nullptr;
-        w.wq = nullptr;
+        w.wq = nullptr; w.chunk_count = nullptr;
         w.q_cap = 0;
         const int64_t qc = std::max<int64_t>(q, 64);
         const int64_t pc = qc * kMaxChunksPerQuery;
         if (alloc(&w.st, qc) || alloc(&w.s, qc) || alloc(&w.t, qc) || alloc(&w.eps, qc) || alloc(&w.r, qc) ||
             alloc(&w.stats, qc) || alloc(&w.chunk_begin, qc + 1) || alloc(&w.partial, pc) ||
-            alloc(&w.qsmm, qc) || alloc(&w.seg_q, 2 * qc) || alloc(&w.seg_off, 2 * (qc + 1)) || alloc(&w.wq, qc)) {
+            alloc(&w.qsmm, qc) || alloc(&w.seg_q, 2 * qc) || alloc(&w.seg_off, 2 * (qc + 1)) || alloc(&w.wq, qc) ||
+            alloc(&w.chunk_count, qc)) {
             cudaGetLastError();
             return fail(GER_ERR_OOM, "workspace for %lld queries", (long long)q);
         }
@@ -621,6 +623,7 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
     m.nq = (int32_t)nq;
     m.st = w.st + q0;
     m.chunk_begin = w.chunk_begin;
+    m.chunk_count = w.chunk_count;
     m.wq = w.wq + q0;
     m.walk_ctr = reinterpret_cast<unsigned long long*>(w.counters + 4);
     m.group = w.counters + 6;

@@ -94,7 +94,8 @@ struct AmcArgs {
     DevGraph g;
     int32_t nq;
     QState* st;
-    int64_t* chunk_begin;  // nq + 1
+    int64_t* chunk_begin;  // nq + 1: chunk prefix of the next walk launch (above kSmemChunkBegin - 1 queries)
+    int32_t* chunk_count;  // nq: chunks per query of the next walk launch (up to kSmemChunkBegin - 1 queries)
     WalkQ* wq;             // nq walk records, packed by the schedule
     unsigned long long* walk_ctr;  // next chunk of the batch (reset by the schedule)
     unsigned int* done;    // CTA counter of the fused reduce (last CTA schedules)

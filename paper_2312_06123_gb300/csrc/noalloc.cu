@@ -42,7 +42,8 @@ constexpr int64_t kNoAllocHeavy = 4096;
 constexpr size_t kOffHeavy = align256(kOffSegOff + sizeof(int64_t) * 2 * (kNoAllocMaxQueries + 1));
 constexpr size_t kOffChunk = align256(kOffHeavy + sizeof(int64_t) * kNoAllocHeavy);
 constexpr size_t kOffWalkQ = align256(kOffChunk + sizeof(int64_t) * (kNoAllocMaxQueries + 1));
-constexpr size_t kOffPartial = align256(kOffWalkQ + sizeof(WalkQ) * kNoAllocMaxQueries);
+constexpr size_t kOffCount = align256(kOffWalkQ + sizeof(WalkQ) * kNoAllocMaxQueries);
+constexpr size_t kOffPartial = align256(kOffCount + sizeof(int32_t) * kNoAllocMaxQueries);
 constexpr size_t kOffEnt = align256(kOffPartial + sizeof(Partial) * kNoAllocMaxQueries * kMaxChunksPerQuery);
 constexpr size_t kOffSums = align256(kOffEnt + sizeof(GEntry) * kNoAllocPool);
 constexpr size_t kOffY = align256(kOffSums + sizeof(uint64_t) * 2 * kNoAllocPool);
@@ -190,6 +191,7 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     m.st = qs;
     m.chunk_begin = reinterpret_cast<int64_t*>(base + kOffChunk);
     m.wq = reinterpret_cast<WalkQ*>(base + kOffWalkQ);
+    m.chunk_count = reinterpret_cast<int32_t*>(base + kOffCount);
     m.walk_ctr = reinterpret_cast<unsigned long long*>(counters + 4);  // inside the 64-byte counter region
     m.done = reinterpret_cast<unsigned int*>(counters + 2);
     m.partial = reinterpret_cast<Partial*>(base + kOffPartial);
