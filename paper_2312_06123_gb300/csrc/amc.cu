@@ -404,98 +404,110 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
     }
 }
 
-// Batch statistics (Algorithm 1: Z, the empirical variance, f of Eq. (7) at
-// delta/tau) and the stop / doubling decision of one query for its batches
-// batch0 .. batch0 + nbatch - 1 in order, from the chunk partials at
-// `begin`, until the query stops (the walks of later batches are then not
-// used). The whole warp calls it; lane 0 updates the query state. Reads and
-// writes go through L2, so that another SM's warp can take the query over.
-// Returns 1 (warp-uniform) when the query stopped.
-__device__ int evaluate_batches(const AmcArgs& a, QState* Q, int64_t begin, int64_t eta, int batch0, int nbatch,
-                                int lane) {
-    const int64_t maxc = kMaxChunksPerQuery / nbatch;
-    // the query's state, loaded once (independent loads, issued together)
-    double psi = 0.0, qeps = 0.0, r_b = 0.0;
-    int64_t walks = 0, steps = 0;
-    unsigned long long chk = 0;
-    int32_t lf = 0;
-    if (lane == 0) {
-        psi = __ldcg(&Q->psi);
-        qeps = __ldcg(&Q->eps);
-        r_b = __ldcg(&Q->r_b);
-        walks = __ldcg(reinterpret_cast<const long long*>(&Q->walks));
-        steps = __ldcg(reinterpret_cast<const long long*>(&Q->walk_steps));
-        chk = __ldcg(reinterpret_cast<const unsigned long long*>(&Q->checksum));
-        lf = __ldcg(&Q->lf);
+// Sums of Z_k, Z_k^2 and the walk checksum over one batch of one query, from
+// its nch chunk partials at `begin`, in a fixed order (lane-strided, then a
+// warp reduction). The whole warp calls it; every lane gets the sums.
+__device__ __forceinline__ void batch_sums(const AmcArgs& a, int64_t begin, int64_t nch, int lane, double* sz,
+                                           double* sz2, uint64_t* cs) {
+    double x = 0.0, x2 = 0.0;
+    uint64_t c = 0;
+    for (int64_t i = lane; i < nch; i += 32) {
+        const Partial p = a.partial[begin + i];
+        x += p.sz;
+        x2 += p.sz2;
+        c += p.cs;
     }
-    const double delta_b = a.delta / (double)a.tau;
-    const double Lg = log(3.0 / delta_b);
-    for (int bi = 0; bi < nbatch; ++bi) {
-        const int batch = batch0 + bi;
-        int64_t ppc, nch;
-        chunk_layout(eta, maxc, &ppc, &nch);
-        double sz = 0.0, sz2 = 0.0;
-        uint64_t cs = 0;
-        for (int64_t i = lane; i < nch; i += 32) {
-            const Partial* p = a.partial + begin + i;
-            sz += __ldcg(&p->sz);
-            sz2 += __ldcg(&p->sz2);
-            cs += __ldcg(reinterpret_cast<const unsigned long long*>(&p->cs));
-        }
-        sz = warp_sum(sz);
-        sz2 = warp_sum(sz2);
-        cs = warp_sum(cs);
-        int stop = 0;
-        if (lane == 0) {
-            const double Z = sz / (double)eta;
-            double var = sz2 / (double)eta - Z * Z;
-            if (var < 0.0) var = 0.0;
-            const double f = sqrt(2.0 * var * Lg / (double)eta) + 3.0 * psi * Lg / (double)eta;
-            walks += eta;
-            steps += 2 * eta * (int64_t)lf;
-            chk += cs;
-            stop = f <= qeps / 2.0 || batch >= a.tau;
-            if (stop || bi == nbatch - 1) {
-                __stcg(reinterpret_cast<long long*>(&Q->walks), (long long)walks);
-                __stcg(reinterpret_cast<long long*>(&Q->walk_steps), (long long)steps);
-                __stcg(reinterpret_cast<unsigned long long*>(&Q->checksum), chk);
-                __stcg(&Q->batch, batch);
-                __stcg(&Q->f_last, f);
-                if (stop) {
-                    __stcg(&Q->r_f, Z);
-                    __stcg(&Q->r, r_b + Z);
-                    __stcg(&Q->status, (int32_t)ST_DONE);
-                } else {
-                    __stcg(reinterpret_cast<long long*>(&Q->eta), (long long)(2 * eta));
-                }
-            }
-        }
-        if (__shfl_sync(0xffffffffu, stop, 0)) return 1;
-        begin += nch;
-        eta *= 2;
-    }
-    return 0;
+    *sz = warp_sum(x);
+    *sz2 = warp_sum(x2);
+    *cs = warp_sum(c);
 }
 
-// Launch-per-batch statistics: one warp per query over the launch's batches;
-// the last CTA to finish lays out the next launch (one batch).
+// Queries per CTA of the statistics kernel, one per warp for the partial
+// sums (their loads are a latency chain per query); the per-query scalar FP64
+// work (Eq. (7): divisions, a logarithm, a square root) then runs one query
+// per lane of warp 0, since a single-lane FP64 instruction holds the SM's
+// narrow FP64 pipe as long as a full warp's.
+constexpr int kReduceQ = kWarps;
+
+// Launch-per-batch statistics (Algorithm 1: Z, the empirical variance, f of
+// Eq. (7) at delta/tau) and the stop / doubling decision of each query in
+// AMC, for the launch's batches in order until the query stops (the walks of
+// later batches of the launch are then not used). A CTA takes kReduceQ
+// queries: its warps add the queries' chunk partials, then warp 0 decides,
+// one query per lane. For small batches it also writes the next launch's
+// chunk counts; for large ones the last CTA to finish lays out the next
+// launch (one batch).
 __global__ void __launch_bounds__(kCta) amc_reduce_kernel(AmcArgs a) {
+    __shared__ double s_sz[kAmcGroup][kReduceQ], s_sz2[kAmcGroup][kReduceQ];
+    __shared__ unsigned long long s_cs[kAmcGroup][kReduceQ];
     __shared__ bool last;
     const int group = *a.group;
     if (a.batch > 1 && a.batch <= group) return;  // walked and evaluated with batch 1
     const int nbatch = a.batch == 1 ? group : 1;
+    const int64_t maxc = kMaxChunksPerQuery / nbatch;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t q = (int64_t)blockIdx.x * kWarps + warp;
+    const int64_t q0 = (int64_t)blockIdx.x * kReduceQ;
     const bool staged = a.nq + 1 <= kSmemChunkBegin;
-    if (q < a.nq) {
+    // the batches' sums, one query per warp at a time
+    for (int j = warp; j < kReduceQ; j += kWarps) {
+        const int64_t q = q0 + j;
+        if (q >= a.nq || a.st[q].status != ST_AMC) continue;
+        int64_t begin = a.chunk_begin[q], eta = a.st[q].eta;
+        for (int bi = 0; bi < nbatch; ++bi) {
+            int64_t ppc, nch;
+            chunk_layout(eta, maxc, &ppc, &nch);
+            double sz, sz2;
+            uint64_t cs;
+            batch_sums(a, begin, nch, lane, &sz, &sz2, &cs);
+            if (lane == 0) {
+                s_sz[bi][j] = sz;
+                s_sz2[bi][j] = sz2;
+                s_cs[bi][j] = cs;
+            }
+            begin += nch;
+            eta *= 2;
+        }
+    }
+    __syncthreads();
+    if (warp == 0 && lane < kReduceQ) {
+        const int64_t q = q0 + lane;
         QState* Q = a.st + q;
-        if (Q->status == ST_AMC) {  // uniform across the warp
-            const int stop = evaluate_batches(a, Q, a.chunk_begin[q], Q->eta, a.batch, nbatch, lane);
-            if (staged && lane == 0 && a.batch + nbatch <= a.tau) {
+        if (q < a.nq && Q->status == ST_AMC) {
+            const double delta_b = a.delta / (double)a.tau;
+            const double Lg = log(3.0 / delta_b);
+            const double psi = Q->psi, qeps = Q->eps, r_b = Q->r_b;
+            const int32_t lf = Q->lf;
+            int64_t eta = Q->eta, walks = Q->walks, steps = Q->walk_steps;
+            uint64_t chk = Q->checksum;
+            bool stop = false;
+            for (int bi = 0; bi < nbatch && !stop; ++bi) {
+                const int batch = a.batch + bi;
+                const double Z = s_sz[bi][lane] / (double)eta;
+                double var = s_sz2[bi][lane] / (double)eta - Z * Z;
+                if (var < 0.0) var = 0.0;
+                const double f = sqrt(2.0 * var * Lg / (double)eta) + 3.0 * psi * Lg / (double)eta;
+                walks += eta;
+                steps += 2 * eta * (int64_t)lf;
+                chk += s_cs[bi][lane];
+                Q->batch = batch;
+                Q->f_last = f;
+                if (f <= qeps / 2.0 || batch >= a.tau) {
+                    Q->r_f = Z;
+                    Q->r = r_b + Z;
+                    Q->status = ST_DONE;
+                    stop = true;
+                } else {
+                    eta *= 2;
+                }
+            }
+            Q->walks = walks;
+            Q->walk_steps = steps;
+            Q->checksum = chk;
+            Q->eta = eta;  // the next batch's pairs, or the last batch's on a stop
+            if (staged && a.batch + nbatch <= a.tau) {
                 // the next launch's chunks of the query (one batch)
                 int32_t nch = 0;
                 if (!stop) {
-                    const int64_t eta = __ldcg(reinterpret_cast<const long long*>(&Q->eta));
                     int64_t ppc, n;
                     chunk_layout(eta, kMaxChunksPerQuery, &ppc, &n);
                     nch = (int32_t)n;
@@ -563,7 +575,7 @@ void launch_amc_walk(const AmcArgs& a, int sm_count, cudaStream_t st) {
 }
 
 void launch_amc_reduce(const AmcArgs& a, cudaStream_t st) {
-    const int grid = (int)((a.nq + kWarps - 1) / kWarps);
+    const int grid = (int)((a.nq + kReduceQ - 1) / kReduceQ);
     prof_begin(FAM_AMC_REDUCE, st);
     amc_reduce_kernel<<<grid, kCta, 0, st>>>(a);
     prof_end(FAM_AMC_REDUCE, st);
