@@ -39,7 +39,7 @@ WALK_STEP_BYTES = 20  # row_ptr pair 8 B + one col_idx 4 B + one (s*, t*) FP32 p
 SPMM_TRAFFIC: dict = {("c2", 128): 6_261_000_000 + 501_000_000}
 # DRAM bytes per walk step of amc_walk (ncu, all 5 AMC launches of the workload's batch):
 # profiles/amc_walk_c2_bench.md
-WALK_TRAFFIC_PER_STEP: dict = {"c2": (571_263_000 + 10_565_000) / 18_505_638}
+WALK_TRAFFIC_PER_STEP: dict = {"c2": (571_229_000 + 10_544_000) / 18_505_638}
 
 
 def _peaks():
