@@ -19,6 +19,11 @@
 // first three batches' walks are few, they share the first launch (the
 // chunks of a query are its batch-1, then batch-2, then batch-3 chunks) and
 // the reduce evaluates them in order, ignoring batches after a stop.
+// A launch's chunks are numbered query by query. For batches of up to
+// kSmemChunkBegin - 1 queries the schedule and the reduce write per-query
+// chunk counts and every walk CTA builds the prefix in shared memory (CTA 0
+// also stores it for the reduce); larger batches get the prefix from a
+// one-CTA layout.
 #include "geer_internal.cuh"
 #include "geer_kernels.h"
 
@@ -63,8 +68,9 @@ __device__ __forceinline__ void chunk_layout(int64_t eta, int64_t maxc, int64_t*
 
 // Chunk layout of the next walk launch (batches b .. b + nb - 1, batch i of
 // a query having eta * 2^(i - b) pairs) for every query still in AMC, by one
-// CTA: per query its chunk count over the launch's batches, and their prefix
-// in chunk_begin. Reads the query state through the L2 (it was written by
+// CTA, for batches too large for a walk CTA's shared-memory prefix: per query
+// its chunk count over the launch's batches, and their prefix in
+// chunk_begin. Reads the query state through the L2 (it was written by
 // other CTAs of the same kernel).
 __device__ void schedule_cta(const AmcArgs& a, int nb) {
     __shared__ int64_t scan[kWarps + 1];

@@ -648,7 +648,7 @@ static void issue_amc(ger_graph* g, AmcArgs m, int64_t nq, cudaStream_t st) {
     for (int b = 1; b <= m.tau; ++b) {
         m.batch = b;
         launch_amc_walk(m, g->sm_count, st);
-        launch_amc_reduce(m, st);  // its last CTA lays out the next launch
+        launch_amc_reduce(m, st);  // it also lays out the next launch
     }
     note_launches(1 + 2 * m.tau);
 }

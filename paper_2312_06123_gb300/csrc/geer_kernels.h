@@ -98,7 +98,7 @@ struct AmcArgs {
     int32_t* chunk_count;  // nq: chunks per query of the next walk launch (up to kSmemChunkBegin - 1 queries)
     WalkQ* wq;             // nq walk records, packed by the schedule
     unsigned long long* walk_ctr;  // next chunk of the batch (reset by the schedule)
-    unsigned int* done;    // CTA counter of the fused reduce (last CTA schedules)
+    unsigned int* done;    // CTA counter of the reduce (its last CTA lays out large batches)
     Partial* partial;
     int64_t partial_cap;
     const GEntry* pool;
@@ -148,7 +148,7 @@ void launch_amc_schedule(const AmcArgs& a, cudaStream_t st);
 void launch_edge_records(const int32_t* col_idx, const uint2* node_info, int64_t nnz, uint4* out, cudaStream_t st);
 // one persistent grid (as many CTAs as fit on the GPU) over the batch's chunks
 void launch_amc_walk(const AmcArgs& a, int sm_count, cudaStream_t st);
-// batch statistics of batch a.batch; the last CTA schedules batch a.batch + 1
+// batch statistics of the launch's batches and the next launch's layout
 void launch_amc_reduce(const AmcArgs& a, cudaStream_t st);
 
 }  // namespace geer

@@ -208,7 +208,7 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     for (int b = 1; b <= o.tau; ++b) {
         m.batch = b;
         launch_amc_walk(m, sm_count, st);
-        launch_amc_reduce(m, st);  // its last CTA lays out the next launch
+        launch_amc_reduce(m, st);  // it also lays out the next launch
     }
     launch_finalize(qs, q, r_dev, stats_dev, st);
     note_launches(2 + 2 * o.tau);
