@@ -110,7 +110,9 @@ __device__ void schedule_cta(const AmcArgs& a, int nb) {
     }
 }
 
-constexpr int kSmemChunkBegin = 2048;  // chunk prefix entries a walk CTA holds in shared memory
+// chunk prefix entries a walk CTA holds in shared memory (int32: a small
+// batch has at most 4095 x kMaxChunksPerQuery chunks)
+constexpr int kSmemChunkBegin = 4096;
 
 // Chunk counts of the next walk launch, for batches whose prefix each walk
 // CTA builds itself (up to kSmemChunkBegin - 1 queries): the count of every
@@ -357,7 +359,7 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
 // launch's layout (chunk_begin) from a ticket counter.
 template <int W, bool REC>
 __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a) {
-    __shared__ int64_t cbeg[kSmemChunkBegin];
+    __shared__ int32_t cbeg[kSmemChunkBegin];
     __shared__ int64_t scan[kWarps + 1];
     // batches of this launch: the first launch walks *a.group batches, the
     // launches of batches it covered have nothing to do
@@ -373,17 +375,18 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
             const int64_t q = tile + threadIdx.x;
             int64_t tot;
             const int64_t ex = cta_excl_scan(q < a.nq ? (int64_t)a.chunk_count[q] : 0, scan, &tot);
-            if (q < a.nq) cbeg[q] = carry + ex;
+            if (q < a.nq) cbeg[q] = (int32_t)(carry + ex);
             carry += tot;
         }
-        if (threadIdx.x == 0) cbeg[a.nq] = carry;
+        if (threadIdx.x == 0) cbeg[a.nq] = (int32_t)carry;
         __syncthreads();
         if (blockIdx.x == 0)  // for the statistics launch that follows
             for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) a.chunk_begin[i] = cbeg[i];
     }
-    const int64_t* cb_arr = staged ? cbeg : a.chunk_begin;
+    const int64_t* cb_glob = a.chunk_begin;
+    auto cb_arr = [&](int i) -> int64_t { return staged ? (int64_t)cbeg[i] : cb_glob[i]; };
     const int lane = threadIdx.x & 31;
-    const int64_t total = cb_arr[a.nq];
+    const int64_t total = cb_arr(a.nq);
     for (;;) {
         // chunks are handed out in order by a ticket counter
         unsigned long long ticket = 0;
@@ -394,12 +397,12 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
         int lo = 0, hi = a.nq + 1;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            if (cb_arr[mid] <= c) lo = mid + 1; else hi = mid;
+            if (cb_arr(mid) <= c) lo = mid + 1; else hi = mid;
         }
         const WalkQ* WQ = a.wq + (lo - 1);
         double sz, sz2;
         uint64_t cs;
-        walk_chunk<W, REC>(a, WQ, c - cb_arr[lo - 1], WQ->eta, a.batch, nbatch, lane, &sz, &sz2, &cs);
+        walk_chunk<W, REC>(a, WQ, c - cb_arr(lo - 1), WQ->eta, a.batch, nbatch, lane, &sz, &sz2, &cs);
         if (lane == 0) {
             Partial p;
             p.sz = sz;
