@@ -37,9 +37,11 @@ WALK_STEP_BYTES = 20  # row_ptr pair 8 B + one col_idx 4 B + one (s*, t*) FP32 p
 # DRAM bytes (read + write) per dense_spmm launch from the ncu capture of the
 # current kernel, per (workload, width): profiles/dense_spmm_c2_w128.md
 SPMM_TRAFFIC: dict = {("c2", 128): 6_261_000_000 + 501_000_000}
-# DRAM bytes per walk step of amc_walk (ncu, all 5 AMC launches of the workload's batch):
-# profiles/amc_walk_c2_bench.md
-WALK_TRAFFIC_PER_STEP: dict = {"c2": (571_229_000 + 10_544_000) / 18_505_638}
+# DRAM bytes per walk step of amc_walk (ncu, all 5 AMC launches of the workload's batch), for the
+# kernel as captured in profiles/amc_walk_c2_bench.md. Empty while the kernel has changed since its
+# last capture (the traffic is then reported as null): the capture there (31.4 B per step) predates
+# the int32 chunk prefix of the walk CTAs.
+WALK_TRAFFIC_PER_STEP: dict = {}
 
 
 def _peaks():
@@ -462,7 +464,8 @@ def main():
         roof = {"kernel": "amc_walk", "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": None if tps is None else tps * walk_steps / (nl / args.steps),
-                "traffic_note": "ncu DRAM bytes per walk step x this run's walk steps per launch",
+                "traffic_note": ("ncu DRAM bytes per walk step x this run's walk steps per launch" if tps is not None
+                                 else "null: the kernel changed since its last ncu capture"),
                 "algorithmic_bytes_per_launch": per_launch_bytes}
     else:
         nl, tms = fam[1]
