@@ -37,11 +37,10 @@ WALK_STEP_BYTES = 20  # row_ptr pair 8 B + one col_idx 4 B + one (s*, t*) FP32 p
 # DRAM bytes (read + write) per dense_spmm launch from the ncu capture of the
 # current kernel, per (workload, width): profiles/dense_spmm_c2_w128.md
 SPMM_TRAFFIC: dict = {("c2", 128): 6_261_000_000 + 501_000_000}
-# DRAM bytes per walk step of amc_walk (ncu, all 5 AMC launches of the workload's batch), for the
-# kernel as captured in profiles/amc_walk_c2_bench.md. Empty while the kernel has changed since its
-# last capture (the traffic is then reported as null): the capture there (31.4 B per step) predates
-# the int32 chunk prefix of the walk CTAs.
-WALK_TRAFFIC_PER_STEP: dict = {}
+# DRAM bytes per walk step of amc_walk (ncu, all 5 AMC launches of the workload's batch, one-pass
+# DRAM counters on the current kernel): profiles/amc_walk_c2_bench.md. A workload missing here, or
+# a kernel changed since its capture, reports its traffic as null.
+WALK_TRAFFIC_PER_STEP: dict = {"c2": (571_255_000 + 4_224_000) / 18_505_638}
 
 
 def _peaks():
