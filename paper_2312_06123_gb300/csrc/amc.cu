@@ -34,10 +34,6 @@ namespace geer {
 #endif
 constexpr int kWalksPerLane = GEER_WALKS_PER_LANE;
 
-namespace {
-
-}  // namespace
-
 // Row start and degree of node w.
 __device__ __forceinline__ uint2 node_row(const DevGraph& g, int32_t w) {
     if (g.node_info) return __ldg(g.node_info + w);
@@ -188,8 +184,8 @@ __device__ __forceinline__ double resolve_g(const GEntry* tab, int32_t mask, int
 #define GEER_WALK_MINB 4
 #endif
 
-// Walks of chunk L of a work unit of query WQ: batches batch0 .. batch0 +
-// nbatch - 1 with eta pairs in batch0 (doubling), chunked by chunk_layout at
+// Walks of chunk L of query WQ in a launch that walks its batches batch0 ..
+// batch0 + nbatch - 1 (eta pairs in batch0, doubling), chunked by chunk_layout at
 // kMaxChunksPerQuery / nbatch chunks per batch. Returns the chunk's sums of
 // Z_k, Z_k^2 and the walk checksum, reduced over the warp.
 template <int W, bool REC>
