@@ -9,6 +9,8 @@ if the library is missing or cannot be loaded, every call raises.
 from __future__ import annotations
 
 import ctypes
+import hashlib
+import json
 import os
 
 import numpy as np
@@ -222,13 +224,66 @@ def mlp_train(x, target, weights, options: MlpTrainOptions | None = None):
     return w, loss[:o.epochs]
 
 
-class Graph:
-    """A graph resident on one GPU (ger_load_csr ... ger_free)."""
+# ---------------------------------------------------------------------------
+# spectral-bound sidecar: lambda depends on the graph alone (Section 3.1 computes it
+# once per graph), so it is kept in a small JSON file keyed by a hash of the CSR
+# ---------------------------------------------------------------------------
+LAMBDA_FORMAT = "geer-lambda-1"
 
-    def __init__(self, row_ptr, col_idx, device: int = 0):
+
+def csr_key(row_ptr, col_idx) -> str:
+    """Content key of a CSR graph: BLAKE2b-256 over n, nnz and both arrays."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    h = hashlib.blake2b(digest_size=32)
+    h.update(np.array([rp.shape[0] - 1, ci.shape[0]], np.int64).tobytes())
+    h.update(memoryview(rp).cast("B"))
+    h.update(memoryview(ci).cast("B"))
+    return h.hexdigest()
+
+
+def _lambda_path(cache_dir: str, key: str) -> str:
+    return os.path.join(cache_dir, f"lambda-{key}.json")
+
+
+def read_lambda_sidecar(cache_dir: str, key: str, n: int, nnz: int):
+    """(lambda, lambda_2, lambda_n) stored for this graph, or None (absent,
+    unreadable, or written for another graph)."""
+    try:
+        with open(_lambda_path(cache_dir, key)) as f:
+            d = json.load(f)
+        if d.get("format") != LAMBDA_FORMAT or d.get("key") != key or d.get("n") != n or d.get("nnz") != nnz:
+            return None
+        lam, l2, ln = float(d["lambda"]), float(d["lambda_2"]), float(d["lambda_n"])
+    except (OSError, ValueError, KeyError, TypeError):
+        return None
+    if not (0.0 <= lam < 1.0):
+        return None
+    return lam, l2, ln
+
+
+def write_lambda_sidecar(cache_dir: str, key: str, n: int, nnz: int, lam: float, l2: float, ln: float) -> str:
+    """Store the graph's spectral bound (written to a temporary file, then renamed)."""
+    os.makedirs(cache_dir, exist_ok=True)
+    path = _lambda_path(cache_dir, key)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump({"format": LAMBDA_FORMAT, "key": key, "n": int(n), "nnz": int(nnz), "lambda": float(lam),
+                   "lambda_2": float(l2), "lambda_n": float(ln)}, f)
+    os.replace(tmp, path)
+    return path
+
+
+class Graph:
+    """A graph resident on one GPU (ger_load_csr ... ger_free). With
+    keyed=True the CSR's content key is computed at load (a pass over the
+    arrays), so that spectral_bound(cache_dir=...) can keep lambda beside it."""
+
+    def __init__(self, row_ptr, col_idx, device: int = 0, keyed: bool = False):
         L = load_library()
         self._rp = _arr(row_ptr, np.int64)
         self._ci = _arr(col_idx, np.int32)
+        self.key = csr_key(self._rp, self._ci) if keyed else None
         h = _P()
         n = self._rp.shape[0] - 1
         _check(L.ger_load_csr(n, self._rp.ctypes.data_as(_P), self._ci.ctypes.data_as(_P), int(device),
@@ -239,8 +294,8 @@ class Graph:
         self._rp = self._ci = None  # the library holds its own copy
 
     @classmethod
-    def from_csr(cls, g, device: int = 0) -> "Graph":
-        return cls(g.row_ptr, g.col_idx, device)
+    def from_csr(cls, g, device: int = 0, keyed: bool = False) -> "Graph":
+        return cls(g.row_ptr, g.col_idx, device, keyed)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -253,10 +308,20 @@ class Graph:
         except Exception:
             pass
 
-    def spectral_bound(self):
-        """(lambda, lambda_2, lambda_n) computed on the GPU (Section 3.1)."""
+    def spectral_bound(self, cache_dir: str | None = None):
+        """(lambda, lambda_2, lambda_n) computed on the GPU (Section 3.1). With
+        cache_dir (and a keyed graph) a stored value is injected instead
+        (ger_set_spectral_bound), and a computed one is stored."""
+        use_cache = cache_dir is not None and self.key is not None
+        if use_cache:
+            hit = read_lambda_sidecar(cache_dir, self.key, self.n, self.nnz)
+            if hit is not None:
+                self.set_spectral_bound(hit[0])
+                return hit
         lam, l2, ln = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         _check(load_library().ger_spectral_bound(self._h, ctypes.byref(lam), ctypes.byref(l2), ctypes.byref(ln)))
+        if use_cache:
+            write_lambda_sidecar(cache_dir, self.key, self.n, self.nnz, lam.value, l2.value, ln.value)
         return lam.value, l2.value, ln.value
 
     def set_spectral_bound(self, lam: float):

@@ -166,6 +166,29 @@ def fit(G, s, t, eps, log: CostLog, options=None, kappas=(8.0, 32.0, 128.0), epo
     return best, times
 
 
+MODEL_FORMAT = "geer-switch-1"
+
+
+def save_model(model: SwitchModel, path: str) -> None:
+    """Store a trained switch (normalisation, FP16 weight bits, loss curve,
+    prices) as a .npz file."""
+    np.savez(path, format=np.array(MODEL_FORMAT), norm=np.asarray(model.norm, np.float32),
+             weights=np.asarray(model.weights, np.uint16), loss=np.asarray(model.loss, np.float32),
+             kappa=np.float64(model.kappa), mu=np.float64(model.mu))
+
+
+def load_model(path: str) -> SwitchModel:
+    """Read a switch stored by save_model; raises ValueError on a file of
+    another format or shape."""
+    with np.load(path) as z:
+        if str(z["format"]) != MODEL_FORMAT:
+            raise ValueError(f"{path}: not a stored switch ({z['format']})")
+        norm, w = z["norm"].astype(np.float32), z["weights"]
+        if norm.shape != (2 * MLP_INPUTS,) or w.shape != (MLP_PARAMS,) or w.dtype != np.uint16:
+            raise ValueError(f"{path}: stored switch of the wrong shape")
+        return SwitchModel(norm, w.copy(), z["loss"].astype(np.float32), float(z["kappa"]), float(z["mu"]))
+
+
 def init_weights(seed: int = 11) -> np.ndarray:
     """He-normal hidden layers, small output layer, zero biases (FP16 bits)."""
     rng = np.random.default_rng(seed)

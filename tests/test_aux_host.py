@@ -1,0 +1,62 @@
+"""Host-side auxiliaries: the CSR content key and the spectral-bound sidecar
+(lambda is a property of the graph alone, Section 3.1), and storing a trained
+learned switch. No GPU needed."""
+import json
+
+import numpy as np
+import pytest
+
+import paper_2312_06123_gb300 as geer
+from paper_2312_06123_gb300 import switch
+from synth import graphs
+
+
+def _csr():
+    g = graphs.chung_lu(300, 6.0, 2.5, 1, "t")
+    return g.row_ptr.copy(), g.col_idx.copy()
+
+
+def test_csr_key_follows_the_content():
+    rp, ci = _csr()
+    k = geer.csr_key(rp, ci)
+    assert k == geer.csr_key(rp.copy(), ci.copy()) and len(k) == 64
+    ci2 = ci.copy()
+    ci2[5] = ci2[6]
+    assert geer.csr_key(rp, ci2) != k
+    # the same bytes split differently between the arrays are another graph
+    assert geer.csr_key(rp[:-1], ci) != k
+
+
+def test_lambda_sidecar_round_trip_and_rejections(tmp_path):
+    d = str(tmp_path)
+    rp, ci = _csr()
+    key, n, nnz = geer.csr_key(rp, ci), len(rp) - 1, int(rp[-1])
+    assert geer.read_lambda_sidecar(d, key, n, nnz) is None
+    path = geer.write_lambda_sidecar(d, key, n, nnz, 0.8125, 0.8125, -0.75)
+    assert geer.read_lambda_sidecar(d, key, n, nnz) == (0.8125, 0.8125, -0.75)
+    assert geer.read_lambda_sidecar(d, key, n + 1, nnz) is None
+    assert geer.read_lambda_sidecar(d, key, n, nnz + 2) is None
+    rec = json.load(open(path))
+    for bad in ({"lambda": 1.0}, {"format": "other"}, {"key": "0" * 64}):
+        json.dump({**rec, **bad}, open(path, "w"))
+        assert geer.read_lambda_sidecar(d, key, n, nnz) is None
+    open(path, "w").write("{not json")
+    assert geer.read_lambda_sidecar(d, key, n, nnz) is None
+
+
+def test_switch_model_round_trip(tmp_path):
+    rng = np.random.default_rng(1)
+    m = switch.SwitchModel(norm=rng.normal(size=12).astype(np.float32), weights=switch.init_weights(4),
+                           loss=np.linspace(1, 0.1, 7).astype(np.float32), kappa=32.0, mu=1.5)
+    p = str(tmp_path / "switch.npz")
+    switch.save_model(m, p)
+    r = switch.load_model(p)
+    assert np.array_equal(r.norm, m.norm) and np.array_equal(r.weights, m.weights)
+    assert np.array_equal(r.loss, m.loss) and r.kappa == 32.0 and r.mu == 1.5
+    np.savez(p, format=np.array("other"), norm=m.norm, weights=m.weights, loss=m.loss, kappa=1.0, mu=0.0)
+    with pytest.raises(ValueError):
+        switch.load_model(p)
+    np.savez(p, format=np.array(switch.MODEL_FORMAT), norm=m.norm, weights=m.weights[:-1], loss=m.loss,
+             kappa=1.0, mu=0.0)
+    with pytest.raises(ValueError):
+        switch.load_model(p)

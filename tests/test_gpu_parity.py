@@ -4,6 +4,7 @@ Tolerances: FP64 path within 1e-9 relative of the oracle, FP32 path within
 1e-5 relative, walks bit-exact (count, steps and endpoint checksum) once the
 oracle replays the GPU's decisions; both paths within eps of the exact
 resistance (dense L^+)."""
+import json
 import math
 import os
 
@@ -79,6 +80,33 @@ def _check_against_oracle(w, g, lam, r, st, rel_r, rel_rb, max_disagree):
         dis += not all(agree.values())
     assert dis <= max_disagree, f"{dis} queries with a different free decision"
     return dis
+
+
+def test_spectral_bound_sidecar(c1, tmp_path):
+    # a computed lambda is stored beside the graph's content key; a later load
+    # of the same graph injects the stored value instead of computing it
+    w, g, _, _ = c1
+    d = str(tmp_path)
+    G = geer.Graph.from_csr(g, keyed=True)
+    got = G.spectral_bound(cache_dir=d)
+    files = list(tmp_path.glob("lambda-*.json"))
+    assert len(files) == 1
+    G2 = geer.Graph.from_csr(g, keyed=True)
+    assert G2.spectral_bound(cache_dir=d) == got
+    o = _opts(precision=geer.GER_FP64)
+    r1, s1 = G.query(w.s, w.t, w.eps, o, stats=True)
+    r2, s2 = G2.query(w.s, w.t, w.eps, o, stats=True)
+    assert np.array_equal(r1, r2) and np.array_equal(s1["ell"], s2["ell"])
+    # a stored value is what a keyed load uses: a larger lambda gives longer l
+    rec = json.load(open(files[0]))
+    rec["lambda"] = 0.5 * (1.0 + got[0])
+    json.dump(rec, open(files[0], "w"))
+    G3 = geer.Graph.from_csr(g, keyed=True)
+    assert G3.spectral_bound(cache_dir=d)[0] == rec["lambda"]
+    _, s3 = G3.query(w.s, w.t, w.eps, o, stats=True)
+    assert np.all(s3["ell"] >= s1["ell"]) and np.any(s3["ell"] > s1["ell"])
+    for h in (G, G2, G3):
+        h.close()
 
 
 def test_fp64_per_query_matches_oracle(c1):
