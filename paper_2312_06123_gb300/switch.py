@@ -25,6 +25,7 @@ walk, network evaluation, gradient and Adam step runs in the CUDA library
 from __future__ import annotations
 
 import copy
+import json
 import time
 from dataclasses import dataclass, field
 
@@ -124,6 +125,54 @@ def price(inputs, push, walks, ell, kappa: float, mu: float) -> CostLog:
                   np.asarray(rows_q, np.int64), np.asarray(rows_j, np.int64), cost, push, walks, ell, kappa, mu)
     out.inputs = inputs
     return out
+
+
+COSTLOG_FORMAT = "geer-costlog-1"
+
+
+def save_cost_log(log: CostLog, path: str) -> None:
+    """Store what a cost log measured as JSON lines: a header (format, prices,
+    iterations logged), then one line per query with l, the push sizes
+    push(0..steps), the walk steps walks(1..steps) of switching after each
+    iteration (null where not run) and the network inputs after each
+    iteration. The training rows are derived again on loading."""
+    q, steps = log.inputs.shape[0], log.inputs.shape[1]
+    with open(path, "w") as f:
+        f.write(json.dumps({"format": COSTLOG_FORMAT, "kappa": log.kappa, "mu": log.mu, "queries": q,
+                            "steps": steps}) + "\n")
+        for i in range(q):
+            walks = [None if not np.isfinite(x) else float(x) for x in log.walks[i, 1:]]
+            f.write(json.dumps({"query": i, "ell": int(log.ell[i]), "push": [float(x) for x in log.push[i]],
+                                "walks": walks, "inputs": log.inputs[i].astype(float).tolist()}) + "\n")
+
+
+def load_cost_log(path: str, kappa: float | None = None, mu: float | None = None) -> CostLog:
+    """Read a cost log stored by save_cost_log and price its rows, with the
+    stored prices unless kappa / mu are given."""
+    with open(path) as f:
+        head = json.loads(f.readline())
+        if head.get("format") != COSTLOG_FORMAT:
+            raise ValueError(f"{path}: not a stored cost log")
+        q, steps = int(head["queries"]), int(head["steps"])
+        inputs = np.zeros((q, steps, MLP_INPUTS), np.float32)
+        push = np.zeros((q, steps + 1))
+        walks = np.full((q, steps + 1), np.nan)
+        ell = np.zeros(q, np.int64)
+        seen = 0
+        for line in f:
+            if not line.strip():
+                continue
+            d = json.loads(line)
+            i = int(d["query"])
+            ell[i] = d["ell"]
+            push[i] = d["push"]
+            walks[i, 1:] = [np.nan if x is None else x for x in d["walks"]]
+            inputs[i] = np.asarray(d["inputs"], np.float32)
+            seen += 1
+    if seen != q:
+        raise ValueError(f"{path}: {seen} of {q} queries")
+    return price(inputs, push, walks, ell, head["kappa"] if kappa is None else kappa,
+                 head["mu"] if mu is None else mu)
 
 
 def batch_seconds(G, s, t, eps, options, repeats: int = 7, before=None) -> float:

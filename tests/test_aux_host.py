@@ -60,3 +60,32 @@ def test_switch_model_round_trip(tmp_path):
              kappa=1.0, mu=0.0)
     with pytest.raises(ValueError):
         switch.load_model(p)
+
+
+def test_cost_log_jsonl_round_trip(tmp_path):
+    nan = float("nan")
+    rng = np.random.default_rng(3)
+    q, steps = 3, 4
+    inputs = rng.normal(size=(q, steps, 6)).astype(np.float32)
+    push = rng.integers(1, 1000, size=(q, steps + 1)).astype(float)
+    walks = rng.integers(1, 10 ** 6, size=(q, steps + 1)).astype(float)
+    walks[:, 0] = nan
+    walks[2, 3:] = nan  # switch points beyond l are not run
+    ell = np.array([9, 2, 3])
+    log = switch.price(inputs, push, walks, ell, 32.0, 1.0)
+    p = str(tmp_path / "log.jsonl")
+    switch.save_cost_log(log, p)
+    lines = open(p).read().splitlines()
+    assert len(lines) == q + 1 and json.loads(lines[0])["format"] == switch.COSTLOG_FORMAT
+    r = switch.load_cost_log(p)
+    assert r.kappa == 32.0 and r.mu == 1.0
+    assert np.array_equal(r.inputs, log.inputs) and np.array_equal(r.ell, log.ell)
+    assert np.array_equal(r.push, log.push) and np.allclose(r.walks, log.walks, equal_nan=True)
+    assert np.array_equal(r.feats, log.feats) and np.array_equal(r.target, log.target)
+    assert np.array_equal(r.query, log.query) and np.array_equal(r.step, log.step)
+    # the same measurements priced again
+    r8 = switch.load_cost_log(p, kappa=8.0)
+    assert np.allclose(r8.cost, switch.price(inputs, push, walks, ell, 8.0, 1.0).cost, equal_nan=True)
+    open(p, "w").write(json.dumps({"format": "other"}) + "\n")
+    with pytest.raises(ValueError):
+        switch.load_cost_log(p)
