@@ -34,12 +34,12 @@ TRAIN_PAIRS, TRAIN_SEED = 2000, 5  # cost-log pairs of the learned switch (the b
 TRAIN_PAIRS_C4 = 7000              # the R-MAT workload trains on ~50k logged rows
 TRAIN_PAIRS_C5 = 256               # the 1B-edge workload logs few pairs (dense columns are 256 MB each)
 WALK_STEP_BYTES = 20  # row_ptr pair 8 B + one col_idx 4 B + one (s*, t*) FP32 pair 8 B
-# DRAM bytes (read + write) per dense_spmm launch from the ncu capture of the
-# current kernel, per (workload, width): profiles/dense_spmm_c2_w128.md
+# DRAM bytes (read + write) per dense_spmm launch, from an ncu capture of the
+# current kernel (dram__bytes_read.sum + dram__bytes_write.sum), per (workload, width)
 SPMM_TRAFFIC: dict = {("c2", 128): 6_261_000_000 + 501_000_000}
-# DRAM bytes per walk step of amc_walk (ncu, all 5 AMC launches of the workload's batch, one-pass
-# DRAM counters on the current kernel): profiles/amc_walk_c2_bench.md. A workload missing here, or
-# a kernel changed since its capture, reports its traffic as null.
+# DRAM bytes per walk step of amc_walk (ncu one-pass DRAM counters over the 5 AMC launches of the
+# workload's batch, divided by their walk steps). A workload missing here, or a kernel changed
+# since its capture, reports its traffic as null.
 WALK_TRAFFIC_PER_STEP: dict = {"c2": (571_255_000 + 4_224_000) / 18_505_638}
 
 

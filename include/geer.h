@@ -40,7 +40,8 @@ extern "C" {
 #define GER_ERR_BIPARTITE     -5  /* bipartite graph: lambda_n = -1 and Eq. (6) is undefined */
 #define GER_ERR_OOM           -6  /* device or host allocation failed */
 #define GER_ERR_CUDA          -7  /* a CUDA runtime call failed */
-#define GER_ERR_TIMEOUT       -8  /* a bounded device-side wait gave up */
+#define GER_ERR_TIMEOUT       -8  /* a bounded device-side wait gave up (reserved: no entry point
+                                     of this version has such a wait, so none returns it) */
 #define GER_ERR_CAPACITY      -9  /* a query outgrew a workspace limit (see ger_options) */
 #define GER_ERR_NO_LAMBDA    -10  /* spectral bound neither computed nor set */
 
@@ -137,6 +138,22 @@ int ger_spectral_bound(ger_graph *g, double *lambda, double *lam2, double *lamn)
 int ger_set_spectral_bound(ger_graph *g, double lambda);
 
 /*
+ * How the graph's lambda (Section 3.1) was obtained. steps: Lanczos steps
+ * taken (0 when lambda was set with ger_set_spectral_bound). converged: 1
+ * when the extreme Ritz values settled to 1e-13 over 10 steps, or the Krylov
+ * space was exhausted, within 300 steps. When they did not, an unconverged
+ * Ritz value lies inside the spectrum and would underestimate lambda (Eq. (6)
+ * would then give too short an l, voiding Theorem 1's eps/2 tail bound), so
+ * ger_spectral_bound's lambda is widened to
+ * max(|lambda_2| + resid_hi, |lambda_n| + resid_lo), resid_* being the
+ * residual bounds beta_k |s_k| of the two extreme Ritz pairs (an eigenvalue
+ * of P lies within each). Any output pointer may be null.
+ * Errors: GER_ERR_INVALID, GER_ERR_NO_LAMBDA (nothing computed or set yet).
+ */
+int ger_spectral_bound_info(const ger_graph *g, int32_t *converged, int32_t *steps, double *resid_hi,
+                            double *resid_lo);
+
+/*
  * Answer q queries r_out[i] ~ r(s[i], t[i]) at error eps (Algorithm 3).
  * s, t: q node ids each (host); r_out: q doubles (host); stats: q entries
  * (host, nullable); opt: nullable (defaults). s[i] == t[i] gives exactly 0
@@ -173,9 +190,21 @@ int ger_query_batch_dev(ger_graph *g, int64_t q, const int32_t *s_dev, const int
  * pinned buffer or allocating library call): all scratch comes from one
  * static 32 MiB device array that every GPU loading the library holds until
  * the process exits. Arguments are those of ger_query_batch_dev, with these
- * limits: q <= 64, and 524288 frontier-table slots per call (the tables of
- * every SMM iteration of every query, each a power of two at least twice the
- * iteration's push volume); beyond them it returns GER_ERR_CAPACITY. The
+ * limits:
+ *   - q <= 64 queries per call;
+ *   - 524288 frontier-table slots per call, shared by the tables of every SMM
+ *     iteration of every query (each a power of two at least twice the
+ *     iteration's push volume), so one table holds at most 262144 push pairs;
+ *   - options.sparse_cap, when set, bounds one table as in the other entry
+ *     points;
+ *   - high-degree frontier nodes are pushed in chunks through a list of 4096
+ *     chunk records; beyond it they are pushed by single warps (slower, the
+ *     same result).
+ * Beyond the first three it returns GER_ERR_CAPACITY. Options it rejects with
+ * GER_ERR_INVALID: switch_policy GER_SWITCH_MLP (the learned switch) and
+ * smm_engine GER_ENGINE_DENSE or GER_ENGINE_HYBRID (their dense blocks are
+ * far larger than the array); per_query, dense_width, dense_switch and
+ * dense_budget_mb are ignored (queries run as one batch, sparse engine). The
  * spectral bound must already be available
  * (ger_spectral_bound or ger_set_spectral_bound), else GER_ERR_NO_LAMBDA.
  * The first call on a device looks up the array's device address; make that
@@ -190,6 +219,14 @@ int ger_query_batch_dev_noalloc(ger_graph *g, int64_t q, const int32_t *s_dev, c
 
 /* Thread-local description of the last error of this thread. */
 const char *ger_last_error(void);
+
+/* Testing hook for the out-of-memory paths (no counterpart in the paper):
+ * the countdown-th next device allocation of a graph's query workspace
+ * (countdown >= 1; 0 disarms) reports failure without allocating, so the
+ * call that needed it returns GER_ERR_OOM. The handle stays usable: a later
+ * call allocates again. Process-wide; not thread-safe against concurrent
+ * queries. Errors: GER_ERR_INVALID for countdown < 0. */
+int ger_test_fail_alloc(int64_t countdown);
 
 /* Number of kernels this library has launched in this process (every node
    of a replayed CUDA graph counts). */

@@ -10,6 +10,8 @@ INFRASTRUCTURE ONLY.
     from dense powers of P.
   * ``spectrum_dense``: eigenvalues of P (via the similar symmetric matrix
     D^-1/2 A D^-1/2).
+  * ``switch_rows_dense``: the two sides of the greedy switch, Eq. (17), with
+    Eqs. (8)-(9), after each SMM iteration, from dense powers of P.
 
 Library primitives (pinv, eigvalsh, matrix products) serve as single steps;
 nothing here is blocked or reordered.
@@ -87,3 +89,38 @@ def spectrum_dense(g) -> np.ndarray:
 def lambda_dense(g) -> float:
     ev = np.sort(spectrum_dense(g))
     return float(max(abs(ev[-2]), abs(ev[0])))
+
+
+def switch_rows_dense(g, s: int, t: int, ell: int, eps: float, delta: float, tau: int, imax: int):
+    """Eq. (17)'s two sides after SMM iterations i = 1..imax: the volume
+    sum_{V_s} d + sum_{V_t} d (supports by integer reachability in exactly i
+    steps) and h(l - i) = (2^tau - 1) max(1, ceil(eta*/2^(tau-1))), with eta*
+    from Eq. (8) and psi from Eq. (9) on s* = P^i e_s, t* = P^i e_t (max_1,
+    max_2 from the sorted vectors). Returns [(volume, h, psi)] (h = psi = 0
+    once l - i = 0)."""
+    import math
+    A = adjacency_dense(g)
+    d = g.degrees().astype(float)
+    P = A / d[:, None]
+    xs = np.zeros(g.n)
+    xs[s] = 1.0
+    xt = np.zeros(g.n)
+    xt[t] = 1.0
+    rs = xs > 0
+    rt = xt > 0
+    rows = []
+    for i in range(1, imax + 1):
+        xs, xt = P @ xs, P @ xt
+        rs, rt = (A @ rs) > 0, (A @ rt) > 0
+        vol = d[rs].sum() + d[rt].sum()
+        lf = ell - i
+        h = 0.0
+        psi = 0.0
+        if lf > 0:
+            ss, tt = np.sort(xs)[::-1], np.sort(xt)[::-1]
+            psi = (2 * math.ceil(lf / 2) * (ss[0] / d[s] + tt[0] / d[t])
+                   + 2 * (lf // 2) * (ss[1] / d[s] + tt[1] / d[t]))
+            eta_star = 2 * psi * psi * math.log(2 * tau / delta) / eps ** 2
+            h = float((2 ** tau - 1) * max(1, math.ceil(eta_star / 2 ** (tau - 1))))
+        rows.append((vol, h, psi))
+    return rows

@@ -100,12 +100,16 @@ def load_library(build_if_missing: bool = True):
     L.ger_graph_size.argtypes = [_P, ctypes.POINTER(i64), ctypes.POINTER(i64)]
     L.ger_spectral_bound.argtypes = [_P, ctypes.POINTER(f64), ctypes.POINTER(f64), ctypes.POINTER(f64)]
     L.ger_set_spectral_bound.argtypes = [_P, f64]
+    L.ger_spectral_bound_info.argtypes = [_P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(f64),
+                                          ctypes.POINTER(f64)]
     L.ger_query_batch.argtypes = [_P, i64, _P, _P, f64, ctypes.POINTER(Options), _P, _P]
     L.ger_query_batch_eps.argtypes = [_P, i64, _P, _P, _P, ctypes.POINTER(Options), _P, _P]
     L.ger_query_batch_dev.argtypes = [_P, i64, _P, _P, _P, ctypes.POINTER(Options), _P, _P, _P]
     L.ger_query_batch_dev_noalloc.argtypes = [_P, i64, _P, _P, _P, ctypes.POINTER(Options), _P, _P, _P]
     L.ger_last_error.argtypes = []
     L.ger_last_error.restype = ctypes.c_char_p
+    L.ger_test_fail_alloc.argtypes = [i64]
+    L.ger_test_fail_alloc.restype = ctypes.c_int
     L.ger_launch_count.argtypes = []
     L.ger_launch_count.restype = i64
     L.ger_profile_enable.argtypes = [ctypes.c_int]
@@ -121,6 +125,7 @@ def load_library(build_if_missing: bool = True):
     L.ger_default_mlp_train_options.restype = None
     L.ger_mlp_train.argtypes = [i64, _P, _P, ctypes.POINTER(MlpTrainOptions), _P, _P]
     for name in ("ger_load_csr", "ger_graph_size", "ger_spectral_bound", "ger_set_spectral_bound",
+                 "ger_spectral_bound_info",
                  "ger_query_batch", "ger_query_batch_eps", "ger_query_batch_dev",
                  "ger_query_batch_dev_noalloc", "ger_set_switch_mlp", "ger_smm_trace", "ger_mlp_forward",
                  "ger_mlp_gradient", "ger_mlp_train", "ger_autotune"):
@@ -146,6 +151,12 @@ def default_options(**kw) -> Options:
 
 def launch_count() -> int:
     return int(load_library().ger_launch_count())
+
+
+def test_fail_alloc(countdown: int):
+    """Testing hook (ger_test_fail_alloc): make the countdown-th next
+    workspace allocation fail; 0 disarms."""
+    _check(load_library().ger_test_fail_alloc(int(countdown)))
 
 
 def profile_enable(on: bool = True):
@@ -228,7 +239,7 @@ def mlp_train(x, target, weights, options: MlpTrainOptions | None = None):
 # spectral-bound sidecar: lambda depends on the graph alone (Section 3.1 computes it
 # once per graph), so it is kept in a small JSON file keyed by a hash of the CSR
 # ---------------------------------------------------------------------------
-LAMBDA_FORMAT = "geer-lambda-1"
+LAMBDA_FORMAT = "geer-lambda-2"
 
 
 def csr_key(row_ptr, col_idx) -> str:
@@ -248,11 +259,14 @@ def _lambda_path(cache_dir: str, key: str) -> str:
 
 def read_lambda_sidecar(cache_dir: str, key: str, n: int, nnz: int):
     """(lambda, lambda_2, lambda_n) stored for this graph, or None (absent,
-    unreadable, or written for another graph)."""
+    unreadable, written for another graph, or not marked as a converged
+    Lanczos result)."""
     try:
         with open(_lambda_path(cache_dir, key)) as f:
             d = json.load(f)
         if d.get("format") != LAMBDA_FORMAT or d.get("key") != key or d.get("n") != n or d.get("nnz") != nnz:
+            return None
+        if d.get("converged") is not True:
             return None
         lam, l2, ln = float(d["lambda"]), float(d["lambda_2"]), float(d["lambda_n"])
     except (OSError, ValueError, KeyError, TypeError):
@@ -262,14 +276,18 @@ def read_lambda_sidecar(cache_dir: str, key: str, n: int, nnz: int):
     return lam, l2, ln
 
 
-def write_lambda_sidecar(cache_dir: str, key: str, n: int, nnz: int, lam: float, l2: float, ln: float) -> str:
-    """Store the graph's spectral bound (written to a temporary file, then renamed)."""
+def write_lambda_sidecar(cache_dir: str, key: str, n: int, nnz: int, lam: float, l2: float, ln: float,
+                         converged: bool = True, steps: int = 0) -> str:
+    """Store the graph's spectral bound (written to a temporary file, then
+    renamed), with whether its Lanczos run converged; only converged values
+    are read back."""
     os.makedirs(cache_dir, exist_ok=True)
     path = _lambda_path(cache_dir, key)
     tmp = f"{path}.tmp{os.getpid()}"
     with open(tmp, "w") as f:
         json.dump({"format": LAMBDA_FORMAT, "key": key, "n": int(n), "nnz": int(nnz), "lambda": float(lam),
-                   "lambda_2": float(l2), "lambda_n": float(ln)}, f)
+                   "lambda_2": float(l2), "lambda_n": float(ln), "converged": bool(converged),
+                   "steps": int(steps)}, f)
     os.replace(tmp, path)
     return path
 
@@ -321,8 +339,21 @@ class Graph:
         lam, l2, ln = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         _check(load_library().ger_spectral_bound(self._h, ctypes.byref(lam), ctypes.byref(l2), ctypes.byref(ln)))
         if use_cache:
-            write_lambda_sidecar(cache_dir, self.key, self.n, self.nnz, lam.value, l2.value, ln.value)
+            info = self.spectral_info()
+            write_lambda_sidecar(cache_dir, self.key, self.n, self.nnz, lam.value, l2.value, ln.value,
+                                 converged=info["converged"], steps=info["steps"])
         return lam.value, l2.value, ln.value
+
+    def spectral_info(self) -> dict:
+        """How lambda was obtained (ger_spectral_bound_info): Lanczos steps (0
+        when set by the caller), convergence, and the residual bounds of the
+        two extreme Ritz pairs (lambda is widened by them when unconverged)."""
+        conv, steps = ctypes.c_int32(), ctypes.c_int32()
+        rh, rl = ctypes.c_double(), ctypes.c_double()
+        _check(load_library().ger_spectral_bound_info(self._h, ctypes.byref(conv), ctypes.byref(steps),
+                                                      ctypes.byref(rh), ctypes.byref(rl)))
+        return {"converged": bool(conv.value), "steps": int(steps.value), "resid_hi": rh.value,
+                "resid_lo": rl.value}
 
     def set_spectral_bound(self, lam: float):
         _check(load_library().ger_set_spectral_bound(self._h, float(lam)))

@@ -166,14 +166,20 @@ __global__ void __launch_bounds__(kCta) amc_schedule_kernel(AmcArgs a) {
     schedule_first(a, group);
 }
 
-// g of a node whose first probe `p` (slot h) is already loaded
-__device__ __forceinline__ double resolve_g(const GEntry* tab, int32_t mask, int32_t v, int4 p, uint32_t h) {
-    for (;;) {
+// g of a node whose first probe `p` (slot h) is already loaded; a node absent
+// from the table (outside the support) has g = 0. A full cycle of probes
+// without v or an empty slot cannot happen while the load stays at most 1/2:
+// it raises DERR_FULL and counts 0.
+__device__ __forceinline__ double resolve_g(const GEntry* tab, int32_t mask, int32_t v, int4 p, uint32_t h,
+                                            int* err_flag) {
+    for (uint32_t probe = 0; probe <= (uint32_t)mask; ++probe) {
         if (p.x == v) return __hiloint2double(p.w, p.z);
         if (p.x == -1) return 0.0;
         h = (h + 1) & (uint32_t)mask;
         p = __ldg(reinterpret_cast<const int4*>(tab + h));
     }
+    atomicCAS(err_flag, 0, DERR_FULL);
+    return 0.0;
 }
 
 // W walk pairs per lane pair and round: lanes 2i, 2i+1 walk pairs
@@ -266,7 +272,7 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
                 }
 #pragma unroll
                 for (int i = 0; i < W; ++i)
-                    if (j > 1 && act[i]) z[i] += resolve_g(tab, mask, pnx[i], ppr[i], phh[i]);
+                    if (j > 1 && act[i]) z[i] += resolve_g(tab, mask, pnx[i], ppr[i], phh[i], a.err_flag);
 #pragma unroll
                 for (int i = 0; i < W; ++i) {
                     pnx[i] = (int32_t)rec[i].x;
@@ -277,7 +283,7 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
             }
 #pragma unroll
             for (int i = 0; i < W; ++i) {
-                if (lf > 0 && act[i]) z[i] += resolve_g(tab, mask, pnx[i], ppr[i], phh[i]);
+                if (lf > 0 && act[i]) z[i] += resolve_g(tab, mask, pnx[i], ppr[i], phh[i], a.err_flag);
                 w[i] = pnx[i];
                 if (act[i]) cs += walk_hash(w[i], k[i], sigma, batch);
             }
@@ -305,7 +311,7 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
                     }
 #pragma unroll
                     for (int i = 0; i < W; ++i) {
-                        if (act[i]) z[i] += resolve_g(tab, mask, nx[i], pr[i], hh[i]);
+                        if (act[i]) z[i] += resolve_g(tab, mask, nx[i], pr[i], hh[i], a.err_flag);
                         w[i] = nx[i];
                     }
                 } else {

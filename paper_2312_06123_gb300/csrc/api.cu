@@ -217,6 +217,10 @@ struct ger_graph {
     uint4* edge_rec = nullptr;   // {neighbour, its first edge, its degree, 0} per edge (walks)
     bool has_lambda = false;
     double lambda = 0, lam2 = 0, lamn = 0;
+    // how lambda was obtained: Lanczos steps (0: set by the caller), whether
+    // the extreme Ritz values converged, and their residual bounds
+    int lam_steps = 0, lam_converged = 1;
+    double lam_resid_hi = 0.0, lam_resid_lo = 0.0;
     cudaStream_t stream = nullptr;
     cudaStream_t stream2 = nullptr;  // captures the SMM while body
     int dense_tuned[2] = {0, 0};     // autotuned dense block width (FP32, FP64), 0: not tuned
@@ -247,8 +251,17 @@ static void free_ws(Workspace& w) {
     w = Workspace();
 }
 
+// Testing hook (ger_test_fail_alloc): the countdown-th next workspace
+// allocation reports failure without calling cudaMalloc.
+static std::atomic<int64_t> g_fail_alloc_countdown{0};
+
 template <typename T>
 static cudaError_t alloc(T** p, size_t count) {
+    if (g_fail_alloc_countdown.load(std::memory_order_relaxed) > 0 &&
+        g_fail_alloc_countdown.fetch_sub(1) == 1) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T) + 16);
 }
 
@@ -388,12 +401,25 @@ static int ensure_lambda(ger_graph* g) {
     DevGraph dg{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info, g->edge_rec};
     double l2 = 0, ln = 0;
     int steps = 0;
-    const int rc = lanczos_spectral_bound(dg, 300, 1e-13, g->stream, &l2, &ln, &steps);
+    LanczosInfo info;
+    const int rc = lanczos_spectral_bound(dg, 300, 1e-13, g->stream, &l2, &ln, &steps, &info);
     if (rc == -2) return fail(GER_ERR_OOM, "spectral bound workspace");
     if (rc != 0) return fail(GER_ERR_CUDA, "spectral bound: %s", cudaGetErrorString(cudaGetLastError()));
     g->lam2 = l2;
     g->lamn = ln;
-    g->lambda = std::max(std::fabs(l2), std::fabs(ln));
+    g->lam_steps = steps;
+    g->lam_converged = info.converged;
+    g->lam_resid_hi = info.resid_hi;
+    g->lam_resid_lo = info.resid_lo;
+    if (info.converged) {
+        g->lambda = std::max(std::fabs(l2), std::fabs(ln));
+    } else {
+        // Ritz values lie inside the spectrum (Cauchy interlacing), so an
+        // unconverged one underestimates |lambda_2| or |lambda_n| and Eq. (6)
+        // would give too short an l: widen each by its residual bound (an
+        // eigenvalue lies within it)
+        g->lambda = std::max(std::fabs(l2) + info.resid_hi, std::fabs(ln) + info.resid_lo);
+    }
     if (!(g->lambda < 1.0)) return fail(GER_ERR_BIPARTITE, "spectral bound lambda = %.17g >= 1", g->lambda);
     g->has_lambda = true;
     return GER_OK;
@@ -423,6 +449,7 @@ static int map_device_error(int e) {
         case DERR_CAPACITY: return fail(GER_ERR_CAPACITY, "an SMM iteration needs a frontier table beyond the limit");
         case DERR_TABLE: return fail(GER_ERR_CAPACITY, "frontier-table pool exhausted");
         case DERR_ELL: return fail(GER_ERR_INVALID, "truncation length undefined (lambda >= 1)");
+        case DERR_FULL: return fail(GER_ERR_CAPACITY, "a frontier table ran out of free slots (load factor broken)");
         default: return fail(GER_ERR_CUDA, "device error %d", e);
     }
 }
@@ -1038,6 +1065,12 @@ void ger_default_options(ger_options* o) {
 
 const char* ger_last_error(void) { return g_err; }
 
+int ger_test_fail_alloc(int64_t countdown) {
+    if (countdown < 0) return fail(GER_ERR_INVALID, "countdown must be >= 0");
+    g_fail_alloc_countdown.store(countdown);
+    return GER_OK;
+}
+
 int64_t ger_launch_count(void) { return g_launches.load(); }
 
 int ger_profile_enable(int on) {
@@ -1197,6 +1230,20 @@ int ger_set_spectral_bound(ger_graph* g, double lambda) {
     g->lambda = lambda;
     g->lam2 = g->lamn = std::nan("");
     g->has_lambda = true;
+    g->lam_steps = 0;
+    g->lam_converged = 1;
+    g->lam_resid_hi = g->lam_resid_lo = 0.0;
+    return GER_OK;
+}
+
+int ger_spectral_bound_info(const ger_graph* g, int32_t* converged, int32_t* steps, double* resid_hi,
+                            double* resid_lo) {
+    if (!g) return fail(GER_ERR_INVALID, "null graph");
+    if (!g->has_lambda) return fail(GER_ERR_NO_LAMBDA, "spectral bound neither computed nor set");
+    if (converged) *converged = g->lam_converged;
+    if (steps) *steps = g->lam_steps;
+    if (resid_hi) *resid_hi = g->lam_resid_hi;
+    if (resid_lo) *resid_lo = g->lam_resid_lo;
     return GER_OK;
 }
 

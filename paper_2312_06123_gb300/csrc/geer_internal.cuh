@@ -30,7 +30,10 @@ constexpr int kMaxChunksPerQuery = 4096;
 enum : int32_t { ST_SMM = 0, ST_AMC = 1, ST_DONE = 2, ST_ERROR = 3 };
 
 // device error codes (mirrored into the host status codes)
-enum : int32_t { DERR_NONE = 0, DERR_NODE_RANGE = 1, DERR_CAPACITY = 2, DERR_TABLE = 3, DERR_ELL = 4 };
+// DERR_FULL: a frontier table had no free slot left, which the load factor
+// (capacity >= twice the push pairs) rules out; the probe gives up instead of
+// looping.
+enum : int32_t { DERR_NONE = 0, DERR_NODE_RANGE = 1, DERR_CAPACITY = 2, DERR_TABLE = 3, DERR_ELL = 4, DERR_FULL = 5 };
 
 // Per-query state, one record per query of a batch (device memory).
 struct QState {

@@ -168,9 +168,17 @@ void prof_end(int fam, cudaStream_t st);
 // fold the recorded events of completed launches into the accumulators
 void prof_collect();
 
+// Convergence record of the spectral bound: whether the extreme Ritz values
+// settled (or the Krylov space was exhausted) before the step limit, and the
+// residual bounds beta_k |s_k| of the two extreme Ritz pairs.
+struct LanczosInfo {
+    int converged = 0;
+    double resid_hi = 0.0, resid_lo = 0.0;
+};
+
 // Spectral bound of P on the device (Section 3.1). Returns 0 on success.
 int lanczos_spectral_bound(const DevGraph& g, int max_steps, double tol, cudaStream_t st, double* lam2,
-                           double* lamn, int* steps);
+                           double* lamn, int* steps, LanczosInfo* info = nullptr);
 
 }  // namespace geer
 

@@ -7,6 +7,7 @@
 // extreme eigenvalues of the tridiagonal matrix, found by Sturm-sequence
 // bisection. Every reduction has a fixed shape, so the result does not
 // depend on scheduling.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -137,8 +138,69 @@ __global__ void lz_ritz_kernel(int64_t k, const double* a, const double* b2, dou
 
 }  // namespace
 
+// Residual bound of a Ritz value theta of the k x k Lanczos tridiagonal
+// matrix T (diagonal a, squared off-diagonal b2[0..k-2]): the Ritz pair
+// (theta, V s) of N has residual |N V s - theta V s| = beta_k |s_k| with s
+// the unit eigenvector of T for theta and beta_k^2 = b2[k-1]. s comes from
+// inverse iteration: (T - sigma I) x = y solved by Gaussian elimination with
+// partial pivoting on the tridiagonal band, sigma a hair off theta.
+static double ritz_residual(int64_t k, const std::vector<double>& a, const std::vector<double>& b2, double theta) {
+    if (k <= 0) return 0.0;
+    const double beta_k = std::sqrt(std::max(b2[k - 1], 0.0));
+    if (k == 1) return beta_k;
+    std::vector<double> off(k - 1);
+    double scale = 0.0;
+    for (int64_t i = 0; i < k; ++i) scale = std::max(scale, std::fabs(a[i]));
+    for (int64_t i = 0; i + 1 < k; ++i) {
+        off[i] = std::sqrt(std::max(b2[i], 0.0));
+        scale = std::max(scale, off[i]);
+    }
+    const double sigma = theta + 1e-12 * std::max(scale, 1.0);
+    std::vector<double> x(k, 1.0 / std::sqrt((double)k));
+    // band LU of T - sigma I with partial pivoting: rows keep diagonal d,
+    // first and second super-diagonals u1, u2, and the multipliers
+    std::vector<double> d(k), u1(k, 0.0), u2(k, 0.0), mult(k, 0.0);
+    std::vector<char> swapped(k, 0);
+    for (int64_t i = 0; i < k; ++i) d[i] = a[i] - sigma;
+    for (int64_t i = 0; i + 1 < k; ++i) u1[i] = off[i];
+    std::vector<double> lower(off);  // sub-diagonal
+    for (int64_t i = 0; i + 1 < k; ++i) {
+        if (std::fabs(lower[i]) > std::fabs(d[i])) {
+            // swap rows i and i + 1 (row i + 1: lower[i], d[i+1], u1[i+1])
+            std::swap(d[i], lower[i]);
+            std::swap(u1[i], d[i + 1]);
+            std::swap(u2[i], u1[i + 1]);
+            swapped[i] = 1;
+        }
+        const double piv = d[i] != 0.0 ? d[i] : 1e-300;
+        mult[i] = lower[i] / piv;
+        d[i + 1] -= mult[i] * u1[i];
+        u1[i + 1] -= mult[i] * u2[i];
+    }
+    if (d[k - 1] == 0.0) d[k - 1] = 1e-300;
+    for (int it = 0; it < 3; ++it) {
+        std::vector<double> y(x);
+        for (int64_t i = 0; i + 1 < k; ++i) {
+            if (swapped[i]) std::swap(y[i], y[i + 1]);
+            y[i + 1] -= mult[i] * y[i];
+        }
+        for (int64_t i = k - 1; i >= 0; --i) {
+            double v = y[i];
+            if (i + 1 < k) v -= u1[i] * y[i + 1];
+            if (i + 2 < k) v -= u2[i] * y[i + 2];
+            y[i] = v / (d[i] != 0.0 ? d[i] : 1e-300);
+        }
+        double nrm = 0.0;
+        for (int64_t i = 0; i < k; ++i) nrm += y[i] * y[i];
+        nrm = std::sqrt(nrm);
+        if (!(nrm > 0.0) || !std::isfinite(nrm)) break;
+        for (int64_t i = 0; i < k; ++i) x[i] = y[i] / nrm;
+    }
+    return beta_k * std::fabs(x[k - 1]);
+}
+
 int lanczos_spectral_bound(const DevGraph& g, int max_steps, double tol, cudaStream_t st, double* lam2,
-                           double* lamn, int* steps) {
+                           double* lamn, int* steps, LanczosInfo* info) {
     const int64_t n = g.n;
     if (n < 3) return -1;
     const int64_t kmax = max_steps < n - 1 ? max_steps : n - 1;
@@ -185,6 +247,7 @@ int lanczos_spectral_bound(const DevGraph& g, int max_steps, double tol, cudaStr
 
     double prev_hi = 0.0, prev_lo = 0.0, hr[2] = {0.0, 0.0};
     int64_t k = 0;
+    bool converged = false;
     for (int64_t j = 0; j < kmax; ++j) {
         double* qj = V + (size_t)j * (size_t)n;
         lz_spmv_kernel<<<grid * 4, blk, 0, st>>>(g, isd, qj, w);
@@ -221,8 +284,14 @@ int lanczos_spectral_bound(const DevGraph& g, int max_steps, double tol, cudaStr
                 cleanup();
                 return -3;
             }
-            if (last) break;
-            if (k >= 20 && std::fabs(hr[0] - prev_hi) < tol && std::fabs(hr[1] - prev_lo) < tol) break;
+            if (last) {
+                converged = beta < 1e-12;  // the Krylov space is exhausted: the Ritz values are exact
+                break;
+            }
+            if (k >= 20 && std::fabs(hr[0] - prev_hi) < tol && std::fabs(hr[1] - prev_lo) < tol) {
+                converged = true;
+                break;
+            }
             prev_hi = hr[0];
             prev_lo = hr[1];
         }
@@ -232,6 +301,19 @@ int lanczos_spectral_bound(const DevGraph& g, int max_steps, double tol, cudaStr
     *lam2 = hr[0];
     *lamn = hr[1];
     *steps = (int)k;
+    if (info) {
+        // residual bounds of the two extreme Ritz pairs, from the tridiagonal matrix
+        std::vector<double> ha(k > 0 ? k : 1), hb(k > 0 ? k : 1);
+        if (k > 0 && (cudaMemcpyAsync(ha.data(), alpha, k * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                      cudaMemcpyAsync(hb.data(), beta2, k * sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                      cudaStreamSynchronize(st) != cudaSuccess)) {
+            cleanup();
+            return -3;
+        }
+        info->converged = converged ? 1 : 0;
+        info->resid_hi = ritz_residual(k, ha, hb, hr[0]);
+        info->resid_lo = ritz_residual(k, ha, hb, hr[1]);
+    }
     cleanup();
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }

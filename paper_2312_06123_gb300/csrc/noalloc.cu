@@ -77,6 +77,14 @@ int scratch_address(int device, unsigned char** out) {
     return GER_OK;
 }
 
+// Status of the launches issued so far (cudaGetLastError: a launch that could
+// not start reports here, not through the kernel's error flag).
+int check_launches() {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(GER_ERR_CUDA, cudaGetErrorString(e));
+    return GER_OK;
+}
+
 int sync_read_int(const void* dev, int* out, cudaStream_t st) {
     if (cudaMemcpyAsync(out, dev, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
@@ -99,6 +107,8 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
         return set_error(GER_ERR_CAPACITY, "ger_query_batch_dev_noalloc takes at most 64 queries per call");
     ger_options o;
     if (opt) o = *opt; else ger_default_options(&o);
+    if (o.switch_policy == GER_SWITCH_MLP)
+        return set_error(GER_ERR_INVALID, "the no-alloc entry point does not run the learned switch");
     if (!(o.delta > 0.0 && o.delta < 1.0) || o.tau < 1 || o.tau > 20 ||
         (o.precision != GER_FP32 && o.precision != GER_FP64) ||
         (o.switch_policy != GER_SWITCH_RULE && o.switch_policy != GER_SWITCH_FIXED) ||
@@ -122,6 +132,7 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     if (rc) return rc;
     cudaStream_t st = stream ? reinterpret_cast<cudaStream_t>(stream) : (cudaStream_t)0;
     const bool fp64 = o.precision == GER_FP64;
+    cudaGetLastError();  // a non-sticky error left by earlier work is not this call's
 
     int* counters = reinterpret_cast<int*>(base + kOffCounters);
     SmmCtl* ctl = reinterpret_cast<SmmCtl*>(base + kOffCtl);
@@ -177,6 +188,10 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     const int grid = sm_count * 8;
     launch_smm_start(fp64, a, grid, st);
     launch_smm_advance(a, 0, false, st);
+    // a launch that failed to start (bad configuration, missing kernel image)
+    // leaves the control words at their zeros: catch it before reading them
+    rc = check_launches();
+    if (rc) return rc;
     for (int iter = 1; iter < 100000; ++iter) {
         int n_want = 0;
         rc = sync_read_int(&ctl->n_want, &n_want, st);
@@ -184,7 +199,9 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
         if (n_want == 0) break;
         launch_smm_iteration(fp64, a, grid, st);
         launch_smm_advance(a, 0, false, st);
-        }
+        rc = check_launches();
+        if (rc) return rc;
+    }
     AmcArgs m;
     m.g = dg;
     m.nq = (int32_t)q;
@@ -212,6 +229,8 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     }
     launch_finalize(qs, q, r_dev, stats_dev, st);
     note_launches(2 + 2 * o.tau);
+    rc = check_launches();
+    if (rc) return rc;
     int derr = 0;
     rc = sync_read_int(counters + 1, &derr, st);
     if (rc) return rc;
@@ -219,8 +238,17 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
         case DERR_NONE: return GER_OK;
         case DERR_NODE_RANGE: return set_error(GER_ERR_NODE_RANGE, "a query node is outside [0, n) or eps <= 0");
         case DERR_CAPACITY:
+            if (o.sparse_cap > 0 && max_table < kNoAllocPool)
+                return set_error(GER_ERR_CAPACITY,
+                                 "an SMM iteration needs a frontier table beyond options.sparse_cap push pairs");
+            return set_error(GER_ERR_CAPACITY,
+                             "an SMM iteration needs a frontier table beyond the no-alloc limit of 524288 slots");
         case DERR_TABLE:
-            return set_error(GER_ERR_CAPACITY, "the frontier tables exceeded the no-alloc limit of 524288 slots");
-        default: return set_error(GER_ERR_INVALID, "truncation length undefined (lambda >= 1)");
+            return set_error(GER_ERR_CAPACITY,
+                             "the frontier tables of the call exceeded the no-alloc pool of 524288 slots");
+        case DERR_FULL:
+            return set_error(GER_ERR_CAPACITY, "a frontier table ran out of free slots (load factor broken)");
+        case DERR_ELL: return set_error(GER_ERR_INVALID, "truncation length undefined (lambda >= 1)");
+        default: return set_error(GER_ERR_CUDA, "unknown device error");
     }
 }

@@ -101,14 +101,20 @@ __device__ __forceinline__ int fixed_shift(int64_t d) {
     return 61 - b;
 }
 
-// insert v into a table (capacity mask+1); returns its slot
-__device__ __forceinline__ uint32_t table_insert(GEntry* tab, uint32_t mask, int32_t v) {
+constexpr uint32_t kNoSlot = 0xffffffffu;
+
+// insert v into a table (capacity mask+1); returns its slot, or kNoSlot
+// (and raises DERR_FULL) when a full cycle of probes finds neither v nor a
+// free slot -- impossible while the table's load stays at most 1/2
+__device__ __forceinline__ uint32_t table_insert(GEntry* tab, uint32_t mask, int32_t v, int* err_flag) {
     uint32_t h = hash32((uint32_t)v) & mask;
-    for (;;) {
+    for (uint32_t probe = 0; probe <= mask; ++probe) {
         const int32_t prev = atomicCAS(&tab[h].v, -1, v);
         if (prev == -1 || prev == v) return h;
         h = (h + 1) & mask;
     }
+    atomicCAS(err_flag, 0, DERR_FULL);
+    return kNoSlot;
 }
 
 }  // namespace
@@ -275,12 +281,16 @@ __global__ void smm_seed_kernel(SmmArgs a) {
         const QState* Q = a.st + q;
         GEntry* tab = a.ent + M->ntab_off;
         const uint32_t mask = (uint32_t)(M->ntab_cap - 1);
-        uint32_t hs = table_insert(tab, mask, Q->s);
-        tab[hs].bits = 1u | ((uint32_t)q << 2);
-        a.sum_s[M->ntab_off + hs] = (unsigned long long)Q->ds << M->shift_s;
-        uint32_t ht = table_insert(tab, mask, Q->t);
-        tab[ht].bits = 2u | ((uint32_t)q << 2);
-        a.sum_t[M->ntab_off + ht] = (unsigned long long)Q->dt << M->shift_t;
+        const uint32_t hs = table_insert(tab, mask, Q->s, a.err_flag);
+        if (hs != kNoSlot) {
+            tab[hs].bits = 1u | ((uint32_t)q << 2);
+            a.sum_s[M->ntab_off + hs] = (unsigned long long)Q->ds << M->shift_s;
+        }
+        const uint32_t ht = table_insert(tab, mask, Q->t, a.err_flag);
+        if (ht != kNoSlot) {
+            tab[ht].bits = 2u | ((uint32_t)q << 2);
+            a.sum_t[M->ntab_off + ht] = (unsigned long long)Q->dt << M->shift_t;
+        }
     }
 }
 
@@ -306,7 +316,8 @@ __device__ __forceinline__ void push_range(const SmmArgs& a, int64_t j, int q, i
     const int32_t* col_idx = a.g.col_idx;
     for (int64_t p = pb + rank; p < pe; p += nthreads) {
         const int32_t v = col_idx[p];
-        const uint32_t h = table_insert(ntab, nmask, v);
+        const uint32_t h = table_insert(ntab, nmask, v, a.err_flag);
+        if (h == kNoSlot) continue;
         if (fs) atomicAdd(&ss[h], fs);
         if (ft) atomicAdd(&tt[h], ft);
         atomicOr(&ntab[h].bits, bits);

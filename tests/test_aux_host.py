@@ -37,7 +37,15 @@ def test_lambda_sidecar_round_trip_and_rejections(tmp_path):
     assert geer.read_lambda_sidecar(d, key, n + 1, nnz) is None
     assert geer.read_lambda_sidecar(d, key, n, nnz + 2) is None
     rec = json.load(open(path))
-    for bad in ({"lambda": 1.0}, {"format": "other"}, {"key": "0" * 64}):
+    # a value from a Lanczos run that did not converge is not reused
+    geer.write_lambda_sidecar(d, key, n, nnz, 0.8125, 0.8125, -0.75, converged=False, steps=300)
+    assert geer.read_lambda_sidecar(d, key, n, nnz) is None
+    path = geer.write_lambda_sidecar(d, key, n, nnz, 0.8125, 0.8125, -0.75, converged=True, steps=40)
+    rec = json.load(open(path))
+    json.dump({k: v for k, v in rec.items() if k != "converged"}, open(path, "w"))
+    assert geer.read_lambda_sidecar(d, key, n, nnz) is None
+    path = geer.write_lambda_sidecar(d, key, n, nnz, 0.8125, 0.8125, -0.75)
+    for bad in ({"lambda": 1.0}, {"format": "other"}, {"key": "0" * 64}, {"format": "geer-lambda-1"}):
         json.dump({**rec, **bad}, open(path, "w"))
         assert geer.read_lambda_sidecar(d, key, n, nnz) is None
     open(path, "w").write("{not json")

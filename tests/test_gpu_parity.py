@@ -215,7 +215,7 @@ def test_amc_options_replay_bit_exact(c1, tau, delta, seed):
         assert np.any(st["walks"] > 0)
         for i in range(q):
             ref = replay(g, s[i], t[i], eps[i], lam, st[i], i, seed=seed, tau=tau, delta=delta)
-            compare(r[i], st[i], ref, rel, rel)
+            compare(r[i], st[i], ref, rel, rel, tau=tau)
 
 
 @pytest.mark.parametrize("heavy", [False, True])
@@ -558,3 +558,48 @@ def test_autotune_changes_run_time_only(c1):
     same = s0["ell_b"] == s1["ell_b"]
     assert np.array_equal(s0["checksum"][same], s1["checksum"][same])
     assert np.allclose(r0[same], r1[same], rtol=1e-9, atol=0)
+
+
+def test_allocation_failure_leaves_the_handle_usable():
+    # A failed workspace allocation (forced through the testing hook) returns
+    # GER_ERR_OOM; the same handle then answers the same batch correctly.
+    w = synth.workload("c1")
+    g = w.graph
+    lam = oracle.lam(g)
+    G = geer.Graph.from_csr(g)
+    G.set_spectral_bound(lam)
+    o = _opts(precision=geer.GER_FP64)
+    r_small = G.query(w.s[:8], w.t[:8], w.eps[:8], o)
+    geer.test_fail_alloc(1)  # the next allocation: the workspace for a larger batch
+    try:
+        with pytest.raises(geer.GeerError) as err:
+            G.query(w.s, w.t, w.eps, o)
+        assert err.value.code == -6
+    finally:
+        geer.test_fail_alloc(0)
+    r, st = G.query(w.s, w.t, w.eps, o, stats=True)
+    assert np.array_equal(r[:8], r_small)
+    for i in range(0, w.q, 9):
+        compare(r[i], st[i], replay(g, w.s[i], w.t[i], w.eps[i], lam, st[i], i), 1e-9, 1e-9)
+    G.close()
+
+
+def test_switch_boundary_matches_oracle():
+    # Eq. (17)'s strict inequality at an exact tie: after iteration 1 the volume
+    # equals h(l - 1) (delta chosen at tau = 1, as in the oracle's pin), so SMM
+    # continues; one walk fewer in h and it stops. The GPU decides as the oracle.
+    g = graphs.random_connected(60, 250, 2)
+    lam = oracle.lam(g)
+    G = geer.Graph.from_csr(g)
+    G.set_spectral_bound(lam)
+    s, t, eps = 10, 40, 0.05
+    ell = oracle.ell(g.degrees()[s], g.degrees()[t], eps, lam)
+    vol, _, psi = exact.switch_rows_dense(g, s, t, ell, eps, 0.01, 1, 1)[0]
+    for target, stops in ((vol - 0.5, False), (vol - 1.5, True)):
+        delta = 2 * math.exp(-target * eps * eps / (2 * psi * psi))
+        ref = oracle.geer(g, s, t, eps, lam, tau=1, delta=delta)
+        for prec in (geer.GER_FP64, geer.GER_FP32):
+            _, st = G.query([s], [t], eps, _opts(precision=prec, tau=1, delta=delta), stats=True)
+            assert (int(st["ell_b"][0]) == 1) == stops
+            assert int(st["ell_b"][0]) == ref.ell_b
+    G.close()

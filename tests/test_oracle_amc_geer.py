@@ -213,3 +213,76 @@ def test_geer_mean_over_seeds_is_r_ell():
     r_ell = exact.r_ell_dense(g, s, t, ref.ell)
     se = np.std(vals) / math.sqrt(len(vals))
     assert abs(np.mean(vals) - r_ell) <= 5 * se + 1e-12
+
+
+# ---------------------------------------------------------------------------
+# The greedy switch of Eq. (17) and its quantities (Eqs. 8, 9)
+# ---------------------------------------------------------------------------
+
+def test_switch_quantities_on_odd_cycle_by_hand():
+    # C_7, s = 0, t = 3, eps = 0.5, delta = 0.01, tau = 5 (2 tau / delta = 1000).
+    # lambda = cos(pi/7) = 0.90097; Eq. (6): ceil(ln(2 / (0.5 (1 - lambda))) / ln(1/lambda) - 1)
+    #   = ceil(34.467) = 35.
+    # Iteration 1: s* = 1/2 on {1, 6}, t* = 1/2 on {2, 4}: V_s, V_t disjoint, volume 4 + 4 = 8;
+    #   max_1 = max_2 = 1/2 (a tie), d(s) = d(t) = 2, l_f = 34:
+    #   psi = 2*17*(1/4 + 1/4) + 2*17*(1/4 + 1/4) = 34 (Eq. 9);
+    #   eta* = 2 * 34^2 * ln 1000 / 0.25 = 63882.92 (Eq. 8); eta_0 = ceil(eta*/16) = 3993;
+    #   h = (2^5 - 1) * 3993 = 123783.
+    # Iteration 2: s* = 1/2 at 0 and 1/4 at {2, 5}; t* = 1/2 at 3 and 1/4 at {1, 5}: volume 6 + 6 = 12;
+    #   l_f = 33: psi = 2*17*(1/4 + 1/4) + 2*16*(1/8 + 1/8) = 17 + 8 = 25;
+    #   eta* = 2 * 625 * ln 1000 / 0.25 = 34538.78; eta_0 = 2159; h = 31 * 2159 = 66929.
+    # r_b: 1/2 + 1/2 = 1 after iterations 0 and 1 (s* and t* vanish at s and t), then
+    #   + (1/2)/2 + (1/2)/2 = 1.5 after iteration 2.
+    # The volume never exceeds h, so SMM runs to l_b = l = 35 and AMC has nothing left.
+    g = graphs.cycle(7)
+    lam = math.cos(math.pi / 7)
+    res = oracle.geer(g, 0, 3, 0.5, lam, trace=True)
+    assert res.ell == 35
+    tr = res.trace
+    assert tr[0].tolist() == [1.0, 8.0, 123783.0, 34.0, 0.5, 8.0]
+    assert tr[1, :4].tolist() == [1.5, 12.0, 66929.0, 25.0]
+    assert res.ell_b == 35 and res.free_ell_b == 35 and res.amc.walks == 0
+
+
+@pytest.mark.parametrize("tau", [1, 3, 5])
+def test_switch_trace_matches_dense_definition(tau):
+    # Every SMM iteration's volume, h(l - l_b) = (2^tau - 1) ceil(eta*/2^(tau-1)) and psi
+    # against the dense computation; the free switch point is the first iteration with
+    # volume > h, or l.
+    g = graphs.random_connected(60, 250, 2)
+    lam = oracle.lam(g)
+    for s, t, eps in ((10, 40, 0.05), (5, 50, 0.02), (0, 30, 0.1)):
+        ell = oracle.ell(g.degrees()[s], g.degrees()[t], eps, lam)
+        res = oracle.geer(g, s, t, eps, lam, tau=tau, forced_ell_b=ell, trace=True)
+        rows = exact.switch_rows_dense(g, s, t, ell, eps, 0.01, tau, ell)
+        first = ell
+        for i, (vol, h, psi) in enumerate(rows, start=1):
+            assert res.trace[i - 1, 1] == vol
+            assert res.trace[i - 1, 2] == h
+            assert res.trace[i - 1, 3] == pytest.approx(psi, rel=1e-12, abs=1e-15)
+            if vol > h and first == ell:
+                first = i
+        assert res.free_ell_b == first
+
+
+def test_switch_inequality_is_strict():
+    # Eq. (17) stops SMM once the volume EXCEEDS h(l - l_b). At tau = 1, h = ceil(eta*);
+    # delta is chosen (it leaves l unchanged) so that eta* after iteration 1 is
+    # volume - 0.5 (h = volume: continue) or volume - 1.5 (h = volume - 1: stop).
+    # Taking h = eta* without the ceiling, >= for >, or 2^tau for 2^tau - 1 flips one case.
+    g = graphs.random_connected(60, 250, 2)
+    lam = oracle.lam(g)
+    s, t, eps = 10, 40, 0.05
+    ell = oracle.ell(g.degrees()[s], g.degrees()[t], eps, lam)
+    assert ell >= 3
+    vol, _, psi = exact.switch_rows_dense(g, s, t, ell, eps, 0.01, 1, 1)[0]
+    for target, stops in ((vol - 0.5, False), (vol - 1.5, True)):
+        # Eq. (8) at tau = 1 solved for delta: eta* = 2 psi^2 ln(2/delta) / eps^2
+        delta = 2 * math.exp(-target * eps * eps / (2 * psi * psi))
+        assert 0 < delta < 1
+        res = oracle.geer(g, s, t, eps, lam, tau=1, delta=delta, forced_ell_b=ell, trace=True)
+        assert res.trace[0, 1] == vol
+        assert res.trace[0, 2] == (vol if not stops else vol - 1)
+        assert (res.free_ell_b == 1) == stops
+        free = oracle.geer(g, s, t, eps, lam, tau=1, delta=delta)
+        assert (free.ell_b == 1) == stops

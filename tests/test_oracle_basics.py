@@ -193,3 +193,18 @@ def test_psi_lemma3_bound_by_enumeration():
     xt = np.zeros(5)
     psi = oracle.psi(lf, 1.0, 0.0, 0.0, 0.0, 2, 2)
     assert psi == pytest.approx(2 * 2 * (1 / 2))
+
+
+def test_bernstein_hand_values():
+    # Eq. (7), f(n, var, psi, delta) = sqrt(2 var log(3/delta) / n) + 3 psi log(3/delta) / n,
+    # evaluated by hand at points where log(3/delta) is an integer:
+    #   delta = 3/e^2 -> log(3/delta) = 2; n = 8, var = 1/2, psi = 1:
+    #     sqrt(2 * 0.5 * 2 / 8) + 3 * 1 * 2 / 8 = sqrt(1/4) + 6/8 = 0.5 + 0.75 = 1.25
+    #   delta = 3/e -> log(3/delta) = 1; n = 2, var = 1, psi = 1/2:
+    #     sqrt(2 * 1 * 1 / 2) + 3 * 0.5 * 1 / 2 = 1 + 0.75 = 1.75
+    #   delta = 3/e^2, n = 50, var = 0, psi = 10: 0 + 3 * 10 * 2 / 50 = 1.2
+    # A dropped 2 under the root, log(2/delta), psi for 3 psi, or 1/n for 1/sqrt(n)
+    # each moves at least one of these values.
+    assert oracle.bernstein(8, 0.5, 1.0, 3 / math.e ** 2) == pytest.approx(1.25, rel=1e-14)
+    assert oracle.bernstein(2, 1.0, 0.5, 3 / math.e) == pytest.approx(1.75, rel=1e-14)
+    assert oracle.bernstein(50, 0.0, 10.0, 3 / math.e ** 2) == pytest.approx(1.2, rel=1e-14)

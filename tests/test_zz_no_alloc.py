@@ -69,3 +69,29 @@ def test_noalloc_limits(setup):
     with pytest.raises(geer.GeerError) as err:
         G2.query_dev_noalloc(s[:4], t[:4], e[:4], r)
     assert err.value.code == -10
+
+
+def test_noalloc_capacity_errors_leave_the_next_call_correct(setup):
+    # The shared array keeps a failed call's contents; the next call must still
+    # match ger_query_batch_dev. Two ways to overflow: a per-table cap
+    # (options.sparse_cap = 4 push pairs: the first push of every query is
+    # larger) and the call's 524288-slot pool (standalone SMM to l on 64
+    # queries: one table of up to 8192 slots per query and iteration).
+    torch, w, G, s, t, e = setup
+    q = w.q
+    r = torch.empty(q, dtype=torch.float64, device=s.device)
+    for bad in (geer.default_options(sparse_cap=4),
+                geer.default_options(switch_policy=geer.GER_SWITCH_FIXED, fixed_ell_b=-1)):
+        with pytest.raises(geer.GeerError) as err:
+            G.query_dev_noalloc(s, t, e, r, None, bad)
+        assert err.value.code == -9, err.value
+    opts = geer.default_options()
+    r_ref = torch.empty(q, dtype=torch.float64, device=s.device)
+    st_ref = torch.empty(q * geer.STATS_DTYPE.itemsize, dtype=torch.uint8, device=s.device)
+    G.query_dev(s, t, e, r_ref, st_ref, opts)
+    st = torch.zeros(q * geer.STATS_DTYPE.itemsize, dtype=torch.uint8, device=s.device)
+    G.query_dev_noalloc(s, t, e, r, st, opts)
+    ref, got = r_ref.cpu().numpy(), r.cpu().numpy()
+    assert np.all(np.abs(got - ref) <= 1e-5 * np.abs(ref))
+    a, b = _stats(torch, st_ref), _stats(torch, st)
+    assert np.array_equal(a["walks"], b["walks"]) and np.array_equal(a["checksum"], b["checksum"])
