@@ -136,6 +136,81 @@ def oracle_sample(w, lam, seconds: float, start: int = 0):
             return k, el
 
 
+def oracle_sample_threads(w, lam, seconds: float, threads: int, start: int = 0):
+    """The oracle on `threads` host threads (one query per task; the C oracle
+    runs without the Python lock), consecutive queries until `seconds`
+    elapse; returns (queries done, elapsed seconds)."""
+    import concurrent.futures as cf
+    import oracle
+    t0 = time.perf_counter()
+    done = 0
+    nxt = start
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        def submit(i):
+            i %= w.q
+            return ex.submit(oracle.geer, w.graph, int(w.s[i]), int(w.t[i]), float(w.eps[i]), lam, q_index=i)
+        pending = set()
+        for _ in range(threads):
+            pending.add(submit(nxt))
+            nxt += 1
+        while pending:
+            fin, pending = cf.wait(pending, return_when=cf.FIRST_COMPLETED)
+            for f in fin:
+                f.result()
+                done += 1
+                if time.perf_counter() - t0 < seconds:
+                    pending.add(submit(nxt))
+                    nxt += 1
+    return done, time.perf_counter() - t0
+
+
+def host_info() -> dict:
+    """Host cores and CPU model (for the CPU baselines)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+def replay_parity(w, lam, stats, seconds: float, threads: int, seed: int = 3):
+    """The error of the GPU's results against the FP64 oracle replaying the
+    GPU's decisions (l_b, eta_0, batches) on the same queries: as many of the
+    batch's first queries as `seconds` of `threads` host threads allow."""
+    import concurrent.futures as cf
+    import oracle
+    t0 = time.perf_counter()
+
+    def one(i):
+        st = stats[i]
+        ref = oracle.geer(w.graph, int(w.s[i]), int(w.t[i]), float(w.eps[i]), lam, seed=seed, q_index=i,
+                          forced_ell_b=int(st["ell_b"]), forced_eta0=int(st["eta0"]),
+                          forced_batches=int(st["batches"]))
+        return i, ref.r, int(ref.amc.checksum), int(ref.amc.walks)
+
+    res = []
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        futs = []
+        i = 0
+        while i < w.q and (time.perf_counter() - t0 < seconds or i < threads):
+            futs.append(ex.submit(one, i))
+            i += 1
+            if len(futs) - len(res) >= 2 * threads:
+                # keep the queue short so the time budget holds
+                res.append(futs[len(res)].result())
+        for f in futs[len(res):]:
+            res.append(f.result())
+    return res, time.perf_counter() - t0
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -252,6 +327,9 @@ def _config(w):
         pairs_txt = (f"{w.q} pairs in thirds low-low / low-high / high-high degree (low <= median, high = top 1%), "
                      f"eps cycling 0.1 / 0.05 / 0.02")
         eps_cfg = "0.1/0.05/0.02"
+    elif w.name == "c2e":
+        pairs_txt = f"{w.q} uniform edges (the paper's edge queries), eps={w.eps[0]:g}"
+        eps_cfg = float(w.eps[0])
     else:
         pairs_txt = f"{w.q} uniform pairs, eps={w.eps[0]:g}"
         eps_cfg = float(w.eps[0])
@@ -269,7 +347,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c2e", "c3", "c4", "c5"])
     ap.add_argument("--ref-seconds", type=float, default=10.0, help="oracle seconds per reference step")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle seconds for cpu_baseline")
     ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 per-query path")
@@ -331,6 +409,9 @@ def main():
     if args.workload == "c3":  # training pairs follow the workload's recipe
         s_tr, t_tr, eps_tr = synth_pairs.bucketed_pairs(g, train_pairs, TRAIN_SEED)
         ms_log = 4
+    elif args.workload == "c2e":  # edge queries: the switch learns from other edges
+        s_tr, t_tr = synth_pairs.edge_pairs(g, train_pairs, TRAIN_SEED)
+        eps_tr, ms_log = float(w.eps[0]), 8
     elif args.workload == "c5":  # dense columns of a 32M-node graph: 256 MB per query
         s_tr, t_tr = synth_pairs.uniform_pairs(g.n, train_pairs, TRAIN_SEED)
         eps_tr, ms_log, log_chunk = float(w.eps[0]), 3, 64
@@ -402,6 +483,7 @@ def main():
     geer.profile_enable(False)
     value, total_ms = replica_value(float(sum(ms)), w.q, args.steps, world, dist, dev)
     stats = np.frombuffer(st_d.cpu().numpy().tobytes(), dtype=geer.STATS_DTYPE)
+    r_host = r_d.cpu().numpy().copy()  # the timed batch's results (r_d is reused below)
 
     # the same batch under Eq. (17)'s rule
     rule_ms = []
@@ -416,6 +498,23 @@ def main():
         b.synchronize()
         rule_ms.append(a.elapsed_time(b))
     rule_value = world * w.q / (float(np.median(rule_ms[3:])) / 1000.0) if rule_ms else None
+    # the same batch with one switch point for every query, l_b = c: the baseline
+    # a per-query (learned) policy has to beat
+    const_values = {}
+    for c in ((1, 2, 3, 4) if not args.no_extras else ()):
+        oc = geer.default_options(switch_policy=geer.GER_SWITCH_FIXED, fixed_ell_b=c, **base)
+        cms = []
+        for _ in range(3 + args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            G.query_dev(s_d, t_d, e_d, r_d, None, oc, stream=stream.cuda_stream)
+            b.record(stream)
+            b.synchronize()
+            cms.append(a.elapsed_time(b))
+        const_values[c] = world * w.q / (float(np.median(cms[3:])) / 1000.0)
 
     # e2e: host buffers through ger_query_batch_eps, copies inside the timed region
     e2e_t = []
@@ -471,13 +570,32 @@ def main():
         roof = {"kernel": fam[0], "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s",
                 "frac": None, "peak_source": peak_kind, "traffic": None}
     spmm = None if args.no_extras else spmm_leg(G, w, geer, peak, workload=args.workload, base=base)
-    # CPU baseline: the oracle as it stands, one host thread, bounded sample
-    cpu = None
+    # CPU baselines: the oracle as it stands on one host thread (the paper's
+    # setting) and on every host core, bounded samples of the same queries
+    cpu = cpu_n = parity = None
+    host = host_info()
     if not args.no_extras:
-        import oracle
         nq, el = oracle_sample(w, lam, args.cpu_seconds)
         cpu = {"value": nq / el, "unit": "queries/s", "cores": 1, "kind": "oracle",
                "sample": f"first {nq} queries of the workload, {el:.1f} s, same lambda and seed"}
+        nth = max(1, host["nproc"] or 1)
+        nqn, eln = oracle_sample_threads(w, lam, args.cpu_seconds, nth)
+        cpu_n = {"value": nqn / eln, "unit": "queries/s", "cores": nth, "kind": "oracle",
+                 "sample": f"first {nqn} queries of the workload on {nth} threads (one query per task), "
+                           f"{eln:.1f} s"}
+        # the error of this run's results against the FP64 oracle replaying its decisions
+        rows, elp = replay_parity(w, lam, stats, args.cpu_seconds, nth)
+        idx = np.array([i for i, _, _, _ in rows], dtype=np.int64)
+        ref_r = np.array([x for _, x, _, _ in rows])
+        rel = np.abs(r_host[idx] - ref_r) / np.maximum(np.abs(ref_r), 1e-300)
+        cs_ok = sum(int(stats["checksum"][i]) == c for i, _, c, _ in rows)
+        wk_ok = sum(int(stats["walks"][i]) == k for i, _, _, k in rows)
+        parity = {"queries": int(len(rows)), "of": int(w.q), "reference": "FP64 oracle replaying the GPU's "
+                  "l_b, eta_0 and batches (first queries of the timed batch)",
+                  "max_rel_err_r": float(rel.max()), "mean_rel_err_r": float(rel.mean()),
+                  "max_abs_err_r": float(np.abs(r_host[idx] - ref_r).max()), "tolerance": 1e-5,
+                  "within_tolerance": int((rel <= 1e-5).sum()), "walk_checksum_matches": int(cs_ok),
+                  "walk_count_matches": int(wk_ok), "seconds": elp, "threads": nth}
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -486,6 +604,9 @@ def main():
         "roofline": roof,
         "spmm": spmm,
         "cpu_baseline": cpu,
+        "cpu_baseline_threads": cpu_n,
+        "host": host,
+        "parity": parity,
         "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": int(w.q * (4 + 4 + 8)),
                 "d2h_bytes_per_step": int(w.q * 8)},
         "gpu_launches": int(launches),
@@ -498,7 +619,9 @@ def main():
                    "train_seed": TRAIN_SEED, "cost_log_rows": int(clog.feats.shape[0]),
                    "setup_seconds": sw_seconds,
                    "train_batch_ms": {k: v * 1e3 for k, v in fit_times.items()},
-                   "rule_value": rule_value},
+                   "rule_value": rule_value,
+                   "constant_lb_values": {str(c): v for c, v in const_values.items()},
+                   "best_constant_lb": (max(const_values, key=const_values.get) if const_values else None)},
         "preprocess": {"spectral_bound_ms": pre_ms, "lambda": lam, "lambda_2": l2, "lambda_n": ln},
         "kernels": {k: {"launches": v[0], "total_ms": v[1]} for k, v in prof.items()},
         "work": {"walk_steps_per_step": walk_steps, "walk_pairs_per_step": int(stats["walks"].sum()),

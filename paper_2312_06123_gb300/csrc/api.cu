@@ -34,7 +34,7 @@ void note_launches(int k) {
 // ---------------------------------------------------------------------------
 // profiler: CUDA events around launches, on the launch stream
 // ---------------------------------------------------------------------------
-static const char* kFamilyNames[] = {"smm_setup", "smm_alloc", "smm_clear", "smm_push",
+static const char* kFamilyNames[] = {"smm_setup", "smm_advance", "smm_push",
                                               "smm_push_heavy", "smm_finish", "smm_top2", "smm_decide", "dense_spmm",
                                               "amc_schedule", "amc_walk", "amc_reduce", "finalize", "lanczos",
                                      "smm_mlp", "mlp_train"};
@@ -149,8 +149,6 @@ struct Workspace {
     int64_t partial_cap = 0;
     // SMM phase
     QSmm* qsmm = nullptr;
-    int32_t* seg_q = nullptr;     // 2 (q_cap)
-    int64_t* seg_off = nullptr;   // 2 (q_cap + 1)
     int64_t* heavy = nullptr;     // heavy_cap chunk records of the heavy push
     int64_t heavy_cap = 0;
     SmmCtl* ctl = nullptr;
@@ -240,7 +238,7 @@ namespace geer {
 
 static void free_ws(Workspace& w) {
     cudaFree(w.st); cudaFree(w.s); cudaFree(w.t); cudaFree(w.eps); cudaFree(w.r); cudaFree(w.stats);
-    cudaFree(w.chunk_begin); cudaFree(w.partial); cudaFree(w.qsmm); cudaFree(w.seg_q); cudaFree(w.seg_off);
+    cudaFree(w.chunk_begin); cudaFree(w.partial); cudaFree(w.qsmm);
     cudaFree(w.wq); cudaFree(w.chunk_count);
     cudaFree(w.ctl); cudaFree(w.ent); cudaFree(w.sums); cudaFree(w.yvals); cudaFree(w.counters);
     cudaFree(w.heavy);
@@ -277,17 +275,17 @@ static int ensure_ws(ger_graph* g, int64_t q, int64_t pool_cap) {
     }
     if (q > w.q_cap) {
         cudaFree(w.st); cudaFree(w.s); cudaFree(w.t); cudaFree(w.eps); cudaFree(w.r); cudaFree(w.stats);
-        cudaFree(w.chunk_begin); cudaFree(w.partial); cudaFree(w.qsmm); cudaFree(w.seg_q); cudaFree(w.seg_off);
+        cudaFree(w.chunk_begin); cudaFree(w.partial); cudaFree(w.qsmm);
         cudaFree(w.wq); cudaFree(w.chunk_count);
         w.st = nullptr; w.s = nullptr; w.t = nullptr; w.eps = nullptr; w.r = nullptr; w.stats = nullptr;
-        w.chunk_begin = nullptr; w.partial = nullptr; w.qsmm = nullptr; w.seg_q = nullptr; w.seg_off = nullptr;
+        w.chunk_begin = nullptr; w.partial = nullptr; w.qsmm = nullptr;
         w.wq = nullptr; w.chunk_count = nullptr;
         w.q_cap = 0;
         const int64_t qc = std::max<int64_t>(q, 64);
         const int64_t pc = qc * kMaxChunksPerQuery;
         if (alloc(&w.st, qc) || alloc(&w.s, qc) || alloc(&w.t, qc) || alloc(&w.eps, qc) || alloc(&w.r, qc) ||
             alloc(&w.stats, qc) || alloc(&w.chunk_begin, qc + 1) || alloc(&w.partial, pc) ||
-            alloc(&w.qsmm, qc) || alloc(&w.seg_q, 2 * qc) || alloc(&w.seg_off, 2 * (qc + 1)) || alloc(&w.wq, qc) ||
+            alloc(&w.qsmm, qc) || alloc(&w.wq, qc) ||
             alloc(&w.chunk_count, qc)) {
             cudaGetLastError();
             return fail(GER_ERR_OOM, "workspace for %lld queries", (long long)q);
@@ -627,10 +625,6 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
     a.ys = w.yvals;
     a.yt = fp64 ? (void*)(w.yvals + w.pool_cap) : (void*)(reinterpret_cast<float*>(w.yvals) + w.pool_cap);
     a.pool_cap = w.pool_cap;
-    a.seg_q[0] = w.seg_q;
-    a.seg_q[1] = w.seg_q + w.q_cap;
-    a.seg_off[0] = w.seg_off;
-    a.seg_off[1] = w.seg_off + (w.q_cap + 1);
     a.heavy = w.heavy;
     a.heavy_cap = w.heavy_cap;
     a.dense_engine = p.o.smm_engine == GER_ENGINE_DENSE;
@@ -755,12 +749,11 @@ static int prepare_engine(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, b
 static void issue_smm_start(ger_graph* g, Engine& E, bool fp64, cudaStream_t st) {
     if (E.dense) {
         launch_smm_setup(E.a, st);
-        launch_smm_alloc(E.a, st);
         issue_dense_start(g, E.d, fp64, E.cols, st);
         launch_smm_decide(E.a, st, true);
     } else {
         if (E.hybrid) cudaMemsetAsync(g->ws.dblock_q, 0xff, E.d.nblocks * (size_t)(E.d.width / 2) * sizeof(int32_t), st);
-        launch_smm_start(fp64, E.a, E.grid, st);
+        launch_smm_start(fp64, E.a, st);
         if (E.hybrid) launch_dense_migrate(fp64, E.d, E.a, st);
     }
 }
@@ -768,7 +761,6 @@ static void issue_smm_start(ger_graph* g, Engine& E, bool fp64, cudaStream_t st)
 // One further SMM iteration (everything before its advance).
 static void issue_smm_iteration(Engine& E, bool fp64, cudaStream_t st) {
     if (E.dense) {
-        launch_smm_alloc(E.a, st);
         launch_dense_iteration(fp64, E.d, st);
         launch_smm_decide(E.a, st);
     } else if (E.hybrid) {
@@ -790,14 +782,14 @@ static int run_queries(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool
     int rc = prepare_engine(g, p, q0, nq, fp64, &E);
     if (rc) return rc;
     issue_smm_start(g, E, fp64, p.st);
-    launch_smm_advance(E.a, 0, false, p.st);
-    int32_t* n_want = reinterpret_cast<int32_t*>(w.host_rb + 2);
+    launch_smm_advance(E.a, E.grid, 0, false, p.st);
+    int32_t* n_go = reinterpret_cast<int32_t*>(w.host_rb + 2);
     for (int iter = 1; iter < 100000; ++iter) {
-        GER_CUDA(cudaMemcpyAsync(n_want, &w.ctl->n_want, sizeof(int32_t), cudaMemcpyDeviceToHost, p.st));
+        GER_CUDA(cudaMemcpyAsync(n_go, &w.ctl->n_go, sizeof(int32_t), cudaMemcpyDeviceToHost, p.st));
         GER_CUDA(cudaStreamSynchronize(p.st));
-        if (*n_want == 0) break;
+        if (*n_go == 0) break;
         issue_smm_iteration(E, fp64, p.st);
-        launch_smm_advance(E.a, 0, false, p.st);
+        launch_smm_advance(E.a, E.grid, 0, false, p.st);
     }
     issue_amc(g, E.m, nq, p.st);
     return GER_OK;
@@ -855,7 +847,7 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
         cudaMemsetAsync(w.counters, 0, 4 * sizeof(int), st);
         cudaMemsetAsync(w.ctl, 0, sizeof(SmmCtl), st);
         issue_smm_start(g, E, fp64, st);
-        launch_smm_advance(a, handle, true, st);
+        launch_smm_advance(a, E.grid, handle, true, st);
         cudaStreamCaptureStatus cs;
         const cudaGraphNode_t* deps = nullptr;
         size_t ndeps = 0;
@@ -879,7 +871,7 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
                 g_prof_suspend = true;  // no event records inside a conditional body
                 const int64_t before = g_captured;
                 issue_smm_iteration(E, fp64, st2);
-                launch_smm_advance(a, handle, true, st2);
+                launch_smm_advance(a, E.grid, handle, true, st2);
                 body_launches = g_captured - before;
                 g_captured = before;
                 g_prof_suspend = false;
@@ -943,7 +935,8 @@ static int run_batch(ger_graph* g, Plan& p) {
     const bool per_query = p.o.per_query != 0;
     const bool fp64 = p.o.precision == GER_FP64;
     const bool use_graph = !per_query && !p.trace && graphs_enabled();
-    int64_t pool = std::max<int64_t>(g->ws.pool_cap, (int64_t)1 << 22);
+    // the F_0 tables (8 slots per query) and room for the later ones
+    int64_t pool = std::max<int64_t>({g->ws.pool_cap, (int64_t)1 << 22, (int64_t)kF0Slots * p.q + ((int64_t)1 << 20)});
     for (int attempt = 0; attempt < 6; ++attempt) {
         rc = ensure_ws(g, p.q, pool);
         if (rc) return rc;
@@ -978,7 +971,7 @@ static int run_batch(ger_graph* g, Plan& p) {
         GER_CUDA(cudaMemcpyAsync(w.host_rb + 1, &w.ctl->cursor, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                  p.st));
         GER_CUDA(cudaMemcpyAsync(w.host_rb + 3, &w.ctl->iter, sizeof(int32_t), cudaMemcpyDeviceToHost, p.st));
-        GER_CUDA(cudaMemcpyAsync(reinterpret_cast<int32_t*>(w.host_rb + 3) + 1, &w.ctl->pad2, sizeof(int32_t),
+        GER_CUDA(cudaMemcpyAsync(reinterpret_cast<int32_t*>(w.host_rb + 3) + 1, &w.ctl->heavy_max, sizeof(int32_t),
                                  cudaMemcpyDeviceToHost, p.st));
         GER_CUDA(cudaStreamSynchronize(p.st));
         {
@@ -1009,7 +1002,7 @@ static int run_batch(ger_graph* g, Plan& p) {
         const int derr = (int)(reinterpret_cast<int*>(w.host_rb)[0]);
         if (derr == DERR_NONE) return GER_OK;
         if (derr == DERR_TABLE) {
-            const int64_t used = w.host_rb[1];
+            const int64_t used = w.host_rb[1] + (int64_t)kF0Slots * p.q;  // handed-out slots and the F_0 tables
             pool = std::max<int64_t>(2 * used, 2 * w.pool_cap);
             continue;
         }

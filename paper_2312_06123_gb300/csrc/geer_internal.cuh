@@ -89,20 +89,30 @@ struct QSmm {
     double inv_ds, inv_dt;       // 1/d(s), 1/d(t)
 };
 
-// Control block of the SMM phase (device memory).
+// Control block of the SMM phase (device memory, zeroed before a batch).
+// Table slots: the F_0 tables of queries 0..nq-1 sit at [0, 8 nq); every
+// later table is handed out by an atomic bump of `cursor` from 8 nq on, in
+// the decision that asks for it. The advance after a decision clears the
+// slots handed out since `mark` and records them as the next iteration's
+// table range.
 struct SmmCtl {
-    unsigned long long cursor;   // next free slot of the table pool
-    int32_t nseg[2];             // tables allocated per parity
-    int64_t lo[2], hi[2];        // slot range per parity
-    int32_t n_want;              // queries asking for another iteration
+    unsigned long long cursor;   // slots handed out beyond the F_0 tables
+    unsigned long long mark;     // cursor at the last advance
+    int64_t lo[2], hi[2];        // slot range of the tables of iterations with this parity
+    int32_t n_want;              // queries of the current decision that continue
+    int32_t n_go;                // n_want of the last decision (the host loop reads it)
     int32_t n_heavy;             // chunks of high-degree frontier nodes left to the heavy push
     int32_t iter;                // current SMM iteration (0: the initial frontier)
-    int32_t pad;
     // hybrid engine: dense columns handed out, queries moved by the last
     // decision, dense blocks already zeroed
     int32_t dense_next, n_mig, dense_open;
-    int32_t pad2;                // largest heavy-push chunk count of any iteration
+    int32_t heavy_max;           // largest heavy-push chunk count of any iteration
+    uint32_t adv_done;           // CTAs of the advance kernel finished (last one keeps the books)
+    int32_t pad;
 };
+
+// slots of one query's F_0 table (F_0 = {s, t}; load 1/4)
+constexpr int kF0Slots = 8;
 
 // What a walk chunk needs of its query, packed by the batch schedule (one
 // record per query in AMC).

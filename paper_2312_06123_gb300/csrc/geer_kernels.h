@@ -28,9 +28,6 @@ struct SmmArgs {
     void* ys;              // T per slot
     void* yt;              // T per slot
     int64_t pool_cap;
-    // per-parity lists of the tables allocated in one iteration
-    int32_t* seg_q[2];     // nq entries: owning query
-    int64_t* seg_off[2];   // nq + 1 entries: first slot (last entry: end)
     int64_t* heavy;        // per chunk of a high-degree frontier node: slot << 20 | chunk index
     int64_t heavy_cap;
     // dense engine (all queries of the launch when dense_engine != 0)
@@ -115,22 +112,22 @@ struct AmcArgs {
 // SMM phase, level-synchronous over the batch. The iteration number lives
 // in the control block (device memory), so the launches of an iteration are
 // the same every time and can sit in a graph's while loop.
-//   start     : setup, alloc, clear, seed, finish, top2, decide (iteration 0)
-//   iteration : alloc, clear, push (+ heavy push), finish, top2, decide
-//   advance   : iteration += 1; optionally sets the graph's while condition
+//   start     : iteration 0 in closed form (sparse and hybrid engines): set-up,
+//               the F_0 tables, the first decision, the F_1 tables
+//   setup     : set-up alone (dense engine, whose F_0 lives in its blocks)
+//   iteration : push (+ heavy push), finish, top2, decide (+ next tables)
+//   advance   : clears the tables just handed out, iteration += 1, and
+//               optionally sets the graph's while condition
 void launch_smm_setup(const SmmArgs& a, cudaStream_t st);
-void launch_smm_alloc(const SmmArgs& a, cudaStream_t st);
-void launch_smm_clear(const SmmArgs& a, int grid, cudaStream_t st);
-void launch_smm_seed(const SmmArgs& a, cudaStream_t st);
 void launch_smm_push(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 void launch_smm_finish(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 void launch_smm_top2(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 void launch_smm_decide(const SmmArgs& a, cudaStream_t st, bool first = false);
 void launch_smm_mlp(const SmmArgs& a, cudaStream_t st);  // the learned switch's call per query
-void launch_smm_advance(const SmmArgs& a, cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st);
-void launch_smm_start(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
+void launch_smm_advance(const SmmArgs& a, int grid, cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st);
+void launch_smm_start(bool fp64, const SmmArgs& a, cudaStream_t st);
 void launch_smm_iteration(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
-// the sparse part of one iteration (alloc .. top2), without the decision
+// the sparse part of one iteration (push .. top2), without the decision
 void launch_smm_body(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 // the dense engine: iteration 0 and one pull-SpMM iteration (+ its epilogue)
 bool dense_width_ok(int width, bool fp64);
@@ -159,7 +156,7 @@ namespace geer {
 void note_launches(int k);
 
 // kernel families timed by the profiler
-enum Family : int { FAM_SMM_SETUP = 0, FAM_SMM_ALLOC, FAM_SMM_CLEAR, FAM_SMM_PUSH, FAM_SMM_PUSH_HEAVY, FAM_SMM_FINISH,
+enum Family : int { FAM_SMM_SETUP = 0, FAM_SMM_ADVANCE, FAM_SMM_PUSH, FAM_SMM_PUSH_HEAVY, FAM_SMM_FINISH,
                     FAM_SMM_TOP2, FAM_SMM_DECIDE, FAM_DENSE_SPMM, FAM_AMC_SCHEDULE, FAM_AMC_WALK, FAM_AMC_REDUCE,
                     FAM_FINALIZE, FAM_LANCZOS, FAM_SMM_MLP, FAM_MLP_TRAIN, FAM_COUNT };
 // bracket one launch on stream st with profiler events (no-op when off)

@@ -36,10 +36,8 @@ constexpr size_t kOffCounters = 0;  // error flag (int) and spare words
 constexpr size_t kOffCtl = align256(kOffCounters + 64);
 constexpr size_t kOffState = align256(kOffCtl + sizeof(SmmCtl));
 constexpr size_t kOffQSmm = align256(kOffState + sizeof(QState) * kNoAllocMaxQueries);
-constexpr size_t kOffSegQ = align256(kOffQSmm + sizeof(QSmm) * kNoAllocMaxQueries);
-constexpr size_t kOffSegOff = align256(kOffSegQ + sizeof(int32_t) * 2 * kNoAllocMaxQueries);
 constexpr int64_t kNoAllocHeavy = 4096;
-constexpr size_t kOffHeavy = align256(kOffSegOff + sizeof(int64_t) * 2 * (kNoAllocMaxQueries + 1));
+constexpr size_t kOffHeavy = align256(kOffQSmm + sizeof(QSmm) * kNoAllocMaxQueries);
 constexpr size_t kOffChunk = align256(kOffHeavy + sizeof(int64_t) * kNoAllocHeavy);
 constexpr size_t kOffWalkQ = align256(kOffChunk + sizeof(int64_t) * (kNoAllocMaxQueries + 1));
 constexpr size_t kOffCount = align256(kOffWalkQ + sizeof(WalkQ) * kNoAllocMaxQueries);
@@ -172,10 +170,6 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     a.yt = fp64 ? (void*)(reinterpret_cast<double*>(base + kOffY) + kNoAllocPool)
                 : (void*)(reinterpret_cast<float*>(base + kOffY) + kNoAllocPool);
     a.pool_cap = kNoAllocPool;
-    a.seg_q[0] = reinterpret_cast<int32_t*>(base + kOffSegQ);
-    a.seg_q[1] = a.seg_q[0] + kNoAllocMaxQueries;
-    a.seg_off[0] = reinterpret_cast<int64_t*>(base + kOffSegOff);
-    a.seg_off[1] = a.seg_off[0] + (kNoAllocMaxQueries + 1);
     a.dense_engine = 0;
     a.dense_width = 2;
     a.dense_fp64 = fp64;
@@ -186,19 +180,19 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     a.err_flag = counters + 1;
     a.wq = reinterpret_cast<WalkQ*>(base + kOffWalkQ);
     const int grid = sm_count * 8;
-    launch_smm_start(fp64, a, grid, st);
-    launch_smm_advance(a, 0, false, st);
+    launch_smm_start(fp64, a, st);
+    launch_smm_advance(a, grid, 0, false, st);
     // a launch that failed to start (bad configuration, missing kernel image)
     // leaves the control words at their zeros: catch it before reading them
     rc = check_launches();
     if (rc) return rc;
     for (int iter = 1; iter < 100000; ++iter) {
-        int n_want = 0;
-        rc = sync_read_int(&ctl->n_want, &n_want, st);
+        int n_go = 0;
+        rc = sync_read_int(&ctl->n_go, &n_go, st);
         if (rc) return rc;
-        if (n_want == 0) break;
+        if (n_go == 0) break;
         launch_smm_iteration(fp64, a, grid, st);
-        launch_smm_advance(a, 0, false, st);
+        launch_smm_advance(a, grid, 0, false, st);
         rc = check_launches();
         if (rc) return rc;
     }

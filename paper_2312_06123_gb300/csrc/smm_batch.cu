@@ -120,176 +120,266 @@ __device__ __forceinline__ uint32_t table_insert(GEntry* tab, uint32_t mask, int
 }  // namespace
 
 // ---------------------------------------------------------------------------
-// set-up: validation, l (Eq. 6 or Eq. 5), first table request
+// set-up: validation and l (Eq. 6 or Eq. 5) of one query
 // ---------------------------------------------------------------------------
-__global__ void smm_setup_kernel(SmmArgs a) {
+// Resets the query's state; returns true when the query enters the SMM loop
+// (s != t, valid input, l defined).
+__device__ __forceinline__ bool setup_query(const SmmArgs& a, int64_t q) {
     const int64_t* row_ptr = a.g.row_ptr;
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->iter = 0;
+    QState* Q = a.st + q;
+    QSmm* M = a.sm + q;
+    const int32_t s = a.s[q], t = a.t[q];
+    const double eps = a.eps ? a.eps[q] : a.eps_scalar;
+    Q->s = s; Q->t = t; Q->eps = eps; Q->qidx = a.q_index_base + (int32_t)q;
+    Q->batch = 0; Q->err = 0; Q->r_b = 0; Q->r_f = 0; Q->r = 0; Q->psi = 0;
+    Q->volume = 0; Q->h = 0; Q->f_last = 0; Q->eta0 = 0; Q->eta = 0; Q->walks = 0;
+    Q->walk_steps = 0; Q->checksum = 0; Q->ppc = 0; Q->nchunks = 0; Q->table_off = 0;
+    Q->table_mask = -1; Q->front = 0; Q->ell = 0; Q->ell_b = 0; Q->lf = 0; Q->ds = 0; Q->dt = 0;
+    M->run = 0; M->want = 0; M->mlp_stop = 0;
+    M->tab_off = M->tab_cap = M->ntab_off = M->ntab_cap = 0;
+    M->dense = a.dense_engine ? 1 : 0;
+    M->dgo = 0;
+    M->dblock = a.dense_engine ? (int32_t)(q / (a.dense_width / 2)) : -1;
+    M->dcol = a.dense_engine ? (int32_t)(q % (a.dense_width / 2)) : -1;
+    Q->dense_vals = nullptr;
+    Q->dense_stride = 0;
+    M->vol_paper = M->vol_union = M->count = 0;
+    M->max1s = M->max1t = M->max2s = M->max2t = M->cnt1s = M->cnt1t = 0;
+    M->sval[0] = M->sval[1] = M->sval[2] = M->sval[3] = 0.0;
+    a.wq[q].eta = 0;  // no walks unless the query enters AMC
+    if (s < 0 || s >= a.g.n || t < 0 || t >= a.g.n || !(eps > 0.0)) {
+        Q->status = ST_ERROR;
+        Q->err = DERR_NODE_RANGE;
+        atomicCAS(a.err_flag, 0, DERR_NODE_RANGE);
+        return false;
+    }
+    if (s == t) {  // r(s,s) = 0 (Definition 1)
+        Q->status = ST_DONE;
+        return false;
+    }
+    const int64_t dsi = row_ptr[s + 1] - row_ptr[s], dti = row_ptr[t + 1] - row_ptr[t];
+    const double ds = (double)dsi, dt = (double)dti;
+    int64_t ell;
+    const double lam = a.lambda;
+    if (!(lam < 1.0)) {
+        ell = -1;
+    } else if (lam <= 0.0) {
+        ell = 0;
+    } else {
+        const double v = a.ell_formula == 1
+                             ? ceil(log(4.0 / (eps - eps * lam)) / log(1.0 / lam) - 1.0)
+                             : ceil(log((2.0 / ds + 2.0 / dt) / (eps * (1.0 - lam))) / log(1.0 / lam) - 1.0);
+        ell = v < 0.0 ? 0 : (int64_t)v;
+    }
+    if (ell < 0) {
+        Q->status = ST_ERROR;
+        Q->err = DERR_ELL;
+        atomicCAS(a.err_flag, 0, DERR_ELL);
+        return false;
+    }
+    Q->status = ST_SMM;
+    Q->ds = (int32_t)dsi;
+    Q->dt = (int32_t)dti;
+    Q->ell = (int32_t)ell;
+    M->shift_s = fixed_shift(dsi);
+    M->shift_t = fixed_shift(dti);
+    M->inv_ds = 1.0 / ds;
+    M->inv_dt = 1.0 / dt;
+    M->lb_target = a.policy == 2 ? (a.fixed_lb < 0 ? (int32_t)ell : min(a.fixed_lb, (int32_t)ell)) : -1;
+    return true;
+}
+
+// Set-up alone (dense engine: F_0 = {s, t} is written into the query's
+// block column by the dense engine, and its first decision follows).
+__global__ void smm_setup_kernel(SmmArgs a) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctl->iter = 0;
+        a.ctl->lo[0] = a.ctl->hi[0] = 0;
+    }
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < a.nq; q += (int64_t)gridDim.x * blockDim.x) {
+        if (setup_query(a, q) && a.sm[q].dense) {
+            a.sm[q].dgo = 1;
+            a.sm[q].run = 1;
+        }
+    }
+}
+
+// A query leaves SMM after iteration lb (Algorithm 3's switch): its state of
+// Eq. (17) (psi, volume, h, eta_0) is kept for the statistics, and it enters
+// AMC with the lookup table of its last frontier (or its dense column), or,
+// with no walk left (l_f = 0), finishes with r = r_b.
+__device__ __forceinline__ void leave_smm(const SmmArgs& a, int64_t q, QState* Q, QSmm* M, int iter, int64_t lb,
+                                          int64_t lf, double psi, double vol, double h, int64_t eta0,
+                                          int64_t count) {
+    M->run = 0;
+    M->dgo = 0;
+    Q->ell_b = (int32_t)lb;
+    Q->lf = (int32_t)lf;
+    Q->psi = psi;
+    Q->volume = vol;
+    Q->h = h;
+    Q->eta0 = eta0;
+    Q->eta = eta0;
+    Q->front = (int32_t)count;
+    if (M->dense) {
+        // the values of the last iteration sit in dense buffer (iter & 1)
+        const size_t esz = a.dense_fp64 ? sizeof(double) : sizeof(float);
+        const char* base = reinterpret_cast<const char*>(a.dense_X[iter & 1]);
+        Q->dense_vals = base + ((size_t)M->dblock * (size_t)a.g.n * (size_t)a.dense_width + 2 * (size_t)M->dcol) * esz;
+        Q->dense_stride = a.dense_width;
+        Q->table_off = 0;
+        Q->table_mask = -1;
+    } else {
+        Q->table_off = M->tab_off;
+        Q->table_mask = (int32_t)(M->tab_cap - 1);
+    }
+    if (lf > 0) {
+        Q->status = ST_AMC;
+        // the query's walk record
+        WalkQ* wr = a.wq + q;
+        wr->s = Q->s;
+        wr->t = Q->t;
+        if (a.g.node_info) {
+            wr->s_info = a.g.node_info[Q->s];
+            wr->t_info = a.g.node_info[Q->t];
+        } else {
+            const int64_t rs = a.g.row_ptr[Q->s], rt = a.g.row_ptr[Q->t];
+            wr->s_info = make_uint2((uint32_t)rs, (uint32_t)Q->ds);
+            wr->t_info = make_uint2((uint32_t)rt, (uint32_t)Q->dt);
+        }
+        wr->lf = (int32_t)lf;
+        wr->qidx = Q->qidx;
+        wr->eta = eta0;
+        wr->table_off = Q->table_off;
+        wr->mask = Q->table_mask;
+        wr->dstride = Q->dense_stride;
+        wr->dvals = Q->dense_vals;
+        wr->inv_ds = 1.0 / (double)Q->ds;
+        wr->inv_dt = 1.0 / (double)Q->dt;
+    } else {
+        Q->status = ST_DONE;
+        Q->r = Q->r_b;
+    }
+}
+
+// A query continues into the next iteration: on the hybrid engine a free
+// dense column when its next push has >= migrate_at pairs, else a frontier
+// table for at most min(push pairs, n) nodes at load <= 1/2, bump-allocated
+// from the pool. Returns false (query failed) when the table is beyond the
+// option's limit or the pool.
+__device__ __forceinline__ bool continue_smm(const SmmArgs& a, int64_t q, QState* Q, QSmm* M, int64_t lb,
+                                             unsigned long long push_pairs) {
+    if (M->dense) {
+        M->dgo = 1;
+        M->run = 1;
+        atomicAdd(&a.ctl->n_want, 1);
+        return true;
+    }
+    if (a.hybrid && (int64_t)push_pairs >= a.migrate_at) {
+        int col = atomicAdd(&a.ctl->dense_next, 1);
+        if (col < a.dense_cap) {
+            const int qpb = a.dense_width / 2;
+            M->dense = 1;
+            M->dgo = 1;
+            M->run = 1;
+            M->dblock = col / qpb;
+            M->dcol = col % qpb;
+            a.dense_block_q[col] = (int32_t)q;
+            a.mig_list[atomicAdd(&a.ctl->n_mig, 1)] = (int32_t)q;
+            atomicAdd(&a.ctl->n_want, 1);
+            return true;
+        }
+    }
+    int64_t cap = 16;
+    const int64_t most = min((int64_t)push_pairs, (int64_t)a.g.n);
+    while (cap < 2 * most) cap <<= 1;
+    if (cap > a.max_table) {
+        Q->status = ST_ERROR;
+        Q->err = DERR_CAPACITY;
+        Q->ell_b = (int32_t)lb;
+        M->run = 0;
+        atomicCAS(a.err_flag, 0, DERR_CAPACITY);
+        return false;
+    }
+    const int64_t off = (int64_t)kF0Slots * a.nq + (int64_t)atomicAdd(&a.ctl->cursor, (unsigned long long)cap);
+    if (off + cap > a.pool_cap) {  // the pool is too small for this batch: the host grows it and reruns
+        Q->status = ST_ERROR;
+        Q->err = DERR_TABLE;
+        M->run = 0;
+        atomicCAS(a.err_flag, 0, DERR_TABLE);
+        return false;
+    }
+    M->ntab_off = off;
+    M->ntab_cap = cap;
+    M->run = 1;
+    atomicAdd(&a.ctl->n_want, 1);
+    return true;
+}
+
+// Iteration 0 of the sparse and hybrid engines, in closed form (Algorithm 3
+// before its first SMM step), one thread per query: set-up; the query's
+// F_0 table at slots [8q, 8q + 8): F_0 = {s, t}, s* = e_s, t* = e_t, g(s) =
+// 1/d(s), g(t) = -1/d(t) (the push source of iteration 1, and the walks'
+// lookup table when no SMM step runs); Algorithm 2's four terms at i = 0,
+// r_b = 1/d(s) + 1/d(t); the first decision (the loop runs once when
+// l >= 1, or as a fixed policy says); and the table of F_1 (whose push has
+// d(s) + d(t) pairs). Eq. (17)'s volume is d(s) + d(t) and max_1 = 1,
+// max_2 = 0 for both vectors (one non-zero entry each).
+template <typename T>
+__global__ void smm_start_kernel(SmmArgs a) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctl->iter = 0;
+        a.ctl->lo[0] = 0;
+        a.ctl->hi[0] = (int64_t)kF0Slots * a.nq;
+    }
+    T* ys = reinterpret_cast<T*>(a.ys);
+    T* yt = reinterpret_cast<T*>(a.yt);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < a.nq; q += (int64_t)gridDim.x * blockDim.x) {
+        const bool smm = setup_query(a, q);
+        // every F_0 table is written, so the push of iteration 1 reads no stale slot
+        const int64_t off = (int64_t)kF0Slots * q;
+        GEntry* tab = a.ent + off;
+        GEntry empty;
+        empty.v = -1;
+        empty.bits = 0u;
+        empty.g = 0.0;
+#pragma unroll
+        for (int k = 0; k < kF0Slots; ++k) tab[k] = empty;
+        if (!smm) continue;
         QState* Q = a.st + q;
         QSmm* M = a.sm + q;
-        const int32_t s = a.s[q], t = a.t[q];
-        const double eps = a.eps ? a.eps[q] : a.eps_scalar;
-        Q->s = s; Q->t = t; Q->eps = eps; Q->qidx = a.q_index_base + (int32_t)q;
-        Q->batch = 0; Q->err = 0; Q->r_b = 0; Q->r_f = 0; Q->r = 0; Q->psi = 0;
-        Q->volume = 0; Q->h = 0; Q->f_last = 0; Q->eta0 = 0; Q->eta = 0; Q->walks = 0;
-        Q->walk_steps = 0; Q->checksum = 0; Q->ppc = 0; Q->nchunks = 0; Q->table_off = 0;
-        Q->table_mask = -1; Q->front = 0; Q->ell = 0; Q->ell_b = 0; Q->lf = 0; Q->ds = 0; Q->dt = 0;
-        M->run = 0; M->want = 0; M->tab_off = M->tab_cap = M->ntab_off = M->ntab_cap = 0;
-        M->dense = a.dense_engine ? 1 : 0;
-        M->dgo = 0;
-        M->dblock = a.dense_engine ? (int32_t)(q / (a.dense_width / 2)) : -1;
-        M->dcol = a.dense_engine ? (int32_t)(q % (a.dense_width / 2)) : -1;
-        Q->dense_vals = nullptr;
-        Q->dense_stride = 0;
-        M->vol_paper = M->vol_union = M->count = 0;
-        M->max1s = M->max1t = M->max2s = M->max2t = M->cnt1s = M->cnt1t = 0;
-        M->sval[0] = M->sval[1] = M->sval[2] = M->sval[3] = 0.0;
-        if (s < 0 || s >= a.g.n || t < 0 || t >= a.g.n || !(eps > 0.0)) {
-            Q->status = ST_ERROR;
-            Q->err = DERR_NODE_RANGE;
-            atomicCAS(a.err_flag, 0, DERR_NODE_RANGE);
-            continue;
-        }
-        if (s == t) {  // r(s,s) = 0 (Definition 1)
-            Q->status = ST_DONE;
-            continue;
-        }
-        const int64_t dsi = row_ptr[s + 1] - row_ptr[s], dti = row_ptr[t + 1] - row_ptr[t];
-        const double ds = (double)dsi, dt = (double)dti;
-        int64_t ell;
-        const double lam = a.lambda;
-        if (!(lam < 1.0)) {
-            ell = -1;
-        } else if (lam <= 0.0) {
-            ell = 0;
+        const double ds = (double)Q->ds, dt = (double)Q->dt;
+        // linear probing in an 8-slot table, as table_insert would place them
+        const uint32_t hs = hash32((uint32_t)Q->s) & (kF0Slots - 1);
+        uint32_t ht = hash32((uint32_t)Q->t) & (kF0Slots - 1);
+        if (ht == hs) ht = (ht + 1) & (kF0Slots - 1);
+        GEntry es, et;
+        es.v = Q->s;
+        es.bits = 1u | ((uint32_t)q << 2);
+        es.g = 1.0 * M->inv_ds - 0.0 * M->inv_dt;
+        et.v = Q->t;
+        et.bits = 2u | ((uint32_t)q << 2);
+        et.g = 0.0 * M->inv_ds - 1.0 * M->inv_dt;
+        tab[hs] = es;
+        tab[ht] = et;
+        ys[off + hs] = T(1);
+        yt[off + hs] = T(0);
+        ys[off + ht] = T(0);
+        yt[off + ht] = T(1);
+        M->tab_off = off;
+        M->tab_cap = kF0Slots;
+        // Algorithm 2 at i = 0: s*(s)/d(s) + t*(t)/d(t) - s*(t)/d(s) - t*(s)/d(t)
+        Q->r_b = 1.0 / ds + 1.0 / dt - 0.0 / ds - 0.0 / dt;
+        const int64_t ell = Q->ell;
+        const bool go = M->lb_target >= 0 ? (M->lb_target > 0) : (ell >= 1);
+        const unsigned long long vol = (unsigned long long)Q->ds + (unsigned long long)Q->dt;
+        if (go) {
+            continue_smm(a, q, Q, M, 0, vol);
         } else {
-            const double v = a.ell_formula == 1
-                                 ? ceil(log(4.0 / (eps - eps * lam)) / log(1.0 / lam) - 1.0)
-                                 : ceil(log((2.0 / ds + 2.0 / dt) / (eps * (1.0 - lam))) / log(1.0 / lam) - 1.0);
-            ell = v < 0.0 ? 0 : (int64_t)v;
-        }
-        if (ell < 0) {
-            Q->status = ST_ERROR;
-            Q->err = DERR_ELL;
-            atomicCAS(a.err_flag, 0, DERR_ELL);
-            continue;
-        }
-        Q->status = ST_SMM;
-        Q->ds = (int32_t)dsi;
-        Q->dt = (int32_t)dti;
-        Q->ell = (int32_t)ell;
-        M->shift_s = fixed_shift(dsi);
-        M->shift_t = fixed_shift(dti);
-        M->inv_ds = 1.0 / ds;
-        M->inv_dt = 1.0 / dt;
-        M->lb_target = a.policy == 2 ? (a.fixed_lb < 0 ? (int32_t)ell : min(a.fixed_lb, (int32_t)ell)) : -1;
-        if (M->dense) M->dgo = 1;  // the dense engine sets up F_0 in its own buffers
-        else M->want = 8;          // F_0 = {s, t}
-    }
-}
-
-// ---------------------------------------------------------------------------
-// alloc (one CTA): tables for the queries that asked for one, in query order
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kSerialCta) smm_alloc_kernel(SmmArgs a) {
-    __shared__ int64_t scan[kSerialWarps + 1];
-    __shared__ int64_t carry, seg_carry;
-    const int tid = threadIdx.x;
-    SmmCtl* C = a.ctl;
-    const int parity = C->iter & 1;
-    const unsigned long long base = C->cursor;
-    if (tid == 0) {
-        carry = 0;
-        seg_carry = 0;
-    }
-    __syncthreads();
-    int32_t* seg_q = a.seg_q[parity];
-    int64_t* seg_off = a.seg_off[parity];
-    for (int64_t tile = 0; tile < a.nq; tile += kSerialCta) {
-        const int64_t q = tile + tid;
-        int64_t want = 0;
-        if (q < a.nq) {
-            QSmm* M = a.sm + q;
-            want = M->want;
-            M->want = 0;
-            M->run = M->dense ? M->dgo : (want > 0);
-        }
-        int64_t tot, ntot;
-        const int64_t ex = cta_excl_scan_w<kSerialWarps>(want, scan, &tot);
-        const int64_t sx = cta_excl_scan_w<kSerialWarps>(want > 0 ? 1 : 0, scan, &ntot);
-        if (want > 0) {
-            const int64_t off = (int64_t)base + carry + ex;
-            QSmm* M = a.sm + q;
-            M->ntab_off = off;
-            M->ntab_cap = want;
-            seg_q[seg_carry + sx] = (int32_t)q;
-            seg_off[seg_carry + sx] = off;
-            if (off + want > a.pool_cap) {  // the pool is too small for this batch
-                a.st[q].status = ST_ERROR;
-                a.st[q].err = DERR_TABLE;
-                M->run = 0;
-                atomicCAS(a.err_flag, 0, DERR_TABLE);
-            }
-        }
-        __syncthreads();
-        if (tid == 0) {
-            carry += tot;
-            seg_carry += ntot;
-        }
-        __syncthreads();
-    }
-    if (tid == 0) {
-        int64_t hi = (int64_t)base + carry;
-        if (hi > a.pool_cap) hi = a.pool_cap;
-        seg_off[seg_carry] = hi;
-        C->nseg[parity] = (int32_t)seg_carry;
-        C->lo[parity] = (int64_t)base;
-        C->hi[parity] = hi;
-        C->cursor = base + (unsigned long long)carry;
-        C->n_want = 0;
-        // the largest heavy-push demand of the batch (the host grows the list to it)
-        if (C->n_heavy > C->pad2) C->pad2 = C->n_heavy;
-        C->n_heavy = 0;
-    }
-}
-
-// clear the tables allocated for `parity`
-__global__ void smm_clear_kernel(SmmArgs a) {
-    const int parity = a.ctl->iter & 1;
-    const int64_t lo = a.ctl->lo[parity], hi = a.ctl->hi[parity];
-    for (int64_t j = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < hi;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        GEntry e;
-        e.v = -1;
-        e.bits = 0;
-        e.g = 0.0;
-        a.ent[j] = e;
-        a.sum_s[j] = 0ull;
-        a.sum_t[j] = 0ull;
-    }
-}
-
-// F_0 = {s, t} with s* = e_s, t* = e_t: sums d(s) 2^S_s and d(t) 2^S_t make
-// y = sum / d = 1 exactly in the finish kernel
-__global__ void smm_seed_kernel(SmmArgs a) {
-    const int nseg = a.ctl->nseg[0];
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nseg; k += gridDim.x * blockDim.x) {
-        const int q = a.seg_q[0][k];
-        const QSmm* M = a.sm + q;
-        if (!M->run) continue;
-        const QState* Q = a.st + q;
-        GEntry* tab = a.ent + M->ntab_off;
-        const uint32_t mask = (uint32_t)(M->ntab_cap - 1);
-        const uint32_t hs = table_insert(tab, mask, Q->s, a.err_flag);
-        if (hs != kNoSlot) {
-            tab[hs].bits = 1u | ((uint32_t)q << 2);
-            a.sum_s[M->ntab_off + hs] = (unsigned long long)Q->ds << M->shift_s;
-        }
-        const uint32_t ht = table_insert(tab, mask, Q->t, a.err_flag);
-        if (ht != kNoSlot) {
-            tab[ht].bits = 2u | ((uint32_t)q << 2);
-            a.sum_t[M->ntab_off + ht] = (unsigned long long)Q->dt << M->shift_t;
+            double psi = 0.0, h = 0.0;
+            int64_t eta0 = 0;
+            if (ell > 0) switch_quantities(ell, 1.0, 0.0, 1.0, 0.0, ds, dt, Q->eps, a.delta, a.tau, &psi, &eta0, &h);
+            leave_smm(a, q, Q, M, 0, 0, ell, psi, (double)vol, h, eta0, 2);
         }
     }
 }
@@ -503,7 +593,8 @@ __global__ void __launch_bounds__(256) smm_top2_kernel(SmmArgs a) {
     }
 }
 
-// decide: one thread per query whose table was just finished
+// decide: one thread per query whose table was just finished; a query that
+// continues gets its next table (or dense column) here
 __global__ void smm_decide_kernel(SmmArgs a) {
     const int iter = a.ctl->iter;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < a.nq; q += gridDim.x * blockDim.x) {
@@ -545,102 +636,51 @@ __global__ void smm_decide_kernel(SmmArgs a) {
         // the table just finished holds the current frontier
         M->tab_off = M->ntab_off;
         M->tab_cap = M->ntab_cap;
-        if (go && M->dense) {
-            M->dgo = 1;
-            atomicAdd(&a.ctl->n_want, 1);
-        } else if (go) {
-            int col = -1;
-            if (a.hybrid && (int64_t)M->vol_union >= a.migrate_at) {
-                // hybrid engine: the next push is large; continue in a free dense column
-                col = atomicAdd(&a.ctl->dense_next, 1);
-                if (col >= a.dense_cap) col = -1;
-            }
-            if (col >= 0) {
-                const int qpb = a.dense_width / 2;
-                M->dense = 1;
-                M->dgo = 1;
-                M->dblock = col / qpb;
-                M->dcol = col % qpb;
-                a.dense_block_q[col] = q;
-                a.mig_list[atomicAdd(&a.ctl->n_mig, 1)] = q;
-                atomicAdd(&a.ctl->n_want, 1);
-                goto next_query;
-            }
-            int64_t cap = 16;
-            // the next frontier has at most min(push pairs, n) distinct nodes; load <= 1/2
-            const int64_t most = min((int64_t)M->vol_union, (int64_t)a.g.n);
-            while (cap < 2 * most) cap <<= 1;
-            if (cap > a.max_table) {
-                Q->status = ST_ERROR;
-                Q->err = DERR_CAPACITY;
-                Q->ell_b = (int32_t)lb;
-                M->run = 0;
-                atomicCAS(a.err_flag, 0, DERR_CAPACITY);
-                continue;
-            }
-            M->want = (int32_t)cap;
-            atomicAdd(&a.ctl->n_want, 1);
-        } else {
-            M->dgo = 0;
-            Q->ell_b = (int32_t)lb;
-            Q->lf = (int32_t)lf;
-            Q->psi = psi;
-            Q->volume = vol;
-            Q->h = h;
-            Q->eta0 = eta0;
-            Q->eta = eta0;
-            Q->front = (int32_t)M->count;
-            if (M->dense) {
-                // the values of the last iteration sit in dense buffer (iter & 1)
-                const size_t esz = a.dense_fp64 ? sizeof(double) : sizeof(float);
-                const char* base = reinterpret_cast<const char*>(a.dense_X[iter & 1]);
-                Q->dense_vals = base + ((size_t)M->dblock * (size_t)a.g.n * (size_t)a.dense_width + 2 * (size_t)M->dcol) * esz;
-                Q->dense_stride = a.dense_width;
-                Q->table_off = 0;
-                Q->table_mask = -1;
-            } else {
-                Q->table_off = M->tab_off;
-                Q->table_mask = (int32_t)(M->tab_cap - 1);
-            }
-            if (lf > 0) {
-                Q->status = ST_AMC;
-                // the static part of the query's walk record
-                WalkQ* wr = a.wq + q;
-                wr->s = Q->s;
-                wr->t = Q->t;
-                if (a.g.node_info) {
-                    wr->s_info = a.g.node_info[Q->s];
-                    wr->t_info = a.g.node_info[Q->t];
-                } else {
-                    const int64_t rs = a.g.row_ptr[Q->s], rt = a.g.row_ptr[Q->t];
-                    wr->s_info = make_uint2((uint32_t)rs, (uint32_t)Q->ds);
-                    wr->t_info = make_uint2((uint32_t)rt, (uint32_t)Q->dt);
-                }
-                wr->lf = (int32_t)lf;
-                wr->qidx = Q->qidx;
-                wr->table_off = Q->table_off;
-                wr->mask = Q->table_mask;
-                wr->dstride = Q->dense_stride;
-                wr->dvals = Q->dense_vals;
-                wr->inv_ds = 1.0 / ds;
-                wr->inv_dt = 1.0 / dt;
-            } else {
-                Q->status = ST_DONE;
-                Q->r = Q->r_b;
-            }
-        }
-    next_query:
+        if (go) continue_smm(a, q, Q, M, lb, M->vol_union);
+        else leave_smm(a, q, Q, M, iter, lb, lf, psi, vol, h, eta0, (int64_t)M->count);
         M->vol_paper = M->vol_union = M->count = 0;
         M->max1s = M->max1t = M->max2s = M->max2t = M->cnt1s = M->cnt1t = 0;
         M->sval[0] = M->sval[1] = M->sval[2] = M->sval[3] = 0.0;
     }
 }
 
-// advance: next iteration; in a captured graph, also the while condition
-// (another iteration while some query asked for one)
-__global__ void smm_advance_kernel(SmmArgs a, cudaGraphConditionalHandle h, int use_handle) {
+// advance: clears the tables handed out since the last advance (by the
+// start kernel or the decision just taken) and, in the CTA that finishes
+// last, keeps the books: their slot range for the next iteration's kernels,
+// iteration += 1, the count of continuing queries for the host loop and, in
+// a captured graph, the while condition (another iteration while some query
+// continues).
+__global__ void __launch_bounds__(256) smm_advance_kernel(SmmArgs a, cudaGraphConditionalHandle h, int use_handle) {
+    __shared__ bool last;
     SmmCtl* C = a.ctl;
-    C->iter += 1;
+    const int64_t base = (int64_t)kF0Slots * a.nq;
+    const int64_t lo = base + (int64_t)C->mark;
+    const int64_t hi = min(base + (int64_t)C->cursor, a.pool_cap);
+    for (int64_t j = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < hi;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        GEntry e;
+        e.v = -1;
+        e.bits = 0;
+        e.g = 0.0;
+        a.ent[j] = e;
+        a.sum_s[j] = 0ull;
+        a.sum_t[j] = 0ull;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&C->adv_done, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    // every other CTA has read mark and cursor (before counting itself done)
+    const int next = C->iter + 1;
+    C->lo[next & 1] = lo;
+    C->hi[next & 1] = hi > lo ? hi : lo;
+    C->mark = C->cursor;
+    C->iter = next;
+    C->n_go = C->n_want;
+    C->n_want = 0;
+    if (C->n_heavy > C->heavy_max) C->heavy_max = C->n_heavy;
+    C->n_heavy = 0;
+    C->adv_done = 0u;
     if (a.hybrid) {
         // the moved queries' columns are filled; their blocks are zeroed
         const int qpb = a.dense_width / 2;
@@ -648,7 +688,7 @@ __global__ void smm_advance_kernel(SmmArgs a, cudaGraphConditionalHandle h, int 
         C->dense_open = (used + qpb - 1) / qpb;
         C->n_mig = 0;
     }
-    if (use_handle) cudaGraphSetConditional(h, C->n_want > 0 ? 1u : 0u);
+    if (use_handle) cudaGraphSetConditional(h, C->n_go > 0 ? 1u : 0u);
 }
 
 // ---------------------------------------------------------------------------
@@ -662,25 +702,12 @@ void launch_smm_setup(const SmmArgs& a, cudaStream_t st) {
     note_launches(1);
 }
 
-void launch_smm_alloc(const SmmArgs& a, cudaStream_t st) {
-    prof_begin(FAM_SMM_ALLOC, st);
-    smm_alloc_kernel<<<1, kSerialCta, 0, st>>>(a);
-    prof_end(FAM_SMM_ALLOC, st);
-    note_launches(1);
-}
-
-void launch_smm_clear(const SmmArgs& a, int grid, cudaStream_t st) {
-    prof_begin(FAM_SMM_CLEAR, st);
-    smm_clear_kernel<<<grid, 256, 0, st>>>(a);
-    prof_end(FAM_SMM_CLEAR, st);
-    note_launches(1);
-}
-
-void launch_smm_seed(const SmmArgs& a, cudaStream_t st) {
+void launch_smm_start(bool fp64, const SmmArgs& a, cudaStream_t st) {
     const int grid = query_grid(a.nq);
-    prof_begin(FAM_SMM_PUSH, st);
-    smm_seed_kernel<<<grid, kQueryCta, 0, st>>>(a);
-    prof_end(FAM_SMM_PUSH, st);
+    prof_begin(FAM_SMM_SETUP, st);
+    if (fp64) smm_start_kernel<double><<<grid, kQueryCta, 0, st>>>(a);
+    else smm_start_kernel<float><<<grid, kQueryCta, 0, st>>>(a);
+    prof_end(FAM_SMM_SETUP, st);
     note_launches(1);
 }
 
@@ -722,14 +749,14 @@ void launch_smm_decide(const SmmArgs& a, cudaStream_t st, bool first) {
     note_launches(1);
 }
 
-void launch_smm_advance(const SmmArgs& a, cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st) {
-    smm_advance_kernel<<<1, 1, 0, st>>>(a, h, use_handle ? 1 : 0);
+void launch_smm_advance(const SmmArgs& a, int grid, cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st) {
+    prof_begin(FAM_SMM_ADVANCE, st);
+    smm_advance_kernel<<<grid, 256, 0, st>>>(a, h, use_handle ? 1 : 0);
+    prof_end(FAM_SMM_ADVANCE, st);
     note_launches(1);
 }
 
 void launch_smm_body(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
-    launch_smm_alloc(a, st);
-    launch_smm_clear(a, grid, st);
     launch_smm_push(fp64, a, grid, st);
     launch_smm_finish(fp64, a, grid, st);
     launch_smm_top2(fp64, a, grid, st);
@@ -738,16 +765,6 @@ void launch_smm_body(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
 void launch_smm_iteration(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
     launch_smm_body(fp64, a, grid, st);
     launch_smm_decide(a, st);
-}
-
-void launch_smm_start(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
-    launch_smm_setup(a, st);
-    launch_smm_alloc(a, st);
-    launch_smm_clear(a, grid, st);
-    launch_smm_seed(a, st);
-    launch_smm_finish(fp64, a, grid, st);
-    launch_smm_top2(fp64, a, grid, st);
-    launch_smm_decide(a, st, true);
 }
 
 }  // namespace geer

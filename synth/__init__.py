@@ -14,6 +14,8 @@ Workloads (graph seed 1, pair seed 2, walk seed 3):
   * ``workload("c5")``: Chung-Lu n=32M, mean degree 62.5 (~1B edges),
     exponent 2.3; 2,048 uniform pairs, eps 0.05 (drawn by the GPU generator
     of ``gpu_graphs`` when a GPU is present).
+  * ``workload("c2e")``: the c2 graph; 1,000 edges drawn uniformly from E
+    (the paper's edge-query workload, Section 5.1), eps 0.05.
 """
 from __future__ import annotations
 
@@ -72,10 +74,11 @@ def _graph(name: str, scale: float = 1.0) -> CSRGraph:
 
 def workload(name: str, scale: float = 1.0, q: int | None = None) -> Workload:
     """Build (or load from the cache directory $GEER_SYNTH_CACHE) a workload."""
-    cache = os.environ.get("GEER_SYNTH_CACHE") if name != "c5" else None  # c5's CSR is ~8 GB
+    gname = "c2" if name == "c2e" else name  # the edge queries run on the c2 graph
+    cache = os.environ.get("GEER_SYNTH_CACHE") if gname != "c5" else None  # c5's CSR is ~8 GB
     path = None
     if cache:
-        path = os.path.join(cache, f"{name}_{scale:g}.npz")
+        path = os.path.join(cache, f"{gname}_{scale:g}.npz")
         if os.path.exists(path):
             z = np.load(path)
             g = CSRGraph(z["row_ptr"], z["col_idx"], str(z["gname"]))
@@ -84,7 +87,7 @@ def workload(name: str, scale: float = 1.0, q: int | None = None) -> Workload:
     else:
         g = None
     if g is None:
-        g = _graph(name, scale)
+        g = _graph(gname, scale)
         if path:
             os.makedirs(cache, exist_ok=True)
             np.savez(path, row_ptr=g.row_ptr, col_idx=g.col_idx, gname=g.name)
@@ -93,6 +96,9 @@ def workload(name: str, scale: float = 1.0, q: int | None = None) -> Workload:
         eps = np.full(s.shape[0], 0.1)
     elif name == "c3":
         s, t, eps = pairs.bucketed_pairs(g, q or 8192, PAIR_SEED)
+    elif name == "c2e":
+        s, t = pairs.edge_pairs(g, q or 1000, PAIR_SEED)
+        eps = np.full(s.shape[0], 0.05)
     else:
         qq = {"c2": 1000, "c4": 4096, "c5": 2048}[name]
         s, t = pairs.uniform_pairs(g.n, q or qq, PAIR_SEED)

@@ -97,3 +97,14 @@ def test_cost_log_jsonl_round_trip(tmp_path):
     open(p, "w").write(json.dumps({"format": "other"}) + "\n")
     with pytest.raises(ValueError):
         switch.load_cost_log(p)
+
+
+def test_edge_pairs_are_edges():
+    from synth import graphs, pairs
+    g = graphs.random_connected(200, 400, 3)
+    s, t = pairs.edge_pairs(g, 500, 2)
+    s2, t2 = pairs.edge_pairs(g, 500, 2)
+    assert np.array_equal(s, s2) and np.array_equal(t, t2)
+    assert np.all(s < t)
+    for a, b in zip(s, t):
+        assert b in g.col_idx[g.row_ptr[a]:g.row_ptr[a + 1]]

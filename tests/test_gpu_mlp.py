@@ -157,6 +157,65 @@ def test_learned_switch_gains_over_the_rule(rmat_model):
     # the best switch point in hindsight bounds what any policy can reach
     best = np.nanmin(log.cost[:, 1:], axis=1)[ok].sum()
     assert best <= learned
+    # a constant switch point l_b = c (the same for every query): the best of
+    # c = 1..4 is the baseline a per-query policy has to beat (reported)
+    const = {}
+    for c in (1, 2, 3, 4):
+        o = geer.default_options(switch_policy=geer.GER_SWITCH_FIXED, fixed_ell_b=c)
+        const[c] = switch.batch_seconds(G, s, t, 0.05, o, repeats=9)
+    c_best = min(const, key=const.get)
+    print("constant l_b: " + ", ".join(f"{c}: {v * 1e3:.3f} ms" for c, v in const.items()) +
+          f"; learned {res['mlp']['seconds'] * 1e3:.3f} ms ({const[c_best] / res['mlp']['seconds']:.3f}x the best "
+          f"constant, l_b = {c_best})")
+    # the modelled cost of the best constant against the network's, on the cost log
+    c_cost = np.nansum(log.cost[:, c_best][ok])
+    print(f"modelled cost: learned {learned:.4g}, best constant {c_cost:.4g}, rule {rule:.4g}")
+
+
+def test_in_loop_decisions_match_the_network_oracle(rmat_model):
+    # The switch point the GPU takes under the learned policy is the first SMM
+    # iteration j < l at which the FP64 network oracle, fed the same raw inputs
+    # (the cost log of a fixed-policy run of the same queries: the same state
+    # after each iteration) normalised the same way, outputs >= 0; l if none.
+    # Rows whose output lies within 1e-4 of 0 (FP32 against FP64 rounding) are
+    # not judged.
+    g, G, lam, model, _, _ = rmat_model
+    assert model is not None
+    q, steps = 512, 8
+    s, t = pairs.uniform_pairs(g.n, q, 23)
+    eps = np.full(q, 0.05)
+    log, st_tr = G.smm_trace(s, t, eps, geer.default_options(), max_steps=steps)
+    G.set_switch_mlp(model.norm, model.weights)
+    try:
+        _, st = G.query(s, t, eps, geer.default_options(switch_policy=geer.GER_SWITCH_MLP), stats=True)
+    finally:
+        G.set_switch_mlp(None, None)
+    theta = model.weights.view(np.float16).astype(np.float64)
+    mean, std = model.norm[:6], model.norm[6:]
+    judged = stops_before_l = 0
+    for i in range(q):
+        ell = int(st_tr["ell"][i])
+        assert int(st["ell"][i]) == ell
+        expect, ambiguous = None, False
+        for j in range(1, min(ell, steps + 1)):
+            x = ((log[i, j - 1, :6] - mean) / std).astype(np.float32)
+            y = float(omlp.forward(theta, x.astype(np.float64)[None, :])[0][0])
+            if abs(y) < 1e-4:
+                ambiguous = True
+                break
+            if y >= 0:
+                expect = j
+                break
+        if ambiguous or (expect is None and ell > steps):
+            continue
+        if expect is None:
+            expect = ell
+        else:
+            stops_before_l += expect < ell
+        judged += 1
+        assert int(st["ell_b"][i]) == expect, (i, int(st["ell_b"][i]), expect, ell)
+    assert judged >= 0.9 * q
+    print(f"{judged} of {q} switch points judged; {stops_before_l} stop before l")
 
 
 def test_learned_switch_keeps_parity_and_eps(c1, rmat_model):

@@ -466,6 +466,39 @@ def test_c2_within_eps_of_reference(c2):
         assert abs(r[i] - ref) <= 0.05 + 1e-4
 
 
+def test_c2_edge_queries_parity_and_eps(c2):
+    # the paper's edge-query workload (Section 5.1): uniform edges of the same
+    # graph; adjacent pairs with r(u, v) <= 1 (Rayleigh: at most the hop distance)
+    w, g, G, lam = c2
+    we = synth.workload("c2e")
+    assert np.array_equal(we.graph.row_ptr, g.row_ptr) and np.array_equal(we.graph.col_idx, g.col_idx)
+    r, st = G.query(we.s, we.t, we.eps, _opts(), stats=True)
+    assert np.isfinite(r).all() and np.all(r <= 1.0 + we.eps)
+    rng = np.random.default_rng(4)
+    for i in sorted(rng.choice(we.q, 12, replace=False)):
+        ref = replay(g, we.s[i], we.t[i], we.eps[i], lam, st[i], i)
+        compare(r[i], st[i], ref, 1e-5, 1e-5)
+    d = g.degrees()
+    for i in range(4):
+        s, t = int(we.s[i]), int(we.t[i])
+        L = oracle.ell(d[s], d[t], 1e-4, lam)
+        assert abs(r[i] - oracle.smm_terms(g, s, t, L).sum()) <= 0.05 + 1e-4
+
+
+def test_c1_all_edges_within_eps_of_pseudo_inverse(c1, c1_pinv):
+    # every edge of the 4k-node graph (19,849 queries in one batch) against L^+
+    w, g, G, lam = c1
+    src = np.repeat(np.arange(g.n), g.degrees())
+    sel = src < g.col_idx
+    u, v = src[sel].astype(np.int32), g.col_idx[sel].astype(np.int32)
+    r = G.query(u, v, 0.1, _opts())
+    err = np.abs(r - exact.er_dense(g, u, v, c1_pinv))
+    m = u.shape[0]
+    # Definition 2 at delta = 0.01 per query, plus 3 binomial standard deviations
+    assert (err > 0.1).sum() <= 0.01 * m + 3 * math.sqrt(0.01 * m)
+    assert err.mean() < 0.1 / 3
+
+
 def test_c2_learned_switch_sampled_parity(c2):
     # the benchmark's configuration: a network trained on other pairs' cost logs
     from paper_2312_06123_gb300 import switch
