@@ -211,6 +211,68 @@ def replay_parity(w, lam, stats, seconds: float, threads: int, seed: int = 3):
     return res, time.perf_counter() - t0
 
 
+def deterministic_reference(w, lam, idx, threads: int):
+    """r(s,t) of the queries idx by the deterministic recipe of Section 5.1:
+    the oracle's SMM to l at eps = 1e-4 (the series of Eq. 3 truncated where
+    Theorem 1 puts its tail below 5e-5), on host threads."""
+    import concurrent.futures as cf
+    import oracle
+    d = w.graph.degrees()
+
+    def one(i):
+        s, t = int(w.s[i]), int(w.t[i])
+        L = oracle.ell(d[s], d[t], 1e-4, lam)
+        return float(oracle.smm_terms(w.graph, s, t, L).sum())
+
+    with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+        return np.array(list(ex.map(one, [int(i) for i in idx])))
+
+
+def sweep_legs(G, w, geer, base, flush_l2, lam, threads: int, sample: int = 8, reps: int = 3):
+    """The paper's parameter sweeps on this workload (Section 5.4): l_b around
+    the switch point l*_b Eq. (17) picks per query (Fig. 10; the hybrid engine
+    takes the deep SMM), and tau = 1..8 (Figs. 8-9; Eq. (17)'s rule). Each
+    point: median host-timed batch (L2 flushed before each call) and the
+    largest error against the deterministic reference on the first `sample`
+    queries."""
+    idx = np.arange(min(sample, w.q))
+    ref = deterministic_reference(w, lam, idx, threads)
+
+    def timed(call):
+        out = None
+        ts = []
+        for k in range(reps + 1):
+            flush_l2()
+            t0 = time.perf_counter()
+            out = call()
+            if k:
+                ts.append(time.perf_counter() - t0)
+        return float(np.median(ts)) * 1e3, out
+
+    rule = geer.default_options(**base)
+    _, st = G.query(w.s, w.t, w.eps, rule, stats=True)
+    lb_star = st["ell_b"].astype(np.int64)
+    hyb = dict(base)
+    hyb.setdefault("smm_engine", geer.GER_ENGINE_HYBRID)
+    hyb.setdefault("dense_switch", max(1, int(w.graph.row_ptr[-1]) // 64))
+    ho = geer.default_options(**hyb)
+    lb_pts = []
+    for k in (-6, -4, -2, 0, 2, 4, 6):
+        lb = np.clip(lb_star + k, 0, None).astype(np.int32)
+        ms, r = timed(lambda: G.query_lb(w.s, w.t, w.eps, lb, ho))
+        lb_pts.append({"offset": k, "batch_ms": ms, "mean_l_b": float(np.minimum(lb, st["ell"]).mean()),
+                       "max_err_vs_reference": float(np.abs(r[idx] - ref).max())})
+    tau_pts = []
+    for tau in range(1, 9):
+        o = geer.default_options(**{**base, "tau": tau})
+        ms, r = timed(lambda: G.query(w.s, w.t, w.eps, o))
+        tau_pts.append({"tau": tau, "batch_ms": ms, "max_err_vs_reference": float(np.abs(r[idx] - ref).max())})
+    return {"l_b_around_rule": lb_pts, "l_b_engine": "hybrid (pushes of nnz/64 pairs continue on the SpMM)",
+            "tau": tau_pts, "reference": f"oracle SMM to l at eps 1e-4 on the first {len(idx)} queries",
+            "eps": float(w.eps[0]) if np.all(w.eps == w.eps[0]) else "per query",
+            "timing": "host wall time of the host-buffer call, L2 flushed before each, median of 3"}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return 0
@@ -351,6 +413,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=10.0, help="oracle seconds per reference step")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle seconds for cpu_baseline")
     ap.add_argument("--plain-steps", type=int, default=2, help="timed steps of the plain FP64 per-query path")
+    ap.add_argument("--no-sweeps", action="store_true", help="skip the l_b and tau sweeps")
     ap.add_argument("--no-extras", action="store_true",
                     help="profiling runs: skip the e2e, plain-FP64 and CPU-baseline legs (timed region unchanged)")
     ap.add_argument("--case", choices=["spmm", "walk", "walk-fixed1"],
@@ -427,12 +490,15 @@ def main():
         torch.cuda.synchronize()
 
     # selection under the timed region's conditions (L2 flushed before each batch)
+    # prices: push pairs at 8..512 walk steps each; a per-iteration fixed cost of 0, 1e5
+    # or 1e6 walk steps per query (a batched SMM iteration's launches, shared by the
+    # queries that take it); the fastest measured policy is kept
     model, fit_times = switch.fit(G, s_tr, t_tr, eps0, clog, options=geer.default_options(**base),
-                                  before=flush_l2)
+                                  before=flush_l2, kappas=(8.0, 32.0, 128.0, 512.0), mus=(0.0, 1e5, 1e6))
     sw_seconds = time.perf_counter() - t_sw
     if model is not None:
         G.set_switch_mlp(model.norm, model.weights)
-        opts = geer.default_options(switch_policy=geer.GER_SWITCH_MLP, **base)
+        opts = model.options(geer.default_options(**base))
     else:
         opts = geer.default_options(**base)
     rule_opts = geer.default_options(**base)
@@ -516,6 +582,31 @@ def main():
             cms.append(a.elapsed_time(b))
         const_values[c] = world * w.q / (float(np.median(cms[3:])) / 1000.0)
 
+    # the autotuner (dense block width, hybrid switch size, tau) on the training
+    # pairs, then the same batch with its tau (options tau = 0): the paper's tau
+    # = 5 stays the headline setting; any tau keeps Theorem 2's guarantee
+    autotuned = None
+    if not args.no_extras:
+        eps_tr_arr = np.broadcast_to(np.asarray(eps_tr, np.float64), (len(s_tr),)).copy()
+        tune = G.autotune(s_tr, t_tr, eps_tr_arr, opts)
+        opts_t = geer.default_options(**{**{k: getattr(opts, k) for k, _ in geer.Options._fields_}, "tau": 0})
+        tms = []
+        for _ in range(3 + args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            G.query_dev(s_d, t_d, e_d, r_d, None, opts_t, stream=stream.cuda_stream)
+            b.record(stream)
+            b.synchronize()
+            tms.append(a.elapsed_time(b))
+        ms_t = float(np.median(tms[3:]))
+        autotuned = {"value": world * w.q / (ms_t / 1000.0), "unit": "queries/s", "ms_per_step": ms_t,
+                     "tau": tune["tau"], "tau_ms_on_training_pairs": tune["tau_ms"],
+                     "dense_width": tune["dense_width"], "dense_switch": tune["dense_switch"],
+                     "note": "ger_autotune on the training pairs; the timed batch as above with tau = 0"}
+
     # e2e: host buffers through ger_query_batch_eps, copies inside the timed region
     e2e_t = []
     if not args.no_extras:
@@ -570,6 +661,10 @@ def main():
         roof = {"kernel": fam[0], "bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s",
                 "frac": None, "peak_source": peak_kind, "traffic": None}
     spmm = None if args.no_extras else spmm_leg(G, w, geer, peak, workload=args.workload, base=base)
+    sweeps = None
+    # (the workloads whose deep SMM fits the sweep's few seconds)
+    if not args.no_extras and not args.no_sweeps and args.workload in ("c1", "c2", "c2e"):
+        sweeps = sweep_legs(G, w, geer, base, flush_l2, lam, max(1, os.cpu_count() or 1))
     # CPU baselines: the oracle as it stands on one host thread (the paper's
     # setting) and on every host core, bounded samples of the same queries
     cpu = cpu_n = parity = None
@@ -603,6 +698,8 @@ def main():
         "config": _config(w),
         "roofline": roof,
         "spmm": spmm,
+        "sweeps": sweeps,
+        "autotuned": autotuned,
         "cpu_baseline": cpu,
         "cpu_baseline_threads": cpu_n,
         "host": host,
@@ -615,7 +712,9 @@ def main():
             "value": plain_value, "unit": "queries/s", "ms_per_step": float(np.mean(pt)),
             "speedup_of_batched_fp32": value / world / plain_value},
         "switch": {"policy": "learned" if model is not None else "rule (no network beat it)",
-                   "kappa": None if model is None else model.kappa, "train_pairs": train_pairs,
+                   "kappa": None if model is None else model.kappa, "mu": None if model is None else model.mu,
+                   "decides_from_l_b_0": None if model is None else bool(model.at_start),
+                   "train_pairs": train_pairs,
                    "train_seed": TRAIN_SEED, "cost_log_rows": int(clog.feats.shape[0]),
                    "setup_seconds": sw_seconds,
                    "train_batch_ms": {k: v * 1e3 for k, v in fit_times.items()},

@@ -51,7 +51,8 @@ extern "C" {
 
 /* switch policy between SMM and AMC */
 #define GER_SWITCH_RULE  0  /* Eq. (17): stop SMM once the support volume exceeds h(l - l_b) */
-#define GER_SWITCH_MLP   1  /* the learned switch installed by ger_set_switch_mlp; Eq. (17) if none */
+#define GER_SWITCH_MLP   1  /* the learned switch installed by ger_set_switch_mlp (stops no later than
+                               Eq. (17)); Eq. (17) alone if none is installed */
 #define GER_SWITCH_FIXED 2  /* run exactly min(fixed_ell_b, l) SMM iterations; fixed_ell_b < 0 means l */
 
 /* engine of the SMM iterations */
@@ -68,7 +69,8 @@ typedef struct ger_graph ger_graph; /* opaque; owns the device copy of the graph
 
 typedef struct ger_options {
     double   delta;         /* failure probability delta (paper default 0.01) */
-    int32_t  tau;           /* maximum number of AMC batches tau (paper default 5), 1..20 */
+    int32_t  tau;           /* maximum number of AMC batches tau (paper default 5), 1..20;
+                               0: the graph's autotuned tau (ger_autotune), else 5 */
     int32_t  precision;     /* GER_FP32 (default) or GER_FP64 */
     int32_t  per_query;     /* 0: all queries of the batch together; 1: one query at a time */
     int32_t  switch_policy; /* GER_SWITCH_RULE (default), GER_SWITCH_MLP or GER_SWITCH_FIXED */
@@ -80,7 +82,8 @@ typedef struct ger_options {
     int32_t  dense_width;   /* dense engine: columns per block (2 per query); 0: autotuned per graph */
     int64_t  dense_switch;  /* hybrid engine: push pairs at which a query moves to the SpMM; 0: autotuned, else nnz / 16 */
     int32_t  dense_budget_mb; /* hybrid engine: device memory for dense columns (MiB); 0: half the free memory */
-    int32_t  reserved0;
+    int32_t  mlp_at_start;  /* GER_SWITCH_MLP: 1 also consults the network before the first SMM
+                               iteration (l_b = 0: AMC alone); 0 (default): after iterations only */
 } ger_options;
 
 /* Per-query statistics (all optional outputs). */
@@ -255,9 +258,13 @@ int ger_profile_read(ger_kernel_profile *out, int max_entries);
  *     queries on the dense engine at every width the precision allows;
  *  2. the hybrid engine's switch size: the whole batch at nnz/64, nnz/16,
  *     nnz/4, nnz push pairs and without moves.
+ *  3. tau, the number of AMC batches of Algorithm 1: the whole batch with the
+ *     caller's options at tau = 1..8 (Theorem 2's guarantee holds at delta /
+ *     tau for any tau, so the choice changes the walks drawn and the run
+ *     time, not the eps guarantee; Section 5.4 measures the same range).
  * The fastest of each is stored on g and used whenever an option leaves the
- * value at 0 (dense_width, dense_switch). out (nullable) receives the choices
- * and the median batch times.
+ * value at 0 (dense_width, dense_switch, tau). out (nullable) receives the
+ * choices and the median batch times.
  * Errors: as ger_query_batch_eps. */
 typedef struct ger_tuning {
     int32_t dense_width;            /* chosen block width (0: no dense engine on this graph) */
@@ -266,6 +273,8 @@ typedef struct ger_tuning {
     float   width_ms[3];            /* widths 32, 64, 128 (FP64: 32, 64) */
     float   switch_ms[5];
     int64_t switch_candidates[5];
+    int32_t tau;                    /* chosen tau (used by options with tau = 0) */
+    float   tau_ms[8];              /* median batch time at tau = 1..8 */
 } ger_tuning;
 
 int ger_autotune(ger_graph *g, int64_t q, const int32_t *s, const int32_t *t, const double *eps,
@@ -285,7 +294,14 @@ int ger_autotune(ger_graph *g, int64_t q, const int32_t *s, const int32_t *t, co
  * log(Eq. 17's volume), log h(l - l_b), max_1(s*)/d(s) + max_1(t*)/d(t).
  * Output: predicted log C(l_b + 1) - log C(l_b), C(j) being the query's
  * cost when it switches after j iterations; the query switches when the
- * output is >= 0 (and always once l_b = l).
+ * output is >= 0, when Eq. (17) says to switch (the network can stop a
+ * query earlier than the rule, never later, so its SMM work is bounded by
+ * the rule's), and always once l_b = l. The network is consulted where the
+ * rule continues: after each SMM iteration, and, with options.mlp_at_start,
+ * also before the first one (l_b = 0: AMC alone, Algorithm 1), with the
+ * inputs of s* = e_s, t* = e_t (log d(s), log d(t), l, log(d(s) + d(t)),
+ * log h(l), 1/d(s) + 1/d(t)). One thread per query evaluates it inside the
+ * decision kernels.
  * ------------------------------------------------------------------------ */
 #define GER_MLP_INPUTS 6
 #define GER_MLP_HIDDEN 64
@@ -298,6 +314,20 @@ int ger_autotune(ger_graph *g, int64_t q, const int32_t *s, const int32_t *t, co
  * it from the next call on.
  * Errors: GER_ERR_INVALID, GER_ERR_OOM, GER_ERR_CUDA. */
 int ger_set_switch_mlp(ger_graph *g, const float *norm, const uint16_t *weights);
+
+/*
+ * Algorithm 3 with the greedy switch of Eq. (17) replaced, per query, by a
+ * given number of SMM iterations: the experiment of Section 5.4 (Fig. 10)
+ * that varies l_b around the switch point l*_b Eq. (17) picks. Query i runs
+ * min(ell_b[i], l) SMM iterations (ell_b[i] = 0: AMC alone, Algorithm 1;
+ * ell_b[i] >= l: SMM alone, Algorithm 2), then AMC for the remaining
+ * l - l_b steps; ell_b[i] < 0 leaves query i to opt's switch policy. Theorem
+ * 2's eps guarantee holds for every l_b (the truncation length l is
+ * unchanged). Host pointers (ell_b: q int32); other arguments and errors as
+ * ger_query_batch_eps.
+ */
+int ger_query_batch_lb(ger_graph *g, int64_t q, const int32_t *s, const int32_t *t, const double *eps,
+                       const int32_t *ell_b, const ger_options *opt, double *r_out, ger_query_stats *stats);
 
 /* Cost log of the learned switch: runs the batch with min(max_steps, l)
  * SMM iterations (GER_SWITCH_FIXED; the other options are used as given)

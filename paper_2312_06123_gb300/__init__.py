@@ -43,7 +43,7 @@ class Options(ctypes.Structure):
                 ("fixed_ell_b", ctypes.c_int32), ("ell_formula", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("sparse_cap", ctypes.c_int64), ("smm_engine", ctypes.c_int32),
                 ("dense_width", ctypes.c_int32), ("dense_switch", ctypes.c_int64), ("dense_budget_mb", ctypes.c_int32),
-                ("reserved0", ctypes.c_int32)]
+                ("mlp_at_start", ctypes.c_int32)]
 
 
 class QueryStats(ctypes.Structure):
@@ -63,7 +63,8 @@ class MlpTrainOptions(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("dense_width", ctypes.c_int32), ("reserved", ctypes.c_int32), ("dense_switch", ctypes.c_int64),
                 ("width_ms", ctypes.c_float * 3), ("switch_ms", ctypes.c_float * 5),
-                ("switch_candidates", ctypes.c_int64 * 5)]
+                ("switch_candidates", ctypes.c_int64 * 5), ("tau", ctypes.c_int32),
+                ("tau_ms", ctypes.c_float * 8)]
 
 
 class KernelProfile(ctypes.Structure):
@@ -119,6 +120,7 @@ def load_library(build_if_missing: bool = True):
     L.ger_set_switch_mlp.argtypes = [_P, _P, _P]
     L.ger_autotune.argtypes = [_P, i64, _P, _P, _P, ctypes.POINTER(Options), ctypes.POINTER(Tuning)]
     L.ger_smm_trace.argtypes = [_P, i64, _P, _P, _P, ctypes.POINTER(Options), i32, _P, _P]
+    L.ger_query_batch_lb.argtypes = [_P, i64, _P, _P, _P, _P, ctypes.POINTER(Options), _P, _P]
     L.ger_mlp_forward.argtypes = [i64, _P, _P, _P]
     L.ger_mlp_gradient.argtypes = [i64, _P, _P, _P, _P, _P]
     L.ger_default_mlp_train_options.argtypes = [ctypes.POINTER(MlpTrainOptions)]
@@ -128,7 +130,7 @@ def load_library(build_if_missing: bool = True):
                  "ger_spectral_bound_info",
                  "ger_query_batch", "ger_query_batch_eps", "ger_query_batch_dev",
                  "ger_query_batch_dev_noalloc", "ger_set_switch_mlp", "ger_smm_trace", "ger_mlp_forward",
-                 "ger_mlp_gradient", "ger_mlp_train", "ger_autotune"):
+                 "ger_mlp_gradient", "ger_mlp_train", "ger_autotune", "ger_query_batch_lb"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -406,7 +408,26 @@ class Graph:
                                            e.ctypes.data_as(_P), ctypes.byref(opt), ctypes.byref(res)))
         return {"dense_width": res.dense_width, "dense_switch": int(res.dense_switch),
                 "width_ms": list(res.width_ms), "switch_ms": list(res.switch_ms),
-                "switch_candidates": [int(x) for x in res.switch_candidates]}
+                "switch_candidates": [int(x) for x in res.switch_candidates], "tau": int(res.tau),
+                "tau_ms": list(res.tau_ms)}
+
+    def query_lb(self, s, t, eps, ell_b, options: Options | None = None, stats: bool = False):
+        """r'(s,t) with query i running min(ell_b[i], l) SMM iterations in
+        place of Eq. (17)'s switch (ger_query_batch_lb; ell_b[i] < 0: the
+        options' policy). Returns r or (r, stats)."""
+        L = load_library()
+        s = _arr(s, np.int32)
+        t = _arr(t, np.int32)
+        q = s.shape[0]
+        e = _arr(np.broadcast_to(eps, (q,)), np.float64)
+        lb = _arr(np.broadcast_to(ell_b, (q,)), np.int32)
+        r = np.zeros(q, dtype=np.float64)
+        st = np.zeros(q, dtype=STATS_DTYPE) if stats else None
+        opt = options if options is not None else default_options()
+        _check(L.ger_query_batch_lb(self._h, q, s.ctypes.data_as(_P), t.ctypes.data_as(_P), e.ctypes.data_as(_P),
+                                    lb.ctypes.data_as(_P), ctypes.byref(opt), r.ctypes.data_as(_P),
+                                    st.ctypes.data_as(_P) if st is not None else None))
+        return (r, st) if stats else r
 
     def smm_trace(self, s, t, eps, options: Options | None = None, max_steps: int = 16):
         """Cost log: (log[q][max_steps][LOG_WIDTH], stats) of a batch run

@@ -194,7 +194,7 @@ __device__ __forceinline__ double resolve_g(const GEntry* tab, int32_t mask, int
 // batch0 + nbatch - 1 (eta pairs in batch0, doubling), chunked by chunk_layout at
 // kMaxChunksPerQuery / nbatch chunks per batch. Returns the chunk's sums of
 // Z_k, Z_k^2 and the walk checksum, reduced over the warp.
-template <int W, bool REC>
+template <int W, bool REC, int K>
 __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, int64_t L, int64_t eta, int batch0,
                                            int nbatch, int lane, double* out_sz, double* out_sz2, uint64_t* out_cs) {
     const int sigma = lane & 1;
@@ -299,7 +299,10 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
                         r[i] = philox4x32_10(
                             make_uint4((uint32_t)k[i], lane_ctr, (uint32_t)qidx, (uint32_t)((j - 1) >> 2)), key);
                     const uint32_t d = sub == 0 ? r[i].x : (sub == 1 ? r[i].y : (sub == 2 ? r[i].z : r[i].w));
-                    nx[i] = act[i] ? __ldg(row_base(g, w[i], inf[i]) + __umulhi(d, inf[i].y)) : start;
+                    if (K > 0)  // packed neighbour lists: entry first edge + pick
+                        nx[i] = act[i] ? packed_col<K>(g.cols_packed, inf[i].x + __umulhi(d, inf[i].y)) : start;
+                    else
+                        nx[i] = act[i] ? __ldg(row_base(g, w[i], inf[i]) + __umulhi(d, inf[i].y)) : start;
                 }
                 // next row records and first probes (or dense values), all independent
                 if (mask >= 0) {
@@ -359,52 +362,130 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
 
 // Launch-per-batch walks: a persistent grid whose warps take chunks of the
 // launch's layout (chunk_begin) from a ticket counter.
-template <int W, bool REC>
+template <int W, bool REC, int K>
 __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a) {
     __shared__ int32_t cbeg[kSmemChunkBegin];
+    __shared__ int32_t perm[kSmemChunkBegin];  // layout position -> query (ordered layouts)
+    __shared__ int32_t coff[kAmcClasses + 1];
     __shared__ int64_t scan[kWarps + 1];
+    __shared__ unsigned long long s_steps;
     // batches of this launch: the first launch walks *a.group batches, the
     // launches of batches it covered have nothing to do
-    const int group = *a.group;
+    int group;
+    const bool fused = a.batch == 1 && a.fused_schedule;
+    if (fused) {
+        // the first launch lays out its own chunks: batches 1..kAmcGroup walk
+        // together when their walk steps (had no query stopped) stay below
+        // kAmcGroupSteps (each CTA decides the same from the walk records)
+        const int nb = a.tau < kAmcGroup ? a.tau : kAmcGroup;
+        if (threadIdx.x == 0) s_steps = 0ull;
+        __syncthreads();
+        unsigned long long mine = 0ull;
+        for (int64_t q = threadIdx.x; q < a.nq; q += blockDim.x) {
+            const WalkQ* wr = a.wq + q;
+            const int64_t eta = wr->eta;  // 0 unless the query is in AMC
+            if (eta > 0) mine += (unsigned long long)(((1ll << nb) - 1) * eta * 2 * (int64_t)wr->lf);
+        }
+        mine = warp_sum(mine);
+        if ((threadIdx.x & 31) == 0) atomicAdd(&s_steps, mine);
+        __syncthreads();
+        group = s_steps <= (unsigned long long)kAmcGroupSteps ? nb : 1;
+        if (blockIdx.x == 0 && threadIdx.x == 0) *a.group = group;
+    } else {
+        group = *a.group;
+    }
     if (a.batch > 1 && a.batch <= group) return;
     const int nbatch = a.batch == 1 ? group : 1;
-    // chunk prefix over the queries: built here from the per-query counts
-    // (small batches), else laid out by the schedule
+    // chunk prefix over the layout's positions: built here from the per-query
+    // counts (small batches), else laid out by the schedule. Small batches
+    // place the queries in AMC longest walks first (their walk-length class
+    // lists), so that the launch's last chunks are short ones.
     const bool staged = a.nq + 1 <= kSmemChunkBegin;
+    const bool ordered = staged && a.amc_list != nullptr;
+    int npos = a.nq;
+    if (ordered) {
+        if (threadIdx.x == 0) {
+            int o = 0;
+            for (int c = 0; c < kAmcClasses; ++c) {
+                coff[c] = o;
+                o += a.class_cnt[c];
+            }
+            coff[kAmcClasses] = o;
+        }
+        __syncthreads();
+        npos = coff[kAmcClasses];
+        for (int p = threadIdx.x; p < npos; p += blockDim.x) {
+            int c = 0;
+            while (p >= coff[c + 1]) ++c;
+            perm[p] = a.amc_list[c * a.amc_stride + (p - coff[c])];
+        }
+        __syncthreads();
+    }
+    auto query_at = [&](int p) -> int { return ordered ? perm[p] : p; };
     if (staged) {
+        const int64_t maxc = kMaxChunksPerQuery / nbatch;
+        if (fused && ordered && blockIdx.x == 0) {
+            // queries outside AMC have no chunks in any launch of this phase
+            for (int q = threadIdx.x; q < a.nq; q += blockDim.x) a.chunk_count[q] = 0;
+            __syncthreads();
+        }
         int64_t carry = 0;
-        for (int64_t tile = 0; tile < a.nq; tile += kCta) {
-            const int64_t q = tile + threadIdx.x;
+        for (int64_t tile = 0; tile < npos; tile += kCta) {
+            const int64_t p = tile + threadIdx.x;
+            int64_t cnt = 0;
+            if (p < npos) {
+                const int q = query_at((int)p);
+                if (fused) {
+                    const int64_t eta = a.wq[q].eta;
+                    for (int i = 0; eta > 0 && i < nbatch; ++i) {
+                        int64_t ppc, n;
+                        chunk_layout(eta << i, maxc, &ppc, &n);
+                        cnt += n;
+                    }
+                    // every query's count, zeros included: the statistics launches
+                    // update only the queries still in AMC, and later walk launches
+                    // build their prefix from these counts
+                    if (blockIdx.x == 0) a.chunk_count[q] = (int32_t)cnt;
+                } else {
+                    cnt = a.chunk_count[q];
+                }
+            }
             int64_t tot;
-            const int64_t ex = cta_excl_scan(q < a.nq ? (int64_t)a.chunk_count[q] : 0, scan, &tot);
-            if (q < a.nq) cbeg[q] = (int32_t)(carry + ex);
+            const int64_t ex = cta_excl_scan(cnt, scan, &tot);
+            if (p < npos) cbeg[p] = (int32_t)(carry + ex);
             carry += tot;
         }
-        if (threadIdx.x == 0) cbeg[a.nq] = (int32_t)carry;
+        if (threadIdx.x == 0) cbeg[npos] = (int32_t)carry;
         __syncthreads();
-        if (blockIdx.x == 0)  // for the statistics launch that follows
-            for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) a.chunk_begin[i] = cbeg[i];
+        if (blockIdx.x == 0) {  // each query's first chunk, for the statistics launch that follows
+            for (int p = threadIdx.x; p < npos; p += blockDim.x) a.chunk_begin[query_at(p)] = cbeg[p];
+            if (threadIdx.x == 0) a.chunk_begin[a.nq] = cbeg[npos];
+        }
     }
     const int64_t* cb_glob = a.chunk_begin;
     auto cb_arr = [&](int i) -> int64_t { return staged ? (int64_t)cbeg[i] : cb_glob[i]; };
     const int lane = threadIdx.x & 31;
-    const int64_t total = cb_arr(a.nq);
+    const int64_t total = cb_arr(npos);
+    if (total > a.partial_cap) {  // cannot happen with a valid layout; never write past the partials
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(a.err_flag, 0, DERR_CHUNKS);
+        return;
+    }
     for (;;) {
         // chunks are handed out in order by a ticket counter
         unsigned long long ticket = 0;
         if (lane == 0) ticket = atomicAdd(a.walk_ctr, 1ull);
         const int64_t c = (int64_t)__shfl_sync(0xffffffffu, ticket, 0);
         if (c >= total) break;
-        // owning query: last q with chunk_begin[q] <= c
-        int lo = 0, hi = a.nq + 1;
+        // owning position: last p with cbeg[p] <= c
+        int lo = 0, hi = npos + 1;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
             if (cb_arr(mid) <= c) lo = mid + 1; else hi = mid;
         }
-        const WalkQ* WQ = a.wq + (lo - 1);
+        const WalkQ* WQ = a.wq + query_at(lo - 1);
         double sz, sz2;
         uint64_t cs;
-        walk_chunk<W, REC>(a, WQ, c - cb_arr(lo - 1), WQ->eta, a.batch, nbatch, lane, &sz, &sz2, &cs);
+        walk_chunk<W, REC, K>(a, WQ, c - cb_arr(lo - 1), WQ->eta, a.batch, nbatch, lane, &sz, &sz2, &cs);
         if (lane == 0) {
             Partial p;
             p.sz = sz;
@@ -453,11 +534,20 @@ __global__ void __launch_bounds__(kCta) amc_reduce_kernel(AmcArgs a) {
     __shared__ unsigned long long s_cs[kAmcGroup][kReduceQ];
     __shared__ bool last;
     const int group = *a.group;
-    if (a.batch > 1 && a.batch <= group) return;  // walked and evaluated with batch 1
-    const int nbatch = a.batch == 1 ? group : 1;
-    const int64_t maxc = kMaxChunksPerQuery / nbatch;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t q0 = (int64_t)blockIdx.x * kReduceQ;
+    // every walk launch of this AMC phase is done: the class lists start empty for the next
+    if (a.class_cnt && a.batch == a.tau && blockIdx.x == 0 && threadIdx.x < kAmcClasses)
+        a.class_cnt[threadIdx.x] = 0;
+    // the last launch writes every query's outputs (warp 0, one query per lane)
+    const bool outputs = a.out_r != nullptr && a.batch == a.tau;
+    if (a.batch > 1 && a.batch <= group) {  // walked and evaluated with batch 1
+        if (outputs && warp == 0 && lane < kReduceQ && q0 + lane < a.nq)
+            store_outputs(a.st[q0 + lane], q0 + lane, a.out_r, a.out_stats);
+        return;
+    }
+    const int nbatch = a.batch == 1 ? group : 1;
+    const int64_t maxc = kMaxChunksPerQuery / nbatch;
     const bool staged = a.nq + 1 <= kSmemChunkBegin;
     // the batches' sums, one query per warp at a time
     for (int j = warp; j < kReduceQ; j += kWarps) {
@@ -527,13 +617,17 @@ __global__ void __launch_bounds__(kCta) amc_reduce_kernel(AmcArgs a) {
                 a.chunk_count[q] = nch;
             }
         }
+        if (outputs && q < a.nq) store_outputs(*Q, q, a.out_r, a.out_stats);
     }
     const int next = a.batch + nbatch;
-    if (next > a.tau) return;  // no next batch to lay out
-    if (staged) {  // each walk CTA builds the prefix; only the ticket counter is reset here
+    if (staged) {
+        // each walk CTA builds the prefix; only the ticket counter is reset here,
+        // after the last batch too: the next AMC phase on the same workspace (the
+        // next query of a one-query-at-a-time batch) starts from ticket 0
         if (blockIdx.x == 0 && threadIdx.x == 0) *a.walk_ctr = 0ull;
         return;
     }
+    if (next > a.tau) return;  // no next batch to lay out
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(a.done, 1u) == gridDim.x - 1;
@@ -558,6 +652,32 @@ __global__ void edge_records_kernel(const int32_t* col_idx, const uint2* node_in
     }
 }
 
+// unit u of the packed neighbour lists: entries u*k .. u*k + k - 1 of col_idx,
+// entry j at bits [j * B, j * B + B) of the 128-bit unit (B = pack_bits(k))
+__global__ void pack_cols_kernel(const int32_t* col_idx, int64_t nnz, int k, uint4* out) {
+    const int B = pack_bits(k);
+    const int64_t units = (nnz + k - 1) / k;
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < units; u += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t w[5] = {0u, 0u, 0u, 0u, 0u};
+        for (int j = 0; j < k; ++j) {
+            const int64_t e = u * k + j;
+            if (e >= nnz) break;
+            const uint32_t v = (uint32_t)col_idx[e];
+            const int o = j * B, wi = o >> 5, sh = o & 31;
+            w[wi] |= v << sh;
+            if (sh + B > 32) w[wi + 1] |= v >> (32 - sh);
+        }
+        out[u] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+void launch_pack_cols(const int32_t* col_idx, int64_t nnz, int k, uint4* out, cudaStream_t st) {
+    const int64_t units = (nnz + k - 1) / k;
+    if (units <= 0) return;
+    pack_cols_kernel<<<(int)std::min<int64_t>((units + 255) / 256, 152 * 32), 256, 0, st>>>(col_idx, nnz, k, out);
+    note_launches(1);
+}
+
 void launch_edge_records(const int32_t* col_idx, const uint2* node_info, int64_t nnz, uint4* out, cudaStream_t st) {
     if (nnz <= 0) return;
     edge_records_kernel<<<(int)std::min<int64_t>((nnz + 255) / 256, 152 * 32), 256, 0, st>>>(col_idx, node_info, nnz,
@@ -565,23 +685,31 @@ void launch_edge_records(const int32_t* col_idx, const uint2* node_info, int64_t
     note_launches(1);
 }
 
-void launch_amc_walk(const AmcArgs& a, int sm_count, cudaStream_t st) {
-    static int per_sm[2] = {0, 0};  // resident CTAs per SM of the two walk kernels
-    const bool rec = a.g.edge_rec != nullptr;
-    if (per_sm[rec] == 0) {
+// One walk kernel per neighbour-list layout: edge records, or col_idx
+// packed k to a 16-byte unit (k = 8, 6, 5), or plain col_idx.
+template <bool REC, int K>
+static void launch_walk_variant(const AmcArgs& a, int sm_count, cudaStream_t st) {
+    static int per_sm = 0;  // resident CTAs per SM
+    if (per_sm == 0) {
         int b = 0;
-        const cudaError_t e =
-            rec ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, amc_walk_kernel<kWalksPerLane, true>, 256, 0)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, amc_walk_kernel<kWalksPerLane, false>, 256, 0);
-        if (e != cudaSuccess || b < 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, amc_walk_kernel<kWalksPerLane, REC, K>, 256, 0) !=
+                cudaSuccess ||
+            b < 1) {
             cudaGetLastError();
             b = 1;
         }
-        per_sm[rec] = b;
+        per_sm = b;
     }
+    amc_walk_kernel<kWalksPerLane, REC, K><<<sm_count * per_sm, 256, 0, st>>>(a);
+}
+
+void launch_amc_walk(const AmcArgs& a, int sm_count, cudaStream_t st) {
     prof_begin(FAM_AMC_WALK, st);
-    if (rec) amc_walk_kernel<kWalksPerLane, true><<<sm_count * per_sm[1], 256, 0, st>>>(a);
-    else amc_walk_kernel<kWalksPerLane, false><<<sm_count * per_sm[0], 256, 0, st>>>(a);
+    if (a.g.edge_rec) launch_walk_variant<true, 0>(a, sm_count, st);
+    else if (a.g.cols_packed && a.g.pack_k == 8) launch_walk_variant<false, 8>(a, sm_count, st);
+    else if (a.g.cols_packed && a.g.pack_k == 6) launch_walk_variant<false, 6>(a, sm_count, st);
+    else if (a.g.cols_packed && a.g.pack_k == 5) launch_walk_variant<false, 5>(a, sm_count, st);
+    else launch_walk_variant<false, 0>(a, sm_count, st);
     prof_end(FAM_AMC_WALK, st);
 }
 

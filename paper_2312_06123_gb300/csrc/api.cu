@@ -37,7 +37,7 @@ void note_launches(int k) {
 static const char* kFamilyNames[] = {"smm_setup", "smm_advance", "smm_push",
                                               "smm_push_heavy", "smm_finish", "smm_top2", "smm_decide", "dense_spmm",
                                               "amc_schedule", "amc_walk", "amc_reduce", "finalize", "lanczos",
-                                     "smm_mlp", "mlp_train"};
+                                     "mlp_train"};
 static_assert(sizeof(kFamilyNames) / sizeof(kFamilyNames[0]) == FAM_COUNT, "one name per kernel family");
 struct ProfRec {
     int fam;
@@ -144,6 +144,8 @@ struct Workspace {
     ger_query_stats* stats = nullptr;
     int64_t* chunk_begin = nullptr;
     int32_t* chunk_count = nullptr;
+    int32_t* lbf = nullptr;       // per-query forced SMM lengths (ger_query_batch_lb)
+    int32_t* amc_list = nullptr;  // kAmcClasses lists of q_cap queries (walk-length classes)
     WalkQ* wq = nullptr;
     Partial* partial = nullptr;
     int64_t partial_cap = 0;
@@ -199,6 +201,7 @@ struct BatchGraph {
     const void* dense_dev = nullptr;  // dense column map and move list the capture uses
     const void* mig = nullptr;
     uint64_t gen = 0;                 // workspace generation the capture saw
+    bool forced = false;              // captured with per-query SMM lengths
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<ProfRec> prof_recs;
@@ -213,6 +216,8 @@ struct ger_graph {
     int32_t* col_idx = nullptr;
     uint2* node_info = nullptr;  // {first edge, degree} per node when nnz < 2^32
     uint4* edge_rec = nullptr;   // {neighbour, its first edge, its degree, 0} per edge (walks)
+    uint4* cols_packed = nullptr; // the walks' packed copy of col_idx (pack_k entries per 16 B)
+    int pack_k = 0;
     bool has_lambda = false;
     double lambda = 0, lam2 = 0, lamn = 0;
     // how lambda was obtained: Lanczos steps (0: set by the caller), whether
@@ -223,6 +228,7 @@ struct ger_graph {
     cudaStream_t stream2 = nullptr;  // captures the SMM while body
     int dense_tuned[2] = {0, 0};     // autotuned dense block width (FP32, FP64), 0: not tuned
     int64_t hybrid_tuned = 0;        // autotuned hybrid switch size (push pairs), 0: not tuned
+    int tau_tuned = 0;               // autotuned tau (AMC batches), 0: not tuned
     int dense_ctas = 0;              // dense SpMM CTAs per SM and block, 0: default
     int4* dense_units = nullptr;     // dense SpMM work units (null when nnz >= 2^32)
     int4* dense_heavy = nullptr;     // dense SpMM heavy rows
@@ -236,10 +242,18 @@ struct ger_graph {
 
 namespace geer {
 
+// The device view of a loaded graph.
+static DevGraph dev_graph(const ger_graph* g) {
+    DevGraph d{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info, g->edge_rec};
+    d.cols_packed = g->cols_packed;
+    d.pack_k = g->cols_packed ? g->pack_k : 0;
+    return d;
+}
+
 static void free_ws(Workspace& w) {
     cudaFree(w.st); cudaFree(w.s); cudaFree(w.t); cudaFree(w.eps); cudaFree(w.r); cudaFree(w.stats);
     cudaFree(w.chunk_begin); cudaFree(w.partial); cudaFree(w.qsmm);
-    cudaFree(w.wq); cudaFree(w.chunk_count);
+    cudaFree(w.wq); cudaFree(w.chunk_count); cudaFree(w.lbf); cudaFree(w.amc_list);
     cudaFree(w.ctl); cudaFree(w.ent); cudaFree(w.sums); cudaFree(w.yvals); cudaFree(w.counters);
     cudaFree(w.heavy);
     cudaFree(w.dX[0]); cudaFree(w.dX[1]);
@@ -276,7 +290,9 @@ static int ensure_ws(ger_graph* g, int64_t q, int64_t pool_cap) {
     if (q > w.q_cap) {
         cudaFree(w.st); cudaFree(w.s); cudaFree(w.t); cudaFree(w.eps); cudaFree(w.r); cudaFree(w.stats);
         cudaFree(w.chunk_begin); cudaFree(w.partial); cudaFree(w.qsmm);
-        cudaFree(w.wq); cudaFree(w.chunk_count);
+        cudaFree(w.wq); cudaFree(w.chunk_count); cudaFree(w.lbf); cudaFree(w.amc_list);
+        w.lbf = nullptr;
+        w.amc_list = nullptr;
         w.st = nullptr; w.s = nullptr; w.t = nullptr; w.eps = nullptr; w.r = nullptr; w.stats = nullptr;
         w.chunk_begin = nullptr; w.partial = nullptr; w.qsmm = nullptr;
         w.wq = nullptr; w.chunk_count = nullptr;
@@ -286,7 +302,7 @@ static int ensure_ws(ger_graph* g, int64_t q, int64_t pool_cap) {
         if (alloc(&w.st, qc) || alloc(&w.s, qc) || alloc(&w.t, qc) || alloc(&w.eps, qc) || alloc(&w.r, qc) ||
             alloc(&w.stats, qc) || alloc(&w.chunk_begin, qc + 1) || alloc(&w.partial, pc) ||
             alloc(&w.qsmm, qc) || alloc(&w.wq, qc) ||
-            alloc(&w.chunk_count, qc)) {
+            alloc(&w.chunk_count, qc) || alloc(&w.lbf, qc) || alloc(&w.amc_list, kAmcClasses * qc)) {
             cudaGetLastError();
             return fail(GER_ERR_OOM, "workspace for %lld queries", (long long)q);
         }
@@ -311,28 +327,8 @@ static int ensure_ws(ger_graph* g, int64_t q, int64_t pool_cap) {
 // outputs
 // ---------------------------------------------------------------------------
 __global__ void finalize_kernel(const QState* st, int64_t nq, double* r, ger_query_stats* stats) {
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x) {
-        const QState& Q = st[q];
-        r[q] = Q.r;
-        if (stats) {
-            ger_query_stats o;
-            o.ell = Q.ell;
-            o.ell_b = Q.ell_b;
-            o.batches = Q.batch;
-            o.flags = Q.err;
-            o.eta0 = Q.eta0;
-            o.walks = Q.walks;
-            o.walk_steps = Q.walk_steps;
-            o.r_b = Q.r_b;
-            o.r_f = Q.r_f;
-            o.psi = Q.psi;
-            o.f_last = Q.f_last;
-            o.volume = Q.volume;
-            o.h = Q.h;
-            o.checksum = Q.checksum;
-            stats[q] = o;
-        }
-    }
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq; q += (int64_t)gridDim.x * blockDim.x)
+        store_outputs(st[q], q, r, stats);
 }
 
 // ---------------------------------------------------------------------------
@@ -396,7 +392,7 @@ static int validate_csr(int64_t n, const int64_t* rp, const int32_t* ci) {
 
 static int ensure_lambda(ger_graph* g) {
     if (g->has_lambda) return GER_OK;
-    DevGraph dg{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info, g->edge_rec};
+    DevGraph dg = dev_graph(g);
     double l2 = 0, ln = 0;
     int steps = 0;
     LanczosInfo info;
@@ -438,6 +434,7 @@ struct Plan {
     cudaStream_t st;
     float* trace = nullptr;  // device cost log (stream-ordered runs only), nullable
     int32_t trace_steps = 0;
+    const int32_t* lb_force = nullptr;  // device per-query SMM lengths, nullable
 };
 
 
@@ -448,6 +445,7 @@ static int map_device_error(int e) {
         case DERR_TABLE: return fail(GER_ERR_CAPACITY, "frontier-table pool exhausted");
         case DERR_ELL: return fail(GER_ERR_INVALID, "truncation length undefined (lambda >= 1)");
         case DERR_FULL: return fail(GER_ERR_CAPACITY, "a frontier table ran out of free slots (load factor broken)");
+        case DERR_CHUNKS: return fail(GER_ERR_CUDA, "a walk launch's chunk layout exceeded the partial-sum array");
         default: return fail(GER_ERR_CUDA, "device error %d", e);
     }
 }
@@ -553,7 +551,7 @@ static int ensure_dense(ger_graph* g, int64_t nq, int width, bool fp64) {
 static DenseArgs make_dense_args(ger_graph* g, int64_t q0, int64_t nq, int width, bool fp64) {
     Workspace& w = g->ws;
     DenseArgs d;
-    d.g = DevGraph{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info, g->edge_rec};
+    d.g = dev_graph(g);
     d.width = width;
     d.nblocks = (int32_t)((nq + width / 2 - 1) / (width / 2));
     d.X[0] = w.dX[0];
@@ -593,7 +591,7 @@ static void issue_dense_start(ger_graph* g, const DenseArgs& d, bool fp64, int64
 // Launch arguments of the SMM and AMC phases for queries [q0, q0 + nq).
 static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool fp64, SmmArgs* pa, AmcArgs* pm) {
     Workspace& w = g->ws;
-    DevGraph dg{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info, g->edge_rec};
+    DevGraph dg = dev_graph(g);
     SmmArgs& a = *pa;
     a.g = dg;
     a.nq = (int32_t)nq;
@@ -637,8 +635,12 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
     a.wq = w.wq + q0;
     a.mlp_norm = g->mlp_norm;
     a.mlp_w = p.o.switch_policy == GER_SWITCH_MLP ? g->mlp_w : nullptr;
+    a.mlp_at_start = p.o.mlp_at_start != 0;
     a.trace = p.trace ? p.trace + q0 * (int64_t)p.trace_steps * kTraceWidth : nullptr;
     a.trace_steps = p.trace_steps;
+    a.lb_force = p.lb_force ? p.lb_force + q0 : nullptr;
+    a.amc_list = w.amc_list;
+    a.amc_stride = w.q_cap;
     AmcArgs& m = *pm;
     m.g = dg;
     m.nq = (int32_t)nq;
@@ -657,21 +659,31 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
     m.delta = p.o.delta;
     m.dense_fp64 = fp64;
     m.err_flag = w.counters + 1;
+    m.amc_list = w.amc_list;
+    m.amc_stride = w.q_cap;
+    m.class_cnt = w.ctl->amc_class;  // device address of the control block's counts
 }
 
 // The tau AMC rounds (schedule -> walks -> batch statistics).
 // The AMC rounds: one walk launch and one statistics launch per batch; the
 // first schedule may fold the first batches into the first launch (the later
 // launches of those batches then return at once).
+// Batches of up to 4,095 queries need no schedule launch: the first walk
+// launch lays out its own chunks. With m.out_r set, the last statistics
+// launch writes the outputs.
 static void issue_amc(ger_graph* g, AmcArgs m, int64_t nq, cudaStream_t st) {
     m.batch = 1;
-    launch_amc_schedule(m, st);
+    m.fused_schedule = nq + 1 <= 4096 ? 1 : 0;
+    if (!m.fused_schedule) {
+        launch_amc_schedule(m, st);
+        note_launches(1);
+    }
     for (int b = 1; b <= m.tau; ++b) {
         m.batch = b;
         launch_amc_walk(m, g->sm_count, st);
         launch_amc_reduce(m, st);  // it also lays out the next launch
     }
-    note_launches(1 + 2 * m.tau);
+    note_launches(2 * m.tau);
 }
 
 // Dense columns of the hybrid engine for a batch of nq queries: as many
@@ -775,8 +787,8 @@ static void issue_smm_iteration(Engine& E, bool fp64, cudaStream_t st) {
 
 // The GEER launch sequence for queries [q0, q0 + nq), stream-ordered, with
 // one host round trip per SMM iteration to learn whether any query
-// continues.
-static int run_queries(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool fp64) {
+// continues; with `outputs`, its last launch writes r and the statistics.
+static int run_queries(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool fp64, bool outputs) {
     Workspace& w = g->ws;
     Engine E;
     int rc = prepare_engine(g, p, q0, nq, fp64, &E);
@@ -790,6 +802,10 @@ static int run_queries(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool
         if (*n_go == 0) break;
         issue_smm_iteration(E, fp64, p.st);
         launch_smm_advance(E.a, E.grid, 0, false, p.st);
+    }
+    if (outputs) {
+        E.m.out_r = p.r + q0;
+        E.m.out_stats = p.stats ? p.stats + q0 : nullptr;
     }
     issue_amc(g, E.m, nq, p.st);
     return GER_OK;
@@ -810,7 +826,7 @@ static bool same_key(const BatchGraph& bg, const Plan& p, bool fp64, const ger_g
            bg.lambda == g->lambda && bg.pool == g->ws.ent && bg.state == g->ws.st && bg.prof == g_prof_on &&
            bg.dense == g->ws.dX[0] && bg.dense_w == (p.o.smm_engine ? dense_width_for(const_cast<ger_graph*>(g), p.o) : 0) &&
            bg.dense_dev == g->ws.dblock_q && bg.mig == g->ws.dmig && bg.gen == g->ws.gen &&
-           bg.mlp == (g->mlp_w != nullptr);
+           bg.mlp == (g->mlp_w != nullptr) && bg.forced == (p.lb_force != nullptr);
 }
 
 // Capture the whole batch as one graph: the initial SMM iteration, a
@@ -844,7 +860,7 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
     int64_t body_launches = 0;
     e = cudaStreamBeginCaptureToGraph(st, graph, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
     if (e == cudaSuccess) {
-        cudaMemsetAsync(w.counters, 0, 4 * sizeof(int), st);
+        cudaMemsetAsync(w.counters, 0, 8 * sizeof(int), st);
         cudaMemsetAsync(w.ctl, 0, sizeof(SmmCtl), st);
         issue_smm_start(g, E, fp64, st);
         launch_smm_advance(a, E.grid, handle, true, st);
@@ -879,12 +895,9 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
             }
         }
         if (e == cudaSuccess) {
+            m.out_r = p.r;  // the last statistics launch writes the outputs
+            m.out_stats = p.stats;
             issue_amc(g, m, p.q, st);
-            const int fg = query_grid(p.q);
-            prof_begin(FAM_FINALIZE, st);
-            finalize_kernel<<<fg, kQueryCta, 0, st>>>(w.st, p.q, p.r, p.stats);
-            prof_end(FAM_FINALIZE, st);
-            note_launches(1);
         }
         cudaGraph_t done = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(st, &done);
@@ -916,6 +929,7 @@ static int build_graph(ger_graph* g, const Plan& p, bool fp64) {
     bg.launches = g_captured;  // kernels outside the while body, once per replay
     bg.body_launches = body_launches;
     bg.mlp = g->mlp_w != nullptr;
+    bg.forced = p.lb_force != nullptr;
     return GER_OK;
 }
 
@@ -949,22 +963,18 @@ static int run_batch(ger_graph* g, Plan& p) {
             GER_CUDA(cudaGraphLaunch(g->bg.exec, p.st));
             note_launches((int)g->bg.launches);
         } else {
-            GER_CUDA(cudaMemsetAsync(w.counters, 0, 4 * sizeof(int), p.st));
+            GER_CUDA(cudaMemsetAsync(w.counters, 0, 8 * sizeof(int), p.st));
             GER_CUDA(cudaMemsetAsync(w.ctl, 0, sizeof(SmmCtl), p.st));
             if (per_query) {
+                // each query's launches write its own outputs
                 for (int64_t i = 0; i < p.q; ++i) {
-                    rc = run_queries(g, p, i, 1, fp64);
+                    rc = run_queries(g, p, i, 1, fp64, true);
                     if (rc) return rc;
                 }
             } else {
-                rc = run_queries(g, p, 0, p.q, fp64);
+                rc = run_queries(g, p, 0, p.q, fp64, true);
                 if (rc) return rc;
             }
-            const int fg = query_grid(p.q);
-            prof_begin(FAM_FINALIZE, p.st);
-            finalize_kernel<<<fg, kQueryCta, 0, p.st>>>(w.st, p.q, p.r, p.stats);
-            prof_end(FAM_FINALIZE, p.st);
-            note_launches(1);
         }
         GER_CUDA(cudaGetLastError());
         GER_CUDA(cudaMemcpyAsync(w.host_rb, w.counters + 1, sizeof(int), cudaMemcpyDeviceToHost, p.st));
@@ -1015,7 +1025,7 @@ static int run_batch(ger_graph* g, Plan& p) {
 // translation units.
 int graph_view(const ger_graph* g, DevGraph* dg, double* lambda, bool* has_lambda, int* device, int* sm_count) {
     if (!g) return fail(GER_ERR_INVALID, "null graph");
-    *dg = DevGraph{g->n, g->nnz, g->row_ptr, g->col_idx, g->node_info, g->edge_rec};
+    *dg = dev_graph(g);
     *lambda = g->lambda;
     *has_lambda = g->has_lambda;
     *device = g->device;
@@ -1157,6 +1167,24 @@ int ger_load_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int 
             cudaGetLastError();
             g->edge_rec = nullptr;
         }
+        // the walks' packed neighbour lists (GEER_PACKED_COLS=0 keeps col_idx)
+        const char* pk_env = std::getenv("GEER_PACKED_COLS");
+        const int pk = pack_k_for(n);
+        if (pk > 0 && !(pk_env && pk_env[0] == '0')) {
+            const int64_t units = (g->nnz + pk - 1) / pk;
+            if (cudaMalloc(&g->cols_packed, (size_t)std::max<int64_t>(units, 1) * sizeof(uint4)) == cudaSuccess) {
+                launch_pack_cols(g->col_idx, g->nnz, pk, g->cols_packed, g->stream);
+                if (cudaStreamSynchronize(g->stream) != cudaSuccess) {
+                    cudaGetLastError();
+                    ger_free(g);
+                    return fail(GER_ERR_CUDA, "packing the neighbour lists");
+                }
+                g->pack_k = pk;
+            } else {
+                cudaGetLastError();
+                g->cols_packed = nullptr;
+            }
+        }
         if (n < INT32_MAX) {
             std::vector<int4> units, heavy;
             int32_t nslots = 0;
@@ -1190,6 +1218,7 @@ void ger_free(ger_graph* g) {
     cudaFree(g->col_idx);
     cudaFree(g->node_info);
     cudaFree(g->edge_rec);
+    cudaFree(g->cols_packed);
     cudaFree(g->dense_units);
     cudaFree(g->dense_heavy);
     cudaFree(g->mlp_w);
@@ -1243,7 +1272,7 @@ int ger_spectral_bound_info(const ger_graph* g, int32_t* converged, int32_t* ste
 static int check_opts(const ger_options* opt, ger_options* o) {
     if (opt) *o = *opt; else ger_default_options(o);
     if (!(o->delta > 0.0 && o->delta < 1.0)) return fail(GER_ERR_INVALID, "delta must be in (0, 1)");
-    if (o->tau < 1 || o->tau > 20) return fail(GER_ERR_INVALID, "tau must be in 1..20");
+    if (o->tau < 0 || o->tau > 20) return fail(GER_ERR_INVALID, "tau must be in 1..20 (0: the autotuned value)");
     if (o->precision != GER_FP32 && o->precision != GER_FP64) return fail(GER_ERR_INVALID, "bad precision");
     if (o->switch_policy != GER_SWITCH_RULE && o->switch_policy != GER_SWITCH_FIXED &&
         o->switch_policy != GER_SWITCH_MLP)
@@ -1257,14 +1286,20 @@ static int check_opts(const ger_options* opt, ger_options* o) {
     return GER_OK;
 }
 
+// tau = 0 in the options: the graph's autotuned tau, else the paper's 5
+static void resolve_tau(const ger_graph* g, ger_options* o) {
+    if (o->tau == 0) o->tau = g->tau_tuned > 0 ? g->tau_tuned : 5;
+}
+
 static int host_batch(ger_graph* g, int64_t q, const int32_t* s, const int32_t* t, const double* eps_arr,
                       double eps, const ger_options* opt, double* r_out, ger_query_stats* stats,
-                      float* trace_out = nullptr, int32_t trace_steps = 0) {
+                      float* trace_out = nullptr, int32_t trace_steps = 0, const int32_t* lb_arr = nullptr) {
     if (!g || q < 0 || (q > 0 && (!s || !t || !r_out))) return fail(GER_ERR_INVALID, "null argument or q < 0");
     if (q > 0x7fffffff) return fail(GER_ERR_INVALID, "q too large");
     Plan p;
     int rc = check_opts(opt, &p.o);
     if (rc) return rc;
+    resolve_tau(g, &p.o);
     for (int64_t i = 0; i < q; ++i) {
         if (s[i] < 0 || s[i] >= g->n || t[i] < 0 || t[i] >= g->n)
             return fail(GER_ERR_NODE_RANGE, "query %lld: node outside [0, %lld)", (long long)i, (long long)g->n);
@@ -1285,6 +1320,10 @@ static int host_batch(ger_graph* g, int64_t q, const int32_t* s, const int32_t* 
         std::vector<double> ev((size_t)q, eps);
         GER_CUDA(cudaMemcpyAsync(w.eps, ev.data(), q * sizeof(double), cudaMemcpyHostToDevice, st));
         GER_CUDA(cudaStreamSynchronize(st));
+    }
+    if (lb_arr) {
+        GER_CUDA(cudaMemcpyAsync(w.lbf, lb_arr, q * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        p.lb_force = w.lbf;
     }
     p.q = q;
     p.s = w.s;
@@ -1329,6 +1368,12 @@ int ger_query_batch_eps(ger_graph* g, int64_t q, const int32_t* s, const int32_t
                         const ger_options* opt, double* r_out, ger_query_stats* stats) {
     if (q > 0 && !eps) return fail(GER_ERR_INVALID, "null eps");
     return host_batch(g, q, s, t, eps, 0.0, opt, r_out, stats);
+}
+
+int ger_query_batch_lb(ger_graph* g, int64_t q, const int32_t* s, const int32_t* t, const double* eps,
+                       const int32_t* ell_b, const ger_options* opt, double* r_out, ger_query_stats* stats) {
+    if (q > 0 && (!eps || !ell_b)) return fail(GER_ERR_INVALID, "null eps or ell_b");
+    return host_batch(g, q, s, t, eps, 0.0, opt, r_out, stats, nullptr, 0, ell_b);
 }
 
 int ger_smm_trace(ger_graph* g, int64_t q, const int32_t* s, const int32_t* t, const double* eps,
@@ -1378,6 +1423,7 @@ int ger_autotune(ger_graph* g, int64_t q, const int32_t* s, const int32_t* t, co
     ger_options base;
     int rc = check_opts(opt, &base);
     if (rc) return rc;
+    resolve_tau(g, &base);
     const bool fp64 = base.precision == GER_FP64;
     ger_tuning res;
     std::memset(&res, 0, sizeof(res));
@@ -1427,6 +1473,23 @@ int ger_autotune(ger_graph* g, int64_t q, const int32_t* s, const int32_t* t, co
         }
     }
     g->hybrid_tuned = res.dense_switch;
+    // 3. tau (Algorithm 1's batch count): the whole batch with the caller's
+    //    options at tau = 1..8; Theorem 2 holds at delta / tau for every tau,
+    //    so the choice changes the walks drawn and the time, never the guarantee
+    float best_tau = 0.f;
+    for (int tau = 1; tau <= 8; ++tau) {
+        ger_options o = base;
+        o.tau = tau;
+        float ms = 0.f;
+        rc = timed_batch(g, q, s, t, eps, &o, 3, &ms);
+        if (rc) return rc;
+        res.tau_ms[tau - 1] = ms;
+        if (tau == 1 || ms < best_tau) {
+            best_tau = ms;
+            res.tau = tau;
+        }
+    }
+    g->tau_tuned = res.tau;
     if (out) *out = res;
     return GER_OK;
 }
@@ -1468,6 +1531,7 @@ int ger_query_batch_dev(ger_graph* g, int64_t q, const int32_t* s_dev, const int
     Plan p;
     int rc = check_opts(opt, &p.o);
     if (rc) return rc;
+    resolve_tau(g, &p.o);
     cudaSetDevice(g->device);
     if (q == 0) return GER_OK;
     rc = ensure_ws(g, q, std::max<int64_t>(g->ws.pool_cap, (int64_t)1 << 22));

@@ -4,7 +4,10 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
+
+#include "../../include/geer.h"
 
 namespace geer {
 
@@ -33,7 +36,10 @@ enum : int32_t { ST_SMM = 0, ST_AMC = 1, ST_DONE = 2, ST_ERROR = 3 };
 // DERR_FULL: a frontier table had no free slot left, which the load factor
 // (capacity >= twice the push pairs) rules out; the probe gives up instead of
 // looping.
-enum : int32_t { DERR_NONE = 0, DERR_NODE_RANGE = 1, DERR_CAPACITY = 2, DERR_TABLE = 3, DERR_ELL = 4, DERR_FULL = 5 };
+// DERR_CHUNKS: a walk launch's chunk layout outgrew the partial-sum array
+// (at most kMaxChunksPerQuery per query); the launch walks nothing.
+enum : int32_t { DERR_NONE = 0, DERR_NODE_RANGE = 1, DERR_CAPACITY = 2, DERR_TABLE = 3, DERR_ELL = 4, DERR_FULL = 5,
+                 DERR_CHUNKS = 6 };
 
 // Per-query state, one record per query of a batch (device memory).
 struct QState {
@@ -77,7 +83,7 @@ struct QSmm {
     int32_t dense;               // 1: this query's SMM runs on the dense engine
     int32_t dgo;                 // dense engine: 1 while iterations continue
     int32_t dblock, dcol;        // dense block and column pair
-    int32_t mlp_stop;            // learned switch: 1 when its network says to stop now
+    int32_t pad_m;
     int64_t tab_off, tab_cap;    // table of the current frontier
     int64_t ntab_off, ntab_cap;  // table being filled
     unsigned long long vol_paper;  // sum_{V_s} d + sum_{V_t} d (Eq. 17)
@@ -109,7 +115,16 @@ struct SmmCtl {
     int32_t heavy_max;           // largest heavy-push chunk count of any iteration
     uint32_t adv_done;           // CTAs of the advance kernel finished (last one keeps the books)
     int32_t pad;
+    // queries that entered AMC, per walk-length class (longest first; see
+    // amc_class): the walk launches hand out the chunks of the longest walks
+    // first, so the launch's last chunks are short ones
+    int32_t amc_class[8];
 };
+
+constexpr int kAmcClasses = 8;
+// class of a query whose walks have l_f steps: 0 for l_f >= 28, then one
+// class per 4 steps down to 7 for l_f < 4
+__host__ __device__ constexpr int amc_class(int lf) { return lf >= 28 ? 0 : 7 - lf / 4; }
 
 // slots of one query's F_0 table (F_0 = {s, t}; load 1/4)
 constexpr int kF0Slots = 8;
@@ -143,7 +158,33 @@ struct DevGraph {
     // per edge e = (u, v): {v, first edge of v, degree of v, 0} (null when absent): a walk
     // step's one load brings the next step's row as well
     const uint4* edge_rec = nullptr;
+    // the walks' copy of col_idx packed at kPackBits(pack_k) bits per entry,
+    // pack_k entries per 16-byte unit (entry e in unit e / pack_k); null with
+    // pack_k = 0 when not built (the walks then read col_idx)
+    const uint4* cols_packed = nullptr;
+    int32_t pack_k = 0;
 };
+
+// Entries per 16-byte unit of the packed neighbour lists and their width:
+// ids below 2^16 in 16 bits (8 per unit), below 2^21 in 21 bits (6 per
+// unit), below 2^25 in 25 bits (5 per unit); larger graphs keep col_idx.
+__host__ __device__ constexpr int pack_bits(int k) { return k == 8 ? 16 : (k == 6 ? 21 : (k == 5 ? 25 : 32)); }
+__host__ __device__ constexpr int pack_k_for(int64_t n) {
+    return n <= (int64_t)1 << 16 ? 8 : (n <= (int64_t)1 << 21 ? 6 : (n <= (int64_t)1 << 25 ? 5 : 0));
+}
+
+// Entry e of the packed neighbour lists (one 16-byte load; the entry may
+// straddle two 32-bit words of its unit, never the unit).
+template <int K>
+__device__ __forceinline__ int32_t packed_col(const uint4* cols, uint32_t e) {
+    constexpr int B = pack_bits(K);
+    const uint32_t u = e / K, j = e - u * K;
+    const uint4 w = __ldg(cols + u);
+    const uint32_t o = j * B, wi = o >> 5, sh = o & 31;
+    const uint32_t lo = wi == 0 ? w.x : (wi == 1 ? w.y : (wi == 2 ? w.z : w.w));
+    const uint32_t hi = wi == 0 ? w.y : (wi == 1 ? w.z : (wi == 2 ? w.w : 0u));
+    return (int32_t)(__funnelshift_r(lo, hi, sh) & ((1u << B) - 1u));
+}
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
@@ -316,6 +357,69 @@ __device__ __forceinline__ void switch_features(const QState* Q, const QSmm* M, 
     f[4] = h > 0.0 ? (float)log(h) : 0.0f;
     f[5] = (float)(s1 / ds + t1 / dt);
     *h_out = h;
+}
+
+// The learned switch's network for one query, by one thread (FP16 weights
+// read from global memory, FP32 arithmetic): the six raw inputs are
+// normalised as (f - mean) / std, then 6 -> 64 -> 64 -> 1 with ReLU hidden
+// layers; returns the output (the query switches when it is >= 0).
+__device__ __forceinline__ float mlp_eval_thread(const unsigned short* w, const float* norm, const float raw[kMlpIn]) {
+    float x[kMlpIn];
+#pragma unroll
+    for (int k = 0; k < kMlpIn; ++k) x[k] = (raw[k] - __ldg(norm + k)) / __ldg(norm + kMlpIn + k);
+    auto h = [&](int i) { return __half2float(__ushort_as_half(__ldg(w + i))); };
+    float h1[kMlpH];
+#pragma unroll
+    for (int j = 0; j < kMlpH; ++j) {
+        float z = h(kMlpOffB1 + j);
+#pragma unroll
+        for (int k = 0; k < kMlpIn; ++k) z = fmaf(h(kMlpOffW1 + j * kMlpIn + k), x[k], z);
+        h1[j] = fmaxf(z, 0.f);
+    }
+    float y = h(kMlpOffB3);
+    // W2 rows are 128 bytes (64 halves) from a 16-byte aligned offset: eight 16-byte loads a row
+    const uint4* w2 = reinterpret_cast<const uint4*>(w + kMlpOffW2);
+#pragma unroll 2
+    for (int j = 0; j < kMlpH; ++j) {
+        float z = h(kMlpOffB2 + j);
+#pragma unroll
+        for (int c = 0; c < kMlpH / 8; ++c) {
+            const uint4 v = __ldg(w2 + j * (kMlpH / 8) + c);
+            const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u[e]));
+                z = fmaf(f.x, h1[c * 8 + 2 * e], z);
+                z = fmaf(f.y, h1[c * 8 + 2 * e + 1], z);
+            }
+        }
+        y = fmaf(h(kMlpOffW3 + j), fmaxf(z, 0.f), y);
+    }
+    return y;
+}
+
+// The outputs of one query (its record of the batch state): r' and, when
+// asked for, the statistics record of include/geer.h.
+__device__ __forceinline__ void store_outputs(const QState& Q, int64_t q, double* r, ger_query_stats* stats) {
+    r[q] = Q.r;
+    if (stats) {
+        ger_query_stats o;
+        o.ell = Q.ell;
+        o.ell_b = Q.ell_b;
+        o.batches = Q.batch;
+        o.flags = Q.err;
+        o.eta0 = Q.eta0;
+        o.walks = Q.walks;
+        o.walk_steps = Q.walk_steps;
+        o.r_b = Q.r_b;
+        o.r_f = Q.r_f;
+        o.psi = Q.psi;
+        o.f_last = Q.f_last;
+        o.volume = Q.volume;
+        o.h = Q.h;
+        o.checksum = Q.checksum;
+        stats[q] = o;
+    }
 }
 
 }  // namespace geer

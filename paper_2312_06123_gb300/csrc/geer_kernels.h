@@ -47,10 +47,18 @@ struct SmmArgs {
     // learned switch (policy 1): input normalisation (mean[6], std[6]) and FP16 weights
     const float* mlp_norm = nullptr;
     const unsigned short* mlp_w = nullptr;  // null: no network, the rule of Eq. (17) decides
+    int32_t mlp_at_start = 0;               // also consult the network before the first SMM iteration
     // cost log: per query and SMM iteration 1..trace_steps, kTraceWidth floats
     float* trace = nullptr;
     int32_t trace_steps = 0;
     WalkQ* wq = nullptr;  // walk records, packed for the queries that enter AMC
+    // per-query SMM length (nullable): query q runs min(lb_force[q], l) SMM
+    // iterations when lb_force[q] >= 0, overriding the policy
+    const int32_t* lb_force = nullptr;
+    // queries entering AMC are appended to list amc_class(l_f): kAmcClasses
+    // lists of amc_stride entries (counts in ctl->amc_class)
+    int32_t* amc_list = nullptr;
+    int64_t amc_stride = 0;
 };
 
 // Columns of one cost-log row: the six switch inputs, the union frontier's
@@ -106,6 +114,19 @@ struct AmcArgs {
     int32_t dense_fp64;    // element type of dense-engine values
     double delta;
     int* err_flag;
+    // the first walk launch lays out its own chunks (batches of up to
+    // kSmemChunkBegin - 1 queries; no schedule launch)
+    int32_t fused_schedule = 0;
+    // the last statistics launch (batch tau) also writes every query's outputs
+    // (null: a separate finalize launch does)
+    double* out_r = nullptr;
+    ger_query_stats* out_stats = nullptr;
+    // the AMC queries by walk-length class (filled as they enter AMC; counts
+    // reset by the last statistics launch): batches of up to
+    // kSmemChunkBegin - 1 queries lay out their chunks in this order
+    const int32_t* amc_list = nullptr;
+    int64_t amc_stride = 0;
+    int32_t* class_cnt = nullptr;
 };
 
 // host launchers (one per kernel)
@@ -123,7 +144,6 @@ void launch_smm_push(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 void launch_smm_finish(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 void launch_smm_top2(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
 void launch_smm_decide(const SmmArgs& a, cudaStream_t st, bool first = false);
-void launch_smm_mlp(const SmmArgs& a, cudaStream_t st);  // the learned switch's call per query
 void launch_smm_advance(const SmmArgs& a, int grid, cudaGraphConditionalHandle h, bool use_handle, cudaStream_t st);
 void launch_smm_start(bool fp64, const SmmArgs& a, cudaStream_t st);
 void launch_smm_iteration(bool fp64, const SmmArgs& a, int grid, cudaStream_t st);
@@ -143,6 +163,8 @@ void launch_dense_migrate(bool fp64, const DenseArgs& d, const SmmArgs& a, cudaS
 void launch_amc_schedule(const AmcArgs& a, cudaStream_t st);
 // edge e -> {col_idx[e], node_info[col_idx[e]], 0}
 void launch_edge_records(const int32_t* col_idx, const uint2* node_info, int64_t nnz, uint4* out, cudaStream_t st);
+// col_idx -> k entries of pack_bits(k) bits per 16-byte unit
+void launch_pack_cols(const int32_t* col_idx, int64_t nnz, int k, uint4* out, cudaStream_t st);
 // one persistent grid (as many CTAs as fit on the GPU) over the batch's chunks
 void launch_amc_walk(const AmcArgs& a, int sm_count, cudaStream_t st);
 // batch statistics of the launch's batches and the next launch's layout
@@ -158,7 +180,7 @@ void note_launches(int k);
 // kernel families timed by the profiler
 enum Family : int { FAM_SMM_SETUP = 0, FAM_SMM_ADVANCE, FAM_SMM_PUSH, FAM_SMM_PUSH_HEAVY, FAM_SMM_FINISH,
                     FAM_SMM_TOP2, FAM_SMM_DECIDE, FAM_DENSE_SPMM, FAM_AMC_SCHEDULE, FAM_AMC_WALK, FAM_AMC_REDUCE,
-                    FAM_FINALIZE, FAM_LANCZOS, FAM_SMM_MLP, FAM_MLP_TRAIN, FAM_COUNT };
+                    FAM_FINALIZE, FAM_LANCZOS, FAM_MLP_TRAIN, FAM_COUNT };
 // bracket one launch on stream st with profiler events (no-op when off)
 void prof_begin(int fam, cudaStream_t st);
 void prof_end(int fam, cudaStream_t st);
@@ -180,7 +202,6 @@ int lanczos_spectral_bound(const DevGraph& g, int max_steps, double tol, cudaStr
 }  // namespace geer
 
 struct ger_graph;
-struct ger_query_stats;
 
 namespace geer {
 

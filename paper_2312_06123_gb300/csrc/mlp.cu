@@ -78,31 +78,6 @@ __device__ __forceinline__ float mlp_eval_warp(const float* sw, const float (&x)
 
 }  // namespace
 
-// The learned switch inside the SMM loop: one warp per query still in SMM
-// after iteration >= 1 with l_b < l; sets mlp_stop for the decide kernel.
-__global__ void __launch_bounds__(256) smm_mlp_kernel(SmmArgs a) {
-    __shared__ float sw[kSwSize];
-    __shared__ float norm[2 * kMlpIn];
-    mlp_load_inference(sw, a.mlp_w);
-    if (threadIdx.x < 2 * kMlpIn) norm[threadIdx.x] = a.mlp_norm[threadIdx.x];
-    __syncthreads();
-    const int iter = a.ctl->iter;
-    if (iter == 0) return;
-    const int lane = threadIdx.x & 31;
-    const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (q >= a.nq) return;
-    QSmm* M = a.sm + q;
-    const QState* Q = a.st + q;
-    if (!M->run || Q->status != ST_SMM || iter >= Q->ell) return;
-    float f[kMlpIn];
-    double h;
-    switch_features(Q, M, iter, a.delta, a.tau, f, &h);
-#pragma unroll
-    for (int k = 0; k < kMlpIn; ++k) f[k] = (f[k] - norm[k]) / norm[kMlpIn + k];
-    const float y = mlp_eval_warp(sw, f, lane);
-    if (lane == 0) M->mlp_stop = y >= 0.f ? 1 : 0;
-}
-
 // Batched inference: one warp per row of normalised inputs.
 __global__ void __launch_bounds__(256) mlp_forward_kernel(const float* x, int64_t rows, const unsigned short* w,
                                                           float* y) {
@@ -283,13 +258,6 @@ __global__ void mlp_master_kernel(const unsigned short* w16, float* master) {
     if (p < kMlpParams) master[p] = h2f(w16[p]);
 }
 
-void launch_smm_mlp(const SmmArgs& a, cudaStream_t st) {
-    const int grid = (int)((a.nq + 7) / 8);
-    prof_begin(FAM_SMM_MLP, st);
-    smm_mlp_kernel<<<grid, 256, 0, st>>>(a);
-    prof_end(FAM_SMM_MLP, st);
-    note_launches(1);
-}
 
 }  // namespace geer
 

@@ -243,6 +243,7 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
         case DERR_FULL:
             return set_error(GER_ERR_CAPACITY, "a frontier table ran out of free slots (load factor broken)");
         case DERR_ELL: return set_error(GER_ERR_INVALID, "truncation length undefined (lambda >= 1)");
+        case DERR_CHUNKS: return set_error(GER_ERR_CUDA, "a walk launch's chunk layout exceeded the partial-sum array");
         default: return set_error(GER_ERR_CUDA, "unknown device error");
     }
 }

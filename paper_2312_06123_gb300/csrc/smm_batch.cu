@@ -135,7 +135,7 @@ __device__ __forceinline__ bool setup_query(const SmmArgs& a, int64_t q) {
     Q->volume = 0; Q->h = 0; Q->f_last = 0; Q->eta0 = 0; Q->eta = 0; Q->walks = 0;
     Q->walk_steps = 0; Q->checksum = 0; Q->ppc = 0; Q->nchunks = 0; Q->table_off = 0;
     Q->table_mask = -1; Q->front = 0; Q->ell = 0; Q->ell_b = 0; Q->lf = 0; Q->ds = 0; Q->dt = 0;
-    M->run = 0; M->want = 0; M->mlp_stop = 0;
+    M->run = 0; M->want = 0;
     M->tab_off = M->tab_cap = M->ntab_off = M->ntab_cap = 0;
     M->dense = a.dense_engine ? 1 : 0;
     M->dgo = 0;
@@ -186,6 +186,7 @@ __device__ __forceinline__ bool setup_query(const SmmArgs& a, int64_t q) {
     M->inv_ds = 1.0 / ds;
     M->inv_dt = 1.0 / dt;
     M->lb_target = a.policy == 2 ? (a.fixed_lb < 0 ? (int32_t)ell : min(a.fixed_lb, (int32_t)ell)) : -1;
+    if (a.lb_force && a.lb_force[q] >= 0) M->lb_target = min(a.lb_force[q], (int32_t)ell);
     return true;
 }
 
@@ -235,6 +236,10 @@ __device__ __forceinline__ void leave_smm(const SmmArgs& a, int64_t q, QState* Q
     }
     if (lf > 0) {
         Q->status = ST_AMC;
+        if (a.amc_list) {
+            const int c = amc_class((int)lf);
+            a.amc_list[c * a.amc_stride + atomicAdd(&a.ctl->amc_class[c], 1)] = (int32_t)q;
+        }
         // the query's walk record
         WalkQ* wr = a.wq + q;
         wr->s = Q->s;
@@ -371,16 +376,26 @@ __global__ void smm_start_kernel(SmmArgs a) {
         // Algorithm 2 at i = 0: s*(s)/d(s) + t*(t)/d(t) - s*(t)/d(s) - t*(s)/d(t)
         Q->r_b = 1.0 / ds + 1.0 / dt - 0.0 / ds - 0.0 / dt;
         const int64_t ell = Q->ell;
-        const bool go = M->lb_target >= 0 ? (M->lb_target > 0) : (ell >= 1);
         const unsigned long long vol = (unsigned long long)Q->ds + (unsigned long long)Q->dt;
-        if (go) {
-            continue_smm(a, q, Q, M, 0, vol);
-        } else {
-            double psi = 0.0, h = 0.0;
-            int64_t eta0 = 0;
-            if (ell > 0) switch_quantities(ell, 1.0, 0.0, 1.0, 0.0, ds, dt, Q->eps, a.delta, a.tau, &psi, &eta0, &h);
-            leave_smm(a, q, Q, M, 0, 0, ell, psi, (double)vol, h, eta0, 2);
+        // Eq. (9) and h(l) at l_b = 0: max_1 = 1 and max_2 = 0 for both vectors
+        double psi = 0.0, h = 0.0;
+        int64_t eta0 = 0;
+        if (ell > 0) switch_quantities(ell, 1.0, 0.0, 1.0, 0.0, ds, dt, Q->eps, a.delta, a.tau, &psi, &eta0, &h);
+        bool go = M->lb_target >= 0 ? (M->lb_target > 0) : (ell >= 1);  // the loop runs once when l >= 1
+        if (go && M->lb_target < 0 && a.policy == 1 && a.mlp_w != nullptr && a.mlp_at_start) {
+            // the learned switch may stop before any SMM step (AMC alone, Algorithm 1):
+            // its inputs at l_b = 0 (those switch_features gives after an iteration)
+            float f[kMlpIn];
+            f[0] = (float)log(ds);
+            f[1] = (float)log(dt);
+            f[2] = (float)ell;
+            f[3] = (float)log((double)vol);
+            f[4] = h > 0.0 ? (float)log(h) : 0.0f;
+            f[5] = (float)(1.0 / ds + 1.0 / dt);
+            go = mlp_eval_thread(a.mlp_w, a.mlp_norm, f) < 0.f;
         }
+        if (go) continue_smm(a, q, Q, M, 0, vol);
+        else leave_smm(a, q, Q, M, 0, 0, ell, psi, (double)vol, h, eta0, 2);
     }
 }
 
@@ -617,9 +632,17 @@ __global__ void smm_decide_kernel(SmmArgs a) {
         if (iter == 0) {
             go = M->lb_target >= 0 ? (M->lb_target > 0) : (ell >= 1);  // the loop runs once when l >= 1
         } else {
-            // Eq. (17), or the learned switch's call when a network is installed
+            // Eq. (17); a learned switch, when installed, may stop a query
+            // earlier than Eq. (17) does, never later (the rule bounds its SMM
+            // work): its network is consulted only where the rule continues
             const bool learned = a.policy == 1 && a.mlp_w != nullptr;
-            const bool free_stop = (lb >= ell) || (learned ? M->mlp_stop != 0 : vol > h);
+            bool free_stop = (lb >= ell) || vol > h;
+            if (!free_stop && learned && M->lb_target < 0) {
+                float f[kMlpIn];
+                double hh;
+                switch_features(Q, M, lb, a.delta, a.tau, f, &hh);
+                free_stop = mlp_eval_thread(a.mlp_w, a.mlp_norm, f) >= 0.f;
+            }
             go = M->lb_target >= 0 ? (lb < M->lb_target) : !free_stop;
             if (a.trace && lb <= a.trace_steps) {
                 // cost log of the learned switch: its inputs and the next push's size
@@ -741,8 +764,7 @@ void launch_smm_top2(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
 
 void launch_smm_decide(const SmmArgs& a, cudaStream_t st, bool first) {
     const int grid = query_grid(a.nq);
-    // the first decision (l_b = 0) is the rule's "run at least once"
-    if (!first && a.policy == 1 && a.mlp_w != nullptr) launch_smm_mlp(a, st);
+    (void)first;
     prof_begin(FAM_SMM_DECIDE, st);
     smm_decide_kernel<<<grid, kQueryCta, 0, st>>>(a);
     prof_end(FAM_SMM_DECIDE, st);

@@ -55,12 +55,19 @@ def test_lambda_sidecar_round_trip_and_rejections(tmp_path):
 def test_switch_model_round_trip(tmp_path):
     rng = np.random.default_rng(1)
     m = switch.SwitchModel(norm=rng.normal(size=12).astype(np.float32), weights=switch.init_weights(4),
-                           loss=np.linspace(1, 0.1, 7).astype(np.float32), kappa=32.0, mu=1.5)
+                           loss=np.linspace(1, 0.1, 7).astype(np.float32), kappa=32.0, mu=1.5, at_start=True)
     p = str(tmp_path / "switch.npz")
     switch.save_model(m, p)
     r = switch.load_model(p)
     assert np.array_equal(r.norm, m.norm) and np.array_equal(r.weights, m.weights)
-    assert np.array_equal(r.loss, m.loss) and r.kappa == 32.0 and r.mu == 1.5
+    assert np.array_equal(r.loss, m.loss) and r.kappa == 32.0 and r.mu == 1.5 and r.at_start
+    # the options that run it: the learned policy, consulted before the first SMM iteration too
+    o = r.options()
+    assert o.switch_policy == geer.GER_SWITCH_MLP and o.mlp_at_start == 1
+    # a switch stored without the flag decides after SMM iterations only
+    np.savez(p, format=np.array(switch.MODEL_FORMAT), norm=m.norm, weights=m.weights, loss=m.loss,
+             kappa=1.0, mu=0.0)
+    assert not switch.load_model(p).at_start
     np.savez(p, format=np.array("other"), norm=m.norm, weights=m.weights, loss=m.loss, kappa=1.0, mu=0.0)
     with pytest.raises(ValueError):
         switch.load_model(p)

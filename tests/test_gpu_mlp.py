@@ -173,32 +173,38 @@ def test_learned_switch_gains_over_the_rule(rmat_model):
 
 
 def test_in_loop_decisions_match_the_network_oracle(rmat_model):
-    # The switch point the GPU takes under the learned policy is the first SMM
-    # iteration j < l at which the FP64 network oracle, fed the same raw inputs
-    # (the cost log of a fixed-policy run of the same queries: the same state
-    # after each iteration) normalised the same way, outputs >= 0; l if none.
-    # Rows whose output lies within 1e-4 of 0 (FP32 against FP64 rounding) are
-    # not judged.
+    # The switch point the GPU takes under the learned policy is the first
+    # decision j (0: before any SMM iteration) at which the FP64 network
+    # oracle, fed the same raw inputs (j = 0: the start inputs in closed form;
+    # j >= 1: the cost log of a fixed-policy run of the same queries, the same
+    # state after each iteration) normalised the same way, outputs >= 0, or
+    # Eq. (17)'s own switch point l*_b if that comes first (the network may
+    # stop a query earlier than the rule, never later). Rows whose output lies
+    # within 1e-4 of 0 (FP32 against FP64 rounding) are not judged.
     g, G, lam, model, _, _ = rmat_model
     assert model is not None
     q, steps = 512, 8
     s, t = pairs.uniform_pairs(g.n, q, 23)
     eps = np.full(q, 0.05)
     log, st_tr = G.smm_trace(s, t, eps, geer.default_options(), max_steps=steps)
+    _, st_rule = G.query(s, t, eps, geer.default_options(), stats=True)
     G.set_switch_mlp(model.norm, model.weights)
     try:
-        _, st = G.query(s, t, eps, geer.default_options(switch_policy=geer.GER_SWITCH_MLP), stats=True)
+        _, st = G.query(s, t, eps, model.options(), stats=True)
     finally:
         G.set_switch_mlp(None, None)
     theta = model.weights.view(np.float16).astype(np.float64)
     mean, std = model.norm[:6], model.norm[6:]
-    judged = stops_before_l = 0
+    d = g.degrees()
+    start = switch.inputs_at_start(d[s], d[t], st_tr["ell"], eps, 0.01, 5)
+    judged = stops_before_l = at_start = 0
     for i in range(q):
         ell = int(st_tr["ell"][i])
+        lb_rule = int(st_rule["ell_b"][i])
         assert int(st["ell"][i]) == ell
         expect, ambiguous = None, False
-        for j in range(1, min(ell, steps + 1)):
-            x = ((log[i, j - 1, :6] - mean) / std).astype(np.float32)
+        for j in range(0 if model.at_start else 1, min(lb_rule, steps + 1)):
+            x = (((start[i] if j == 0 else log[i, j - 1, :6]) - mean) / std).astype(np.float32)
             y = float(omlp.forward(theta, x.astype(np.float64)[None, :])[0][0])
             if abs(y) < 1e-4:
                 ambiguous = True
@@ -206,16 +212,18 @@ def test_in_loop_decisions_match_the_network_oracle(rmat_model):
             if y >= 0:
                 expect = j
                 break
-        if ambiguous or (expect is None and ell > steps):
+        if ambiguous or (expect is None and lb_rule > steps):
             continue
         if expect is None:
-            expect = ell
+            expect = lb_rule
         else:
-            stops_before_l += expect < ell
+            stops_before_l += expect < lb_rule
+            at_start += expect == 0
         judged += 1
         assert int(st["ell_b"][i]) == expect, (i, int(st["ell_b"][i]), expect, ell)
     assert judged >= 0.9 * q
-    print(f"{judged} of {q} switch points judged; {stops_before_l} stop before l")
+    print(f"{judged} of {q} switch points judged; {stops_before_l} stop before the rule's, {at_start} before "
+          f"any SMM iteration")
 
 
 def test_learned_switch_keeps_parity_and_eps(c1, rmat_model):
@@ -226,8 +234,7 @@ def test_learned_switch_keeps_parity_and_eps(c1, rmat_model):
     assert model is not None
     G.set_switch_mlp(model.norm, model.weights)
     try:
-        r, st = G.query(w.s, w.t, w.eps, geer.default_options(precision=geer.GER_FP64,
-                                                                switch_policy=geer.GER_SWITCH_MLP), stats=True)
+        r, st = G.query(w.s, w.t, w.eps, model.options(geer.default_options(precision=geer.GER_FP64)), stats=True)
     finally:
         G.set_switch_mlp(None, None)
     exact_r = exact.er_dense(g, w.s, w.t, exact.laplacian_pinv(g))

@@ -591,6 +591,46 @@ def test_autotune_changes_run_time_only(c1):
     same = s0["ell_b"] == s1["ell_b"]
     assert np.array_equal(s0["checksum"][same], s1["checksum"][same])
     assert np.allclose(r0[same], r1[same], rtol=1e-9, atol=0)
+    # tau: any choice keeps Theorem 2's guarantee (the test runs at delta / tau);
+    # options with tau = 0 take the tuned value
+    assert 1 <= tune["tau"] <= 8 and all(x > 0 for x in tune["tau_ms"])
+    r2, s2 = G.query(w.s, w.t, w.eps, _opts(precision=geer.GER_FP64, tau=0), stats=True)
+    r3, s3 = G.query(w.s, w.t, w.eps, _opts(precision=geer.GER_FP64, tau=tune["tau"]), stats=True)
+    assert np.array_equal(r2, r3) and np.array_equal(s2, s3)
+    assert np.all(s2["batches"] <= tune["tau"])
+    err = np.abs(r2 - exact.er_dense(g, w.s, w.t, exact.laplacian_pinv(g)))
+    assert (err > w.eps).sum() <= 3 and err.mean() < 0.1 / 3
+    for i in range(0, w.q, 11):
+        compare(r2[i], s2[i], replay(g, w.s[i], w.t[i], w.eps[i], lam, s2[i], i, tau=tune["tau"]), 1e-9, 1e-9,
+                tau=tune["tau"])
+
+
+@pytest.mark.parametrize("prec,rel", [(geer.GER_FP64, 1e-9), (geer.GER_FP32, 1e-5)])
+def test_per_query_smm_length(c1, prec, rel):
+    # ger_query_batch_lb: query i runs min(ell_b[i], l) SMM iterations (Fig. 10's
+    # experiment); -1 leaves the query to the rule of Eq. (17)
+    w, g, G, lam = c1
+    q = 40
+    s, t, eps = w.s[:q], w.t[:q], w.eps[:q]
+    lb = np.array([(i % 6) - 1 for i in range(q)], dtype=np.int32)  # -1, 0, 1, 2, 3, 4
+    r, st = G.query_lb(s, t, eps, lb, _opts(precision=prec), stats=True)
+    _, rule = G.query(s, t, eps, _opts(precision=prec), stats=True)
+    for i in range(q):
+        want = int(rule["ell_b"][i]) if lb[i] < 0 else min(int(lb[i]), int(st["ell"][i]))
+        assert int(st["ell_b"][i]) == want
+        ref = replay(g, s[i], t[i], eps[i], lam, st[i], i)
+        compare(r[i], st[i], ref, rel, rel)
+    # one length for every query is the fixed policy, bit for bit
+    r4, s4 = G.query_lb(s, t, eps, np.full(q, 2, np.int32), _opts(precision=prec), stats=True)
+    r5, s5 = G.query(s, t, eps, _opts(precision=prec, switch_policy=geer.GER_SWITCH_FIXED, fixed_ell_b=2),
+                     stats=True)
+    assert np.array_equal(r4, r5) and np.array_equal(s4, s5)
+    # around the rule's own switch point l*_b (Fig. 10): every offset stays within eps of L^+
+    Lp = exact.laplacian_pinv(g)
+    for k in (-2, 2):
+        lbk = np.clip(rule["ell_b"].astype(np.int64) + k, 0, None).astype(np.int32)
+        rk = G.query_lb(s, t, eps, lbk, _opts(precision=prec))
+        assert (np.abs(rk - exact.er_dense(g, s, t, Lp)) > eps).sum() <= 2
 
 
 def test_allocation_failure_leaves_the_handle_usable():

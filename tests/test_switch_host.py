@@ -81,3 +81,33 @@ def test_initial_weights_layout():
     assert np.std(w3) == pytest.approx(math.sqrt(1 / h), rel=0.4)
     assert np.array_equal(switch.init_weights(11), switch.init_weights(11))
     assert not np.array_equal(switch.init_weights(11), switch.init_weights(12))
+
+
+def test_price_start_rows_by_hand():
+    # decision j = 0 (before the first SMM iteration): C(0) = walks(0), AMC alone, no push;
+    # C(1) = kappa * push(0) + walks(1) + mu
+    nan = float("nan")
+    inputs0 = np.full((1, MLP_INPUTS), 7.0, np.float32)
+    lg = switch.price(np.zeros((1, 3, MLP_INPUTS), np.float32), np.array([[10.0, 20, 30, 40]]),
+                      np.array([[4000.0, 1000, 500, 100]]), np.array([5]), 2.0, 3.0, inputs0)
+    assert lg.cost[0].tolist() == [4000, 2 * 10 + 1000 + 3, 2 * 30 + 500 + 6, 2 * 60 + 100 + 9]
+    assert lg.step.tolist() == [0, 1, 2]
+    assert lg.target[0] == pytest.approx(math.log(1023 / 4000), rel=1e-6)
+    assert np.array_equal(lg.feats[0], inputs0[0])
+    # without the start inputs (or with walks(0) not logged) there is no j = 0 row
+    assert 0 not in _log(push=[[10, 20, 30, 40]], walks=[[nan, 1000, 500, 100]], ell=[5]).step.tolist()
+    # l = 0: no decision at all
+    lz = switch.price(np.zeros((1, 3, MLP_INPUTS), np.float32), np.array([[1.0, 1, 1, 1]]),
+                      np.array([[5.0, 5, 5, 5]]), np.array([0]), 2.0, 0.0, inputs0)
+    assert lz.step.size == 0
+
+
+def test_inputs_at_start_by_hand():
+    # d(s) = 2, d(t) = 4, l = 3, eps = 0.5, delta = 0.01, tau = 1: s* = e_s, t* = e_t give
+    # max_1 = 1, max_2 = 0, so psi = 2 * ceil(3/2) * (1/2 + 1/4) = 3 (Eq. 9);
+    # eta* = 2 * 9 * ln(2/0.01) / 0.25 = 381.48 (Eq. 8); h = (2^1 - 1) * ceil(381.48) = 382
+    f = switch.inputs_at_start(np.array([2]), np.array([4]), np.array([3]), 0.5, 0.01, 1)[0]
+    want = [math.log(2), math.log(4), 3.0, math.log(6), math.log(382), 0.75]
+    assert np.allclose(f, np.array(want, np.float32), rtol=1e-6)
+    # l = 0: no walks, h = 0 and its input is 0
+    assert switch.inputs_at_start(np.array([2]), np.array([4]), np.array([0]), 0.5, 0.01, 1)[0][4] == 0.0
