@@ -364,9 +364,10 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
 // launch's layout (chunk_begin) from a ticket counter.
 template <int W, bool REC, int K>
 __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a) {
-    __shared__ int32_t cbeg[kSmemChunkBegin];
-    __shared__ int32_t perm[kSmemChunkBegin];  // layout position -> query (ordered layouts)
-    __shared__ int32_t coff[kAmcClasses + 1];
+    // the launch's chunk prefix (nq + 1 entries, staged batches only): dynamic
+    // shared memory sized to the batch, so the rest of the SM's unified L1
+    // keeps caching the lookup tables and node records the walks read
+    extern __shared__ int32_t cbeg[];
     __shared__ int64_t scan[kWarps + 1];
     __shared__ unsigned long long s_steps;
     // batches of this launch: the first launch walks *a.group batches, the
@@ -396,45 +397,16 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
     }
     if (a.batch > 1 && a.batch <= group) return;
     const int nbatch = a.batch == 1 ? group : 1;
-    // chunk prefix over the layout's positions: built here from the per-query
-    // counts (small batches), else laid out by the schedule. Small batches
-    // place the queries in AMC longest walks first (their walk-length class
-    // lists), so that the launch's last chunks are short ones.
+    // chunk prefix over the queries: built here from the per-query counts
+    // (small batches), else laid out by the schedule
     const bool staged = a.nq + 1 <= kSmemChunkBegin;
-    const bool ordered = staged && a.amc_list != nullptr;
-    int npos = a.nq;
-    if (ordered) {
-        if (threadIdx.x == 0) {
-            int o = 0;
-            for (int c = 0; c < kAmcClasses; ++c) {
-                coff[c] = o;
-                o += a.class_cnt[c];
-            }
-            coff[kAmcClasses] = o;
-        }
-        __syncthreads();
-        npos = coff[kAmcClasses];
-        for (int p = threadIdx.x; p < npos; p += blockDim.x) {
-            int c = 0;
-            while (p >= coff[c + 1]) ++c;
-            perm[p] = a.amc_list[c * a.amc_stride + (p - coff[c])];
-        }
-        __syncthreads();
-    }
-    auto query_at = [&](int p) -> int { return ordered ? perm[p] : p; };
     if (staged) {
         const int64_t maxc = kMaxChunksPerQuery / nbatch;
-        if (fused && ordered && blockIdx.x == 0) {
-            // queries outside AMC have no chunks in any launch of this phase
-            for (int q = threadIdx.x; q < a.nq; q += blockDim.x) a.chunk_count[q] = 0;
-            __syncthreads();
-        }
         int64_t carry = 0;
-        for (int64_t tile = 0; tile < npos; tile += kCta) {
-            const int64_t p = tile + threadIdx.x;
+        for (int64_t tile = 0; tile < a.nq; tile += kCta) {
+            const int64_t q = tile + threadIdx.x;
             int64_t cnt = 0;
-            if (p < npos) {
-                const int q = query_at((int)p);
+            if (q < a.nq) {
                 if (fused) {
                     const int64_t eta = a.wq[q].eta;
                     for (int i = 0; eta > 0 && i < nbatch; ++i) {
@@ -452,20 +424,18 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
             }
             int64_t tot;
             const int64_t ex = cta_excl_scan(cnt, scan, &tot);
-            if (p < npos) cbeg[p] = (int32_t)(carry + ex);
+            if (q < a.nq) cbeg[q] = (int32_t)(carry + ex);
             carry += tot;
         }
-        if (threadIdx.x == 0) cbeg[npos] = (int32_t)carry;
+        if (threadIdx.x == 0) cbeg[a.nq] = (int32_t)carry;
         __syncthreads();
-        if (blockIdx.x == 0) {  // each query's first chunk, for the statistics launch that follows
-            for (int p = threadIdx.x; p < npos; p += blockDim.x) a.chunk_begin[query_at(p)] = cbeg[p];
-            if (threadIdx.x == 0) a.chunk_begin[a.nq] = cbeg[npos];
-        }
+        if (blockIdx.x == 0)  // for the statistics launch that follows
+            for (int i = threadIdx.x; i <= a.nq; i += blockDim.x) a.chunk_begin[i] = cbeg[i];
     }
     const int64_t* cb_glob = a.chunk_begin;
     auto cb_arr = [&](int i) -> int64_t { return staged ? (int64_t)cbeg[i] : cb_glob[i]; };
     const int lane = threadIdx.x & 31;
-    const int64_t total = cb_arr(npos);
+    const int64_t total = cb_arr(a.nq);
     if (total > a.partial_cap) {  // cannot happen with a valid layout; never write past the partials
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(a.err_flag, 0, DERR_CHUNKS);
         return;
@@ -476,13 +446,13 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
         if (lane == 0) ticket = atomicAdd(a.walk_ctr, 1ull);
         const int64_t c = (int64_t)__shfl_sync(0xffffffffu, ticket, 0);
         if (c >= total) break;
-        // owning position: last p with cbeg[p] <= c
-        int lo = 0, hi = npos + 1;
+        // owning query: last q with chunk_begin[q] <= c
+        int lo = 0, hi = a.nq + 1;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
             if (cb_arr(mid) <= c) lo = mid + 1; else hi = mid;
         }
-        const WalkQ* WQ = a.wq + query_at(lo - 1);
+        const WalkQ* WQ = a.wq + (lo - 1);
         double sz, sz2;
         uint64_t cs;
         walk_chunk<W, REC, K>(a, WQ, c - cb_arr(lo - 1), WQ->eta, a.batch, nbatch, lane, &sz, &sz2, &cs);
@@ -536,9 +506,6 @@ __global__ void __launch_bounds__(kCta) amc_reduce_kernel(AmcArgs a) {
     const int group = *a.group;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t q0 = (int64_t)blockIdx.x * kReduceQ;
-    // every walk launch of this AMC phase is done: the class lists start empty for the next
-    if (a.class_cnt && a.batch == a.tau && blockIdx.x == 0 && threadIdx.x < kAmcClasses)
-        a.class_cnt[threadIdx.x] = 0;
     // the last launch writes every query's outputs (warp 0, one query per lane)
     const bool outputs = a.out_r != nullptr && a.batch == a.tau;
     if (a.batch > 1 && a.batch <= group) {  // walked and evaluated with batch 1
@@ -689,18 +656,20 @@ void launch_edge_records(const int32_t* col_idx, const uint2* node_info, int64_t
 // packed k to a 16-byte unit (k = 8, 6, 5), or plain col_idx.
 template <bool REC, int K>
 static void launch_walk_variant(const AmcArgs& a, int sm_count, cudaStream_t st) {
-    static int per_sm = 0;  // resident CTAs per SM
+    // the chunk prefix: nq + 1 int32 for batches up to kSmemChunkBegin - 1 queries
+    const size_t smem = a.nq + 1 <= kSmemChunkBegin ? (size_t)(a.nq + 1) * sizeof(int32_t) : 0;
+    static int per_sm = 0;  // resident CTAs per SM (register bound; the prefix is at most 16 KB)
     if (per_sm == 0) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, amc_walk_kernel<kWalksPerLane, REC, K>, 256, 0) !=
-                cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, amc_walk_kernel<kWalksPerLane, REC, K>, 256,
+                                                          kSmemChunkBegin * sizeof(int32_t)) != cudaSuccess ||
             b < 1) {
             cudaGetLastError();
             b = 1;
         }
         per_sm = b;
     }
-    amc_walk_kernel<kWalksPerLane, REC, K><<<sm_count * per_sm, 256, 0, st>>>(a);
+    amc_walk_kernel<kWalksPerLane, REC, K><<<sm_count * per_sm, 256, smem, st>>>(a);
 }
 
 void launch_amc_walk(const AmcArgs& a, int sm_count, cudaStream_t st) {

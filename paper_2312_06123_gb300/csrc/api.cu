@@ -145,7 +145,6 @@ struct Workspace {
     int64_t* chunk_begin = nullptr;
     int32_t* chunk_count = nullptr;
     int32_t* lbf = nullptr;       // per-query forced SMM lengths (ger_query_batch_lb)
-    int32_t* amc_list = nullptr;  // kAmcClasses lists of q_cap queries (walk-length classes)
     WalkQ* wq = nullptr;
     Partial* partial = nullptr;
     int64_t partial_cap = 0;
@@ -253,7 +252,7 @@ static DevGraph dev_graph(const ger_graph* g) {
 static void free_ws(Workspace& w) {
     cudaFree(w.st); cudaFree(w.s); cudaFree(w.t); cudaFree(w.eps); cudaFree(w.r); cudaFree(w.stats);
     cudaFree(w.chunk_begin); cudaFree(w.partial); cudaFree(w.qsmm);
-    cudaFree(w.wq); cudaFree(w.chunk_count); cudaFree(w.lbf); cudaFree(w.amc_list);
+    cudaFree(w.wq); cudaFree(w.chunk_count); cudaFree(w.lbf);
     cudaFree(w.ctl); cudaFree(w.ent); cudaFree(w.sums); cudaFree(w.yvals); cudaFree(w.counters);
     cudaFree(w.heavy);
     cudaFree(w.dX[0]); cudaFree(w.dX[1]);
@@ -290,9 +289,8 @@ static int ensure_ws(ger_graph* g, int64_t q, int64_t pool_cap) {
     if (q > w.q_cap) {
         cudaFree(w.st); cudaFree(w.s); cudaFree(w.t); cudaFree(w.eps); cudaFree(w.r); cudaFree(w.stats);
         cudaFree(w.chunk_begin); cudaFree(w.partial); cudaFree(w.qsmm);
-        cudaFree(w.wq); cudaFree(w.chunk_count); cudaFree(w.lbf); cudaFree(w.amc_list);
+        cudaFree(w.wq); cudaFree(w.chunk_count); cudaFree(w.lbf);
         w.lbf = nullptr;
-        w.amc_list = nullptr;
         w.st = nullptr; w.s = nullptr; w.t = nullptr; w.eps = nullptr; w.r = nullptr; w.stats = nullptr;
         w.chunk_begin = nullptr; w.partial = nullptr; w.qsmm = nullptr;
         w.wq = nullptr; w.chunk_count = nullptr;
@@ -302,7 +300,7 @@ static int ensure_ws(ger_graph* g, int64_t q, int64_t pool_cap) {
         if (alloc(&w.st, qc) || alloc(&w.s, qc) || alloc(&w.t, qc) || alloc(&w.eps, qc) || alloc(&w.r, qc) ||
             alloc(&w.stats, qc) || alloc(&w.chunk_begin, qc + 1) || alloc(&w.partial, pc) ||
             alloc(&w.qsmm, qc) || alloc(&w.wq, qc) ||
-            alloc(&w.chunk_count, qc) || alloc(&w.lbf, qc) || alloc(&w.amc_list, kAmcClasses * qc)) {
+            alloc(&w.chunk_count, qc) || alloc(&w.lbf, qc)) {
             cudaGetLastError();
             return fail(GER_ERR_OOM, "workspace for %lld queries", (long long)q);
         }
@@ -639,8 +637,6 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
     a.trace = p.trace ? p.trace + q0 * (int64_t)p.trace_steps * kTraceWidth : nullptr;
     a.trace_steps = p.trace_steps;
     a.lb_force = p.lb_force ? p.lb_force + q0 : nullptr;
-    a.amc_list = w.amc_list;
-    a.amc_stride = w.q_cap;
     AmcArgs& m = *pm;
     m.g = dg;
     m.nq = (int32_t)nq;
@@ -659,9 +655,6 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
     m.delta = p.o.delta;
     m.dense_fp64 = fp64;
     m.err_flag = w.counters + 1;
-    m.amc_list = w.amc_list;
-    m.amc_stride = w.q_cap;
-    m.class_cnt = w.ctl->amc_class;  // device address of the control block's counts
 }
 
 // The tau AMC rounds (schedule -> walks -> batch statistics).

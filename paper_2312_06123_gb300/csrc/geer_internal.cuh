@@ -115,16 +115,7 @@ struct SmmCtl {
     int32_t heavy_max;           // largest heavy-push chunk count of any iteration
     uint32_t adv_done;           // CTAs of the advance kernel finished (last one keeps the books)
     int32_t pad;
-    // queries that entered AMC, per walk-length class (longest first; see
-    // amc_class): the walk launches hand out the chunks of the longest walks
-    // first, so the launch's last chunks are short ones
-    int32_t amc_class[8];
 };
-
-constexpr int kAmcClasses = 8;
-// class of a query whose walks have l_f steps: 0 for l_f >= 28, then one
-// class per 4 steps down to 7 for l_f < 4
-__host__ __device__ constexpr int amc_class(int lf) { return lf >= 28 ? 0 : 7 - lf / 4; }
 
 // slots of one query's F_0 table (F_0 = {s, t}; load 1/4)
 constexpr int kF0Slots = 8;
@@ -359,41 +350,54 @@ __device__ __forceinline__ void switch_features(const QState* Q, const QSmm* M, 
     *h_out = h;
 }
 
-// The learned switch's network for one query, by one thread (FP16 weights
-// read from global memory, FP32 arithmetic): the six raw inputs are
-// normalised as (f - mean) / std, then 6 -> 64 -> 64 -> 1 with ReLU hidden
-// layers; returns the output (the query switches when it is >= 0).
-__device__ __forceinline__ float mlp_eval_thread(const unsigned short* w, const float* norm, const float raw[kMlpIn]) {
+// Floats of the network's weights staged in shared memory (a whole number of
+// 16-byte FP16 vectors).
+constexpr int kMlpStaged = (kMlpParams + 7) / 8 * 8;
+
+// The whole CTA converts the network's FP16 weights into FP32 in shared
+// memory (16-byte loads; the weight buffer is allocated with 16 bytes to
+// spare, so the last vector stays inside it).
+__device__ __forceinline__ void mlp_stage(float* sw, const unsigned short* w) {
+    const uint4* src = reinterpret_cast<const uint4*>(w);
+    for (int i = threadIdx.x; i < kMlpStaged / 8; i += blockDim.x) {
+        const uint4 v = __ldg(src + i);
+        const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u[e]));
+            sw[8 * i + 2 * e] = f.x;
+            sw[8 * i + 2 * e + 1] = f.y;
+        }
+    }
+}
+
+// The network for one query, by one thread, from the staged weights (FP32
+// arithmetic; four partial sums per dot product).
+__device__ __forceinline__ float mlp_eval_staged(const float* sw, const float* norm, const float raw[kMlpIn]) {
     float x[kMlpIn];
 #pragma unroll
     for (int k = 0; k < kMlpIn; ++k) x[k] = (raw[k] - __ldg(norm + k)) / __ldg(norm + kMlpIn + k);
-    auto h = [&](int i) { return __half2float(__ushort_as_half(__ldg(w + i))); };
     float h1[kMlpH];
 #pragma unroll
     for (int j = 0; j < kMlpH; ++j) {
-        float z = h(kMlpOffB1 + j);
+        float z = sw[kMlpOffB1 + j];
 #pragma unroll
-        for (int k = 0; k < kMlpIn; ++k) z = fmaf(h(kMlpOffW1 + j * kMlpIn + k), x[k], z);
+        for (int k = 0; k < kMlpIn; ++k) z = fmaf(sw[kMlpOffW1 + j * kMlpIn + k], x[k], z);
         h1[j] = fmaxf(z, 0.f);
     }
-    float y = h(kMlpOffB3);
-    // W2 rows are 128 bytes (64 halves) from a 16-byte aligned offset: eight 16-byte loads a row
-    const uint4* w2 = reinterpret_cast<const uint4*>(w + kMlpOffW2);
-#pragma unroll 2
+    float y = sw[kMlpOffB3];
+#pragma unroll 4
     for (int j = 0; j < kMlpH; ++j) {
-        float z = h(kMlpOffB2 + j);
+        const float* row = sw + kMlpOffW2 + j * kMlpH;
+        float z0 = sw[kMlpOffB2 + j], z1 = 0.f, z2 = 0.f, z3 = 0.f;
 #pragma unroll
-        for (int c = 0; c < kMlpH / 8; ++c) {
-            const uint4 v = __ldg(w2 + j * (kMlpH / 8) + c);
-            const uint32_t u[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u[e]));
-                z = fmaf(f.x, h1[c * 8 + 2 * e], z);
-                z = fmaf(f.y, h1[c * 8 + 2 * e + 1], z);
-            }
+        for (int k = 0; k < kMlpH; k += 4) {
+            z0 = fmaf(row[k], h1[k], z0);
+            z1 = fmaf(row[k + 1], h1[k + 1], z1);
+            z2 = fmaf(row[k + 2], h1[k + 2], z2);
+            z3 = fmaf(row[k + 3], h1[k + 3], z3);
         }
-        y = fmaf(h(kMlpOffW3 + j), fmaxf(z, 0.f), y);
+        y = fmaf(sw[kMlpOffW3 + j], fmaxf((z0 + z1) + (z2 + z3), 0.f), y);
     }
     return y;
 }

@@ -55,10 +55,6 @@ struct SmmArgs {
     // per-query SMM length (nullable): query q runs min(lb_force[q], l) SMM
     // iterations when lb_force[q] >= 0, overriding the policy
     const int32_t* lb_force = nullptr;
-    // queries entering AMC are appended to list amc_class(l_f): kAmcClasses
-    // lists of amc_stride entries (counts in ctl->amc_class)
-    int32_t* amc_list = nullptr;
-    int64_t amc_stride = 0;
 };
 
 // Columns of one cost-log row: the six switch inputs, the union frontier's
@@ -121,12 +117,6 @@ struct AmcArgs {
     // (null: a separate finalize launch does)
     double* out_r = nullptr;
     ger_query_stats* out_stats = nullptr;
-    // the AMC queries by walk-length class (filled as they enter AMC; counts
-    // reset by the last statistics launch): batches of up to
-    // kSmemChunkBegin - 1 queries lay out their chunks in this order
-    const int32_t* amc_list = nullptr;
-    int64_t amc_stride = 0;
-    int32_t* class_cnt = nullptr;
 };
 
 // host launchers (one per kernel)

@@ -236,10 +236,6 @@ __device__ __forceinline__ void leave_smm(const SmmArgs& a, int64_t q, QState* Q
     }
     if (lf > 0) {
         Q->status = ST_AMC;
-        if (a.amc_list) {
-            const int c = amc_class((int)lf);
-            a.amc_list[c * a.amc_stride + atomicAdd(&a.ctl->amc_class[c], 1)] = (int32_t)q;
-        }
         // the query's walk record
         WalkQ* wr = a.wq + q;
         wr->s = Q->s;
@@ -332,10 +328,16 @@ __device__ __forceinline__ bool continue_smm(const SmmArgs& a, int64_t q, QState
 // max_2 = 0 for both vectors (one non-zero entry each).
 template <typename T>
 __global__ void smm_start_kernel(SmmArgs a) {
+    extern __shared__ float sw[];  // the staged network when it decides at l_b = 0
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctl->iter = 0;
         a.ctl->lo[0] = 0;
         a.ctl->hi[0] = (int64_t)kF0Slots * a.nq;
+    }
+    const bool learned = a.policy == 1 && a.mlp_w != nullptr && a.mlp_at_start;
+    if (learned) {
+        mlp_stage(sw, a.mlp_w);
+        __syncthreads();
     }
     T* ys = reinterpret_cast<T*>(a.ys);
     T* yt = reinterpret_cast<T*>(a.yt);
@@ -382,7 +384,7 @@ __global__ void smm_start_kernel(SmmArgs a) {
         int64_t eta0 = 0;
         if (ell > 0) switch_quantities(ell, 1.0, 0.0, 1.0, 0.0, ds, dt, Q->eps, a.delta, a.tau, &psi, &eta0, &h);
         bool go = M->lb_target >= 0 ? (M->lb_target > 0) : (ell >= 1);  // the loop runs once when l >= 1
-        if (go && M->lb_target < 0 && a.policy == 1 && a.mlp_w != nullptr && a.mlp_at_start) {
+        if (go && M->lb_target < 0 && learned) {
             // the learned switch may stop before any SMM step (AMC alone, Algorithm 1):
             // its inputs at l_b = 0 (those switch_features gives after an iteration)
             float f[kMlpIn];
@@ -392,7 +394,7 @@ __global__ void smm_start_kernel(SmmArgs a) {
             f[3] = (float)log((double)vol);
             f[4] = h > 0.0 ? (float)log(h) : 0.0f;
             f[5] = (float)(1.0 / ds + 1.0 / dt);
-            go = mlp_eval_thread(a.mlp_w, a.mlp_norm, f) < 0.f;
+            go = mlp_eval_staged(sw, a.mlp_norm, f) < 0.f;
         }
         if (go) continue_smm(a, q, Q, M, 0, vol);
         else leave_smm(a, q, Q, M, 0, 0, ell, psi, (double)vol, h, eta0, 2);
@@ -609,53 +611,68 @@ __global__ void __launch_bounds__(256) smm_top2_kernel(SmmArgs a) {
 }
 
 // decide: one thread per query whose table was just finished; a query that
-// continues gets its next table (or dense column) here
+// continues gets its next table (or dense column) here. With a learned
+// switch, the CTA stages the network's weights in shared memory once some
+// query of it needs the network (where Eq. (17) continues).
 __global__ void smm_decide_kernel(SmmArgs a) {
+    extern __shared__ float sw[];  // kMlpStaged floats with a learned switch, else none
     const int iter = a.ctl->iter;
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < a.nq; q += gridDim.x * blockDim.x) {
-        QSmm* M = a.sm + q;
-        QState* Q = a.st + q;
-        if (!M->run || Q->status != ST_SMM) continue;
-        const double ds = (double)Q->ds, dt = (double)Q->dt;
-        // Algorithm 2: r_b += s*(s)/d(s) + t*(t)/d(t) - s*(t)/d(s) - t*(s)/d(t)
-        Q->r_b += M->sval[0] / ds + M->sval[3] / dt - M->sval[2] / ds - M->sval[1] / dt;
+    const bool learned = iter > 0 && a.policy == 1 && a.mlp_w != nullptr;
+    bool staged = false;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // a loop of the same trip count for every thread of the CTA (the staging is CTA-wide)
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.nq; base += stride) {
+        const int64_t q = base + threadIdx.x;
+        const bool active = q < a.nq && a.sm[q].run && a.st[q].status == ST_SMM;
+        QSmm* M = a.sm + (active ? q : 0);
+        QState* Q = a.st + (active ? q : 0);
         const int64_t lb = iter;
-        const int64_t ell = Q->ell;
-        double s1, s2, t1, t2;
-        smm_maxima(M, &s1, &s2, &t1, &t2);
-        const double vol = (double)M->vol_paper;
-        const int64_t lf = ell - lb;
-        double psi = 0.0, h = 0.0;
-        int64_t eta0 = 0;
-        if (lf > 0) switch_quantities(lf, s1, s2, t1, t2, ds, dt, Q->eps, a.delta, a.tau, &psi, &eta0, &h);
-        bool go;
-        if (iter == 0) {
-            go = M->lb_target >= 0 ? (M->lb_target > 0) : (ell >= 1);  // the loop runs once when l >= 1
-        } else {
-            // Eq. (17); a learned switch, when installed, may stop a query
-            // earlier than Eq. (17) does, never later (the rule bounds its SMM
-            // work): its network is consulted only where the rule continues
-            const bool learned = a.policy == 1 && a.mlp_w != nullptr;
-            bool free_stop = (lb >= ell) || vol > h;
-            if (!free_stop && learned && M->lb_target < 0) {
-                float f[kMlpIn];
-                double hh;
-                switch_features(Q, M, lb, a.delta, a.tau, f, &hh);
-                free_stop = mlp_eval_thread(a.mlp_w, a.mlp_norm, f) >= 0.f;
-            }
-            go = M->lb_target >= 0 ? (lb < M->lb_target) : !free_stop;
-            if (a.trace && lb <= a.trace_steps) {
-                // cost log of the learned switch: its inputs and the next push's size
-                float f[kMlpIn];
-                double hh;
-                switch_features(Q, M, lb, a.delta, a.tau, f, &hh);
-                float* row = a.trace + ((int64_t)q * a.trace_steps + (lb - 1)) * kTraceWidth;
+        double psi = 0.0, h = 0.0, vol = 0.0;
+        int64_t eta0 = 0, ell = 0, lf = 0;
+        bool go = false, need = false;
+        float f[kMlpIn];
+        if (active) {
+            const double ds = (double)Q->ds, dt = (double)Q->dt;
+            // Algorithm 2: r_b += s*(s)/d(s) + t*(t)/d(t) - s*(t)/d(s) - t*(s)/d(t)
+            Q->r_b += M->sval[0] / ds + M->sval[3] / dt - M->sval[2] / ds - M->sval[1] / dt;
+            ell = Q->ell;
+            double s1, s2, t1, t2;
+            smm_maxima(M, &s1, &s2, &t1, &t2);
+            vol = (double)M->vol_paper;
+            lf = ell - lb;
+            if (lf > 0) switch_quantities(lf, s1, s2, t1, t2, ds, dt, Q->eps, a.delta, a.tau, &psi, &eta0, &h);
+            if (iter == 0) {
+                go = M->lb_target >= 0 ? (M->lb_target > 0) : (ell >= 1);  // the loop runs once when l >= 1
+            } else {
+                // Eq. (17); a learned switch may stop a query earlier than Eq. (17)
+                // does, never later (the rule bounds its SMM work): its network is
+                // consulted only where the rule continues
+                const bool rule_stop = (lb >= ell) || vol > h;
+                go = M->lb_target >= 0 ? (lb < M->lb_target) : !rule_stop;
+                need = learned && M->lb_target < 0 && !rule_stop;
+                if (need || (a.trace && lb <= a.trace_steps)) {
+                    double hh;
+                    switch_features(Q, M, lb, a.delta, a.tau, f, &hh);
+                }
+                if (a.trace && lb <= a.trace_steps) {
+                    // cost log of the learned switch: its inputs and the next push's size
+                    float* row = a.trace + ((int64_t)q * a.trace_steps + (lb - 1)) * kTraceWidth;
 #pragma unroll
-                for (int k = 0; k < kMlpIn; ++k) row[k] = f[k];
-                row[6] = (float)M->vol_union;
-                row[7] = (float)M->vol_paper;
+                    for (int k = 0; k < kMlpIn; ++k) row[k] = f[k];
+                    row[6] = (float)M->vol_union;
+                    row[7] = (float)M->vol_paper;
+                }
             }
         }
+        if (learned && __syncthreads_or(need)) {
+            if (!staged) {
+                mlp_stage(sw, a.mlp_w);
+                __syncthreads();
+                staged = true;
+            }
+            if (need && mlp_eval_staged(sw, a.mlp_norm, f) >= 0.f) go = false;
+        }
+        if (!active) continue;
         // the table just finished holds the current frontier
         M->tab_off = M->ntab_off;
         M->tab_cap = M->ntab_cap;
@@ -727,9 +744,10 @@ void launch_smm_setup(const SmmArgs& a, cudaStream_t st) {
 
 void launch_smm_start(bool fp64, const SmmArgs& a, cudaStream_t st) {
     const int grid = query_grid(a.nq);
+    const size_t smem = (a.policy == 1 && a.mlp_w && a.mlp_at_start) ? kMlpStaged * sizeof(float) : 0;
     prof_begin(FAM_SMM_SETUP, st);
-    if (fp64) smm_start_kernel<double><<<grid, kQueryCta, 0, st>>>(a);
-    else smm_start_kernel<float><<<grid, kQueryCta, 0, st>>>(a);
+    if (fp64) smm_start_kernel<double><<<grid, kQueryCta, smem, st>>>(a);
+    else smm_start_kernel<float><<<grid, kQueryCta, smem, st>>>(a);
     prof_end(FAM_SMM_SETUP, st);
     note_launches(1);
 }
@@ -765,8 +783,9 @@ void launch_smm_top2(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
 void launch_smm_decide(const SmmArgs& a, cudaStream_t st, bool first) {
     const int grid = query_grid(a.nq);
     (void)first;
+    const size_t smem = (a.policy == 1 && a.mlp_w) ? kMlpStaged * sizeof(float) : 0;
     prof_begin(FAM_SMM_DECIDE, st);
-    smm_decide_kernel<<<grid, kQueryCta, 0, st>>>(a);
+    smm_decide_kernel<<<grid, kQueryCta, smem, st>>>(a);
     prof_end(FAM_SMM_DECIDE, st);
     note_launches(1);
 }
