@@ -40,7 +40,7 @@ SPMM_TRAFFIC: dict = {("c2", 128): 6_261_000_000 + 501_000_000}
 # DRAM bytes per walk step of amc_walk (ncu one-pass DRAM counters over the 5 AMC launches of the
 # workload's batch, divided by their walk steps). A workload missing here, or a kernel changed
 # since its capture, reports its traffic as null.
-WALK_TRAFFIC_PER_STEP: dict = {"c2": (571_255_000 + 4_224_000) / 18_505_638}
+WALK_TRAFFIC_PER_STEP: dict = {"c2": (278_108_160 + 3_887_104) / 18_505_638}
 
 
 def _peaks():
