@@ -33,6 +33,11 @@ namespace geer {
 #define GEER_WALKS_PER_LANE 1
 #endif
 constexpr int kWalksPerLane = GEER_WALKS_PER_LANE;
+// chunks a warp takes per ticket (one atomic on the shared ticket counter each)
+#ifndef GEER_CHUNKS_PER_TICKET
+#define GEER_CHUNKS_PER_TICKET 1
+#endif
+constexpr int kChunksPerTicket = GEER_CHUNKS_PER_TICKET;
 
 // Row start and degree of node w.
 __device__ __forceinline__ uint2 node_row(const DevGraph& g, int32_t w) {
@@ -288,11 +293,10 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
                 if (act[i]) cs += walk_hash(w[i], k[i], sigma, batch);
             }
         } else if (act[0]) {
-            for (int j = 1; j <= lf; ++j) {
+            // step j: Philox word (j-1)&3 (one generator call per 4 steps) picks the
+            // next node among the current node's neighbours
+            auto pick = [&](int j, int32_t (&nx)[W]) {
                 const int sub = (j - 1) & 3;
-                int32_t nx[W];
-                uint32_t hh[W];
-                int4 pr[W];
 #pragma unroll
                 for (int i = 0; i < W; ++i) {
                     if (sub == 0 && act[i])
@@ -304,8 +308,15 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
                     else
                         nx[i] = act[i] ? __ldg(row_base(g, w[i], inf[i]) + __umulhi(d, inf[i].y)) : start;
                 }
-                // next row records and first probes (or dense values), all independent
-                if (mask >= 0) {
+            };
+            // one loop per value source, so the loop the warp runs holds only its own code
+            if (mask >= 0) {
+                for (int j = 1; j <= lf; ++j) {
+                    int32_t nx[W];
+                    uint32_t hh[W];
+                    int4 pr[W];
+                    pick(j, nx);
+                    // next row records and first probes, all independent
 #pragma unroll
                     for (int i = 0; i < W; ++i) {
                         hh[i] = hash32((uint32_t)nx[i]) & (uint32_t)mask;
@@ -317,7 +328,11 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
                         if (act[i]) z[i] += resolve_g(tab, mask, nx[i], pr[i], hh[i], a.err_flag);
                         w[i] = nx[i];
                     }
-                } else {
+                }
+            } else {
+                for (int j = 1; j <= lf; ++j) {
+                    int32_t nx[W];
+                    pick(j, nx);
 #pragma unroll
                     for (int i = 0; i < W; ++i) {
                         double xs, xt;
@@ -441,11 +456,12 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
         return;
     }
     for (;;) {
-        // chunks are handed out in order by a ticket counter
+        // chunks are handed out in order by a ticket counter, kChunksPerTicket at a time
         unsigned long long ticket = 0;
-        if (lane == 0) ticket = atomicAdd(a.walk_ctr, 1ull);
-        const int64_t c = (int64_t)__shfl_sync(0xffffffffu, ticket, 0);
-        if (c >= total) break;
+        if (lane == 0) ticket = atomicAdd(a.walk_ctr, (unsigned long long)kChunksPerTicket);
+        const int64_t c0 = (int64_t)__shfl_sync(0xffffffffu, ticket, 0);
+        if (c0 >= total) break;
+      for (int64_t c = c0; c < c0 + kChunksPerTicket && c < total; ++c) {
         // owning query: last q with chunk_begin[q] <= c
         int lo = 0, hi = a.nq + 1;
         while (lo < hi) {
@@ -463,6 +479,7 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
             p.cs = cs;
             a.partial[c] = p;
         }
+      }
     }
 }
 

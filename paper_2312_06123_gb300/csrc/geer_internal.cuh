@@ -180,10 +180,14 @@ __device__ __forceinline__ int32_t packed_col(const uint4* cols, uint32_t e) {
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
 // ---------------------------------------------------------------------------
+#ifndef GEER_PHILOX_UNROLL
+#define GEER_PHILOX_UNROLL 10
+#endif
+constexpr int kPhiloxUnroll = GEER_PHILOX_UNROLL;  // rounds unrolled (code size of the walk loop)
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     constexpr uint32_t kMul0 = 0xD2511F53u, kMul1 = 0xCD9E8D57u;
     constexpr uint32_t kWeyl0 = 0x9E3779B9u, kWeyl1 = 0xBB67AE85u;
-#pragma unroll
+#pragma unroll kPhiloxUnroll
     for (int r = 0; r < 10; ++r) {
         uint32_t lo0 = kMul0 * c.x, hi0 = __umulhi(kMul0, c.x);
         uint32_t lo1 = kMul1 * c.z, hi1 = __umulhi(kMul1, c.z);
