@@ -146,7 +146,10 @@ __device__ void schedule_first(const AmcArgs& a, int nb) {
 // Batches walked together at the start (when cheap), and the walk steps
 // below which they are: the speculative batches cost at most this much, the
 // launches they save are latency-bound.
-constexpr int kAmcGroup = 3;
+#ifndef GEER_AMC_GROUP
+#define GEER_AMC_GROUP 3
+#endif
+constexpr int kAmcGroup = GEER_AMC_GROUP;
 constexpr int64_t kAmcGroupSteps = (int64_t)1 << 25;
 
 // First layout of a batch's AMC: walk batches 1..kAmcGroup in one launch
