@@ -263,6 +263,8 @@ def fit(G, s, t, eps, log: CostLog, options=None, kappas=(8.0, 32.0, 128.0), epo
         for k in kappas:
             for mu in mus:
                 lg = price(log.inputs, log.push, log.walks, log.ell, k, mu, log.inputs0 if at_start else None)
+                if lg.feats.shape[0] < min_rows:  # (e.g. no decision after an iteration: l <= 1)
+                    continue
                 model = train(lg, epochs=epochs, seed=seed)
                 model.at_start = at_start
                 G.set_switch_mlp(model.norm, model.weights)
@@ -270,6 +272,8 @@ def fit(G, s, t, eps, log: CostLog, options=None, kappas=(8.0, 32.0, 128.0), epo
                 times[f"kappa={k:g}" + (f",mu={mu:g}" if mu else "") + (",from l_b=0" if at_start else "")] = tk
                 cands.append((k * (1.0 + mu) * (0.5 if at_start else 1.0), tk, model))
     G.set_switch_mlp(None, None)
+    if not cands:
+        return None, times
     # the fastest network, where times within tie_tol of it count as ties that
     # go to the dearest prices (the network that pushes least: a query pushed
     # into a hub-heavy frontier costs far more than any walks it saves)
