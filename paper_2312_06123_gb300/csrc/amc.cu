@@ -46,6 +46,14 @@ __device__ __forceinline__ uint2 node_row(const DevGraph& g, int32_t w) {
     return make_uint2((uint32_t)rs, (uint32_t)(__ldg(g.row_ptr + w + 1) - rs));
 }
 
+// node_row when the node records are known to exist (the packed neighbour
+// lists, K > 0, are built only with them)
+template <int K>
+__device__ __forceinline__ uint2 node_row_k(const DevGraph& g, int32_t w) {
+    if constexpr (K > 0) return __ldg(g.node_info + w);
+    else return node_row(g, w);
+}
+
 __device__ __forceinline__ const int32_t* row_base(const DevGraph& g, int32_t w, uint2 info) {
     // node_info holds the low 32 bits of the row start (nnz < 2^32); otherwise
     // re-read the full 64-bit start
@@ -314,22 +322,70 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
             };
             // one loop per value source, so the loop the warp runs holds only its own code
             if (mask >= 0) {
-                for (int j = 1; j <= lf; ++j) {
+                // one step with draw d[i]: the neighbour, then its row record
+                // and first lookup probe (independent loads), then g of it
+                auto step = [&](const uint32_t (&d)[W]) {
                     int32_t nx[W];
                     uint32_t hh[W];
                     int4 pr[W];
-                    pick(j, nx);
-                    // next row records and first probes, all independent
+#pragma unroll
+                    for (int i = 0; i < W; ++i) {
+                        if (K > 0)
+                            nx[i] = act[i] ? packed_col<K>(g.cols_packed, inf[i].x + __umulhi(d[i], inf[i].y)) : start;
+                        else
+                            nx[i] = act[i] ? __ldg(row_base(g, w[i], inf[i]) + __umulhi(d[i], inf[i].y)) : start;
+                    }
 #pragma unroll
                     for (int i = 0; i < W; ++i) {
                         hh[i] = hash32((uint32_t)nx[i]) & (uint32_t)mask;
                         pr[i] = __ldg(reinterpret_cast<const int4*>(tab + hh[i]));
-                        if (act[i]) inf[i] = node_row(g, nx[i]);
+                        if (act[i]) inf[i] = node_row_k<K>(g, nx[i]);
                     }
 #pragma unroll
                     for (int i = 0; i < W; ++i) {
                         if (act[i]) z[i] += resolve_g(tab, mask, nx[i], pr[i], hh[i], a.err_flag);
                         w[i] = nx[i];
+                    }
+                };
+                auto block = [&](int j) {  // the Philox block of steps j .. j + 3
+#pragma unroll
+                    for (int i = 0; i < W; ++i)
+                        if (act[i])
+                            r[i] = philox4x32_10(
+                                make_uint4((uint32_t)k[i], lane_ctr, (uint32_t)qidx, (uint32_t)((j - 1) >> 2)), key);
+                };
+                uint32_t d[W];
+                // four steps per block, each taking its word of the block
+                int j = 1;
+                for (; j + 3 <= lf; j += 4) {
+                    block(j);
+#pragma unroll
+                    for (int i = 0; i < W; ++i) d[i] = r[i].x;
+                    step(d);
+#pragma unroll
+                    for (int i = 0; i < W; ++i) d[i] = r[i].y;
+                    step(d);
+#pragma unroll
+                    for (int i = 0; i < W; ++i) d[i] = r[i].z;
+                    step(d);
+#pragma unroll
+                    for (int i = 0; i < W; ++i) d[i] = r[i].w;
+                    step(d);
+                }
+                if (j <= lf) {  // the last 1-3 steps
+                    block(j);
+#pragma unroll
+                    for (int i = 0; i < W; ++i) d[i] = r[i].x;
+                    step(d);
+                    if (j + 1 <= lf) {
+#pragma unroll
+                        for (int i = 0; i < W; ++i) d[i] = r[i].y;
+                        step(d);
+                    }
+                    if (j + 2 <= lf) {
+#pragma unroll
+                        for (int i = 0; i < W; ++i) d[i] = r[i].z;
+                        step(d);
                     }
                 }
             } else {
@@ -465,16 +521,26 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
         const int64_t c0 = (int64_t)__shfl_sync(0xffffffffu, ticket, 0);
         if (c0 >= total) break;
       for (int64_t c = c0; c < c0 + kChunksPerTicket && c < total; ++c) {
-        // owning query: last q with chunk_begin[q] <= c
-        int lo = 0, hi = a.nq + 1;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (cb_arr(mid) <= c) lo = mid + 1; else hi = mid;
+        // owning query: the last q with chunk_begin[q] <= c, by a 32-way warp
+        // search (two rounds for up to 1,024 queries): the answer lies in
+        // [lo, lo + span); each round the lanes test 32 evenly spaced entries
+        // (non-decreasing, so the passing lanes are a prefix) and keep the
+        // interval after the last passing one
+        int lo = 0, span = (int)a.nq;
+        while (span > 1) {
+            const int step = (span + 31) >> 5;
+            const int pos = lo + (lane + 1) * step;
+            const bool ok = pos < lo + span && cb_arr(pos) <= c;
+            const int pass = __popc(__ballot_sync(0xffffffffu, ok));
+            const int nlo = lo + pass * step;
+            span = min(step, lo + span - nlo);
+            lo = nlo;
         }
-        const WalkQ* WQ = a.wq + (lo - 1);
+        const int owner = lo;
+        const WalkQ* WQ = a.wq + owner;
         double sz, sz2;
         uint64_t cs;
-        walk_chunk<W, REC, K>(a, WQ, c - cb_arr(lo - 1), WQ->eta, a.batch, nbatch, lane, &sz, &sz2, &cs);
+        walk_chunk<W, REC, K>(a, WQ, c - cb_arr(owner), WQ->eta, a.batch, nbatch, lane, &sz, &sz2, &cs);
         if (lane == 0) {
             Partial p;
             p.sz = sz;

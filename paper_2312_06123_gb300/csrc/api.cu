@@ -1160,10 +1160,12 @@ int ger_load_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int 
             cudaGetLastError();
             g->edge_rec = nullptr;
         }
-        // the walks' packed neighbour lists (GEER_PACKED_COLS=0 keeps col_idx)
+        // the walks' packed neighbour lists (GEER_PACKED_COLS=0 keeps col_idx);
+        // their entries are addressed from the node records' 32-bit first
+        // edge, so they exist only with the node records (nnz < 2^32)
         const char* pk_env = std::getenv("GEER_PACKED_COLS");
         const int pk = pack_k_for(n);
-        if (pk > 0 && !(pk_env && pk_env[0] == '0')) {
+        if (pk > 0 && g->node_info && !(pk_env && pk_env[0] == '0')) {
             const int64_t units = (g->nnz + pk - 1) / pk;
             if (cudaMalloc(&g->cols_packed, (size_t)std::max<int64_t>(units, 1) * sizeof(uint4)) == cudaSuccess) {
                 launch_pack_cols(g->col_idx, g->nnz, pk, g->cols_packed, g->stream);

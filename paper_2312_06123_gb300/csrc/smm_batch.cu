@@ -268,6 +268,12 @@ __device__ __forceinline__ void leave_smm(const SmmArgs& a, int64_t q, QState* Q
 // table for at most min(push pairs, n) nodes at load <= 1/2, bump-allocated
 // from the pool. Returns false (query failed) when the table is beyond the
 // option's limit or the pool.
+#ifndef GEER_TABLE_SPREAD
+#define GEER_TABLE_SPREAD 4
+#endif
+constexpr int64_t kTableSpread = GEER_TABLE_SPREAD;  // slots per possible entry of a small table
+constexpr int64_t kSpreadMost = 1024;                // tables of at most this many entries are spread
+
 __device__ __forceinline__ bool continue_smm(const SmmArgs& a, int64_t q, QState* Q, QSmm* M, int64_t lb,
                                              unsigned long long push_pairs) {
     if (M->dense) {
@@ -293,7 +299,15 @@ __device__ __forceinline__ bool continue_smm(const SmmArgs& a, int64_t q, QState
     }
     int64_t cap = 16;
     const int64_t most = min((int64_t)push_pairs, (int64_t)a.g.n);
-    while (cap < 2 * most) cap <<= 1;
+    // small tables are spread to a lower load: the walks look up mostly
+    // absent nodes, and an unsuccessful linear-probing search takes about
+    // (1 + 1/(1 - load)^2) / 2 probes (a warp waits for its longest one)
+    const int64_t spread = most <= kSpreadMost ? kTableSpread : 2;
+    while (cap < spread * most) cap <<= 1;
+    if (cap > a.max_table && spread > 2) {
+        cap = 16;
+        while (cap < 2 * most) cap <<= 1;
+    }
     if (cap > a.max_table) {
         Q->status = ST_ERROR;
         Q->err = DERR_CAPACITY;
