@@ -233,6 +233,7 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
     const int32_t start = sigma ? WQ->t : WQ->s;
     const GEntry* tab = a.pool + WQ->table_off;
     const int32_t mask = WQ->mask;
+    const uint32_t* filt = WQ->filt;
     // dense-engine queries: (s*, t*) read directly from their block column
     const char* dvals = reinterpret_cast<const char*>(WQ->dvals);
     const int64_t dstride = WQ->dstride;
@@ -258,7 +259,10 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
             inf[i] = start_info;
             r[i] = make_uint4(0, 0, 0, 0);
         }
-        if (REC && act[0] && mask >= 0) {
+        // every lane of the warp takes the same branch (REC and mask are the
+        // chunk's), so warp-wide shuffles inside it are converged; lanes past
+        // the chunk's last pair (act false) only predicate their loads off
+        if (REC && mask >= 0) {
             // one dependent load per step: the edge record of the chosen
             // neighbour carries that neighbour's row; the lookup probe of
             // step j is resolved during step j + 1's load. The W walks of
@@ -303,7 +307,7 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
                 w[i] = pnx[i];
                 if (act[i]) cs += walk_hash(w[i], k[i], sigma, batch);
             }
-        } else if (act[0]) {
+        } else {
             // step j: Philox word (j-1)&3 (one generator call per 4 steps) picks the
             // next node among the current node's neighbours
             auto pick = [&](int j, int32_t (&nx)[W]) {
@@ -314,7 +318,7 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
                         r[i] = philox4x32_10(
                             make_uint4((uint32_t)k[i], lane_ctr, (uint32_t)qidx, (uint32_t)((j - 1) >> 2)), key);
                     const uint32_t d = sub == 0 ? r[i].x : (sub == 1 ? r[i].y : (sub == 2 ? r[i].z : r[i].w));
-                    if (K > 0)  // packed neighbour lists: entry first edge + pick
+                    if constexpr (K > 0)  // packed neighbour lists: entry first edge + pick
                         nx[i] = act[i] ? packed_col<K>(g.cols_packed, inf[i].x + __umulhi(d, inf[i].y)) : start;
                     else
                         nx[i] = act[i] ? __ldg(row_base(g, w[i], inf[i]) + __umulhi(d, inf[i].y)) : start;
@@ -322,28 +326,36 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
             };
             // one loop per value source, so the loop the warp runs holds only its own code
             if (mask >= 0) {
+                // lane l holds word l of the lookup table's membership filter
+                const uint32_t fw = filt ? __ldg(filt + lane) : 0xffffffffu;
                 // one step with draw d[i]: the neighbour, then its row record
-                // and first lookup probe (independent loads), then g of it
+                // and, where its filter bit is set, the first lookup probe
+                // (independent loads), then g of it
                 auto step = [&](const uint32_t (&d)[W]) {
                     int32_t nx[W];
                     uint32_t hh[W];
                     int4 pr[W];
+                    bool look[W];
 #pragma unroll
                     for (int i = 0; i < W; ++i) {
-                        if (K > 0)
+                        if constexpr (K > 0)
                             nx[i] = act[i] ? packed_col<K>(g.cols_packed, inf[i].x + __umulhi(d[i], inf[i].y)) : start;
                         else
                             nx[i] = act[i] ? __ldg(row_base(g, w[i], inf[i]) + __umulhi(d[i], inf[i].y)) : start;
                     }
 #pragma unroll
                     for (int i = 0; i < W; ++i) {
-                        hh[i] = hash32((uint32_t)nx[i]) & (uint32_t)mask;
-                        pr[i] = __ldg(reinterpret_cast<const int4*>(tab + hh[i]));
+                        const uint32_t hv = hash32((uint32_t)nx[i]);
+                        hh[i] = hv & (uint32_t)mask;
+                        const uint32_t fb = filter_bit(hv);
+                        const uint32_t fword = __shfl_sync(0xffffffffu, fw, (int)(fb >> 5));
+                        look[i] = act[i] && ((fword >> (fb & 31u)) & 1u);
+                        pr[i] = look[i] ? __ldg(reinterpret_cast<const int4*>(tab + hh[i])) : make_int4(-1, 0, 0, 0);
                         if (act[i]) inf[i] = node_row_k<K>(g, nx[i]);
                     }
 #pragma unroll
                     for (int i = 0; i < W; ++i) {
-                        if (act[i]) z[i] += resolve_g(tab, mask, nx[i], pr[i], hh[i], a.err_flag);
+                        if (look[i]) z[i] += resolve_g(tab, mask, nx[i], pr[i], hh[i], a.err_flag);
                         w[i] = nx[i];
                     }
                 };

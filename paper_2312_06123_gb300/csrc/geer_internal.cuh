@@ -75,7 +75,7 @@ struct __align__(16) GEntry {
 };
 
 // Per-query scratch of the SMM phase (device memory), reset by each decision.
-struct QSmm {
+struct __align__(16) QSmm {
     int32_t run;                 // 1 while SMM iterations continue
     int32_t shift_s, shift_t;    // fixed-point scales 2^shift of s*, t*
     int32_t lb_target;           // iterations wanted by a fixed policy, -1: rule
@@ -93,6 +93,9 @@ struct QSmm {
     unsigned long long cnt1s, cnt1t;                // entries equal to max1
     double sval[4];              // s*(s), t*(s), s*(t), t*(t)
     double inv_ds, inv_dt;       // 1/d(s), 1/d(t)
+    // membership filters of the tables of iterations with parity 0 and 1
+    // (tables of at most kFilterSlots slots; see filter_bit)
+    uint32_t filt[2][32];
 };
 
 // Control block of the SMM phase (device memory, zeroed before a batch).
@@ -131,7 +134,7 @@ struct __align__(16) WalkQ {
     int32_t mask, dstride;
     const void* dvals;        // ... or the query's dense column (mask < 0)
     double inv_ds, inv_dt;
-    int64_t pad;
+    const uint32_t* filt;     // membership filter of the lookup table (null: none)
 };
 
 // Per-chunk partial sums of the walk kernel.
@@ -220,6 +223,16 @@ __device__ __forceinline__ uint32_t hash32(uint32_t h) {
     h ^= h >> 16;
     return h;
 }
+
+// Membership filter of a small frontier table: 1,024 bits, one 32-bit word
+// per lane of a warp, with bit filter_bit(v) set for every node v of the
+// table. A walk step whose node's bit is clear skips the lookup (g = 0: the
+// node is outside the support) -- most of a short SMM's walk nodes are. The
+// bit comes from the top ten bits of the node's hash, the table slot from
+// its low bits (tables with a filter have at most 2^12 slots).
+constexpr int kFilterWords = 32;
+constexpr int64_t kFilterSlots = 4096;
+__device__ __forceinline__ uint32_t filter_bit(uint32_t hash) { return hash >> 22; }
 
 __device__ __forceinline__ unsigned lanemask_lt() {
     unsigned m;

@@ -257,6 +257,7 @@ __device__ __forceinline__ void leave_smm(const SmmArgs& a, int64_t q, QState* Q
         wr->dvals = Q->dense_vals;
         wr->inv_ds = 1.0 / (double)Q->ds;
         wr->inv_dt = 1.0 / (double)Q->dt;
+        wr->filt = (!M->dense && M->tab_cap <= kFilterSlots) ? M->filt[lb & 1] : nullptr;
     } else {
         Q->status = ST_DONE;
         Q->r = Q->r_b;
@@ -327,6 +328,10 @@ __device__ __forceinline__ bool continue_smm(const SmmArgs& a, int64_t q, QState
     M->ntab_off = off;
     M->ntab_cap = cap;
     M->run = 1;
+    // the next table's filter starts empty (its finish sets the bits)
+    uint4* fz = reinterpret_cast<uint4*>(M->filt[(lb + 1) & 1]);
+#pragma unroll
+    for (int k = 0; k < kFilterWords / 4; ++k) fz[k] = make_uint4(0u, 0u, 0u, 0u);
     atomicAdd(&a.ctl->n_want, 1);
     return true;
 }
@@ -389,6 +394,13 @@ __global__ void smm_start_kernel(SmmArgs a) {
         yt[off + ht] = T(1);
         M->tab_off = off;
         M->tab_cap = kF0Slots;
+        // F_0's filter: s and t
+        uint4* fz = reinterpret_cast<uint4*>(M->filt[0]);
+#pragma unroll
+        for (int k = 0; k < kFilterWords / 4; ++k) fz[k] = make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t bs = filter_bit(hash32((uint32_t)Q->s)), bt = filter_bit(hash32((uint32_t)Q->t));
+        M->filt[0][bs >> 5] |= 1u << (bs & 31u);
+        M->filt[0][bt >> 5] |= 1u << (bt & 31u);
         // Algorithm 2 at i = 0: s*(s)/d(s) + t*(t)/d(t) - s*(t)/d(s) - t*(s)/d(t)
         Q->r_b = 1.0 / ds + 1.0 / dt - 0.0 / ds - 0.0 / dt;
         const int64_t ell = Q->ell;
@@ -527,6 +539,10 @@ __global__ void __launch_bounds__(256) smm_finish_kernel(SmmArgs a) {
                     yt[j] = t_v;
                     a.ent[j].g = (double)s_v * M->inv_ds - (double)t_v * M->inv_dt;
                     const uint32_t bits = e.bits & 3u;
+                    if (M->ntab_cap <= kFilterSlots) {  // the table's membership filter
+                        const uint32_t fb = filter_bit(hash32((uint32_t)v));
+                        atomicOr(&M->filt[parity][fb >> 5], 1u << (fb & 31u));
+                    }
                     vp = (unsigned long long)(dv * (int64_t)((bits & 1u) + ((bits >> 1) & 1u)));
                     vu = (unsigned long long)dv;
                     cnt = 1;
