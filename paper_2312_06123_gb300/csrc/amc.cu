@@ -60,6 +60,13 @@ __device__ __forceinline__ const int32_t* row_base(const DevGraph& g, int32_t w,
     return g.node_info ? g.col_idx + info.x : g.col_idx + __ldg(g.row_ptr + w);
 }
 
+// Chunks per query and batch when a launch walks nb batches (the common
+// counts without a run-time 64-bit division).
+__device__ __forceinline__ int64_t max_chunks(int nb) {
+    return nb == 1 ? kMaxChunksPerQuery
+                   : (nb == 2 ? kMaxChunksPerQuery / 2 : (nb == 3 ? kMaxChunksPerQuery / 3 : kMaxChunksPerQuery / nb));
+}
+
 // Walk pairs per chunk and chunk count of a batch of eta walk pairs, at
 // most maxc chunks (a chunk is a whole number of warp rounds).
 __device__ __forceinline__ void chunk_layout(int64_t eta, int64_t maxc, int64_t* ppc, int64_t* nch) {
@@ -87,7 +94,7 @@ __device__ void schedule_cta(const AmcArgs& a, int nb) {
     const int tid = threadIdx.x;
     if (tid == 0) carry = 0;
     __syncthreads();
-    const int64_t maxc = kMaxChunksPerQuery / nb;
+    const int64_t maxc = max_chunks(nb);
     for (int64_t tile = 0; tile < a.nq; tile += kCta) {
         const int64_t q = tile + tid;
         int64_t nch = 0;
@@ -128,7 +135,7 @@ constexpr int kSmemChunkBegin = 4096;
 // query in AMC over the launch's batches (nb of them), its walk record's
 // eta, and a fresh ticket counter.
 __device__ void count_cta(const AmcArgs& a, int nb) {
-    const int64_t maxc = kMaxChunksPerQuery / nb;
+    const int64_t maxc = max_chunks(nb);
     for (int64_t q = threadIdx.x; q < a.nq; q += blockDim.x) {
         int32_t nch = 0;
         const QState* Q = a.st + q;
@@ -208,7 +215,7 @@ __device__ __forceinline__ double resolve_g(const GEntry* tab, int32_t mask, int
 
 // Walks of chunk L of query WQ in a launch that walks its batches batch0 ..
 // batch0 + nbatch - 1 (eta pairs in batch0, doubling), chunked by chunk_layout at
-// kMaxChunksPerQuery / nbatch chunks per batch. Returns the chunk's sums of
+// max_chunks(nbatch) chunks per batch. Returns the chunk's sums of
 // Z_k, Z_k^2 and the walk checksum, reduced over the warp.
 template <int W, bool REC, int K>
 __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, int64_t L, int64_t eta, int batch0,
@@ -216,7 +223,7 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
     const int sigma = lane & 1;
     const uint2 key = make_uint2((uint32_t)a.seed, (uint32_t)(a.seed >> 32));
     const DevGraph g = a.g;
-    const int64_t maxc = kMaxChunksPerQuery / nbatch;
+    const int64_t maxc = max_chunks(nbatch);
     // which of the unit's batches this chunk belongs to, and its place in it
     int64_t ppc, nchb;
     int bi = 0;
@@ -487,7 +494,7 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
     // (small batches), else laid out by the schedule
     const bool staged = a.nq + 1 <= kSmemChunkBegin;
     if (staged) {
-        const int64_t maxc = kMaxChunksPerQuery / nbatch;
+        const int64_t maxc = max_chunks(nbatch);
         int64_t carry = 0;
         for (int64_t tile = 0; tile < a.nq; tile += kCta) {
             const int64_t q = tile + threadIdx.x;
@@ -564,24 +571,6 @@ __global__ void __launch_bounds__(256, GEER_WALK_MINB) amc_walk_kernel(AmcArgs a
     }
 }
 
-// Sums of Z_k, Z_k^2 and the walk checksum over one batch of one query, from
-// its nch chunk partials at `begin`, in a fixed order (lane-strided, then a
-// warp reduction). The whole warp calls it; every lane gets the sums.
-__device__ __forceinline__ void batch_sums(const AmcArgs& a, int64_t begin, int64_t nch, int lane, double* sz,
-                                           double* sz2, uint64_t* cs) {
-    double x = 0.0, x2 = 0.0;
-    uint64_t c = 0;
-    for (int64_t i = lane; i < nch; i += 32) {
-        const Partial p = a.partial[begin + i];
-        x += p.sz;
-        x2 += p.sz2;
-        c += p.cs;
-    }
-    *sz = warp_sum(x);
-    *sz2 = warp_sum(x2);
-    *cs = warp_sum(c);
-}
-
 // Queries per CTA of the statistics kernel, one per warp for the partial
 // sums (their loads are a latency chain per query); the per-query scalar FP64
 // work (Eq. (7): divisions, a logarithm, a square root) then runs one query
@@ -612,26 +601,54 @@ __global__ void __launch_bounds__(kCta) amc_reduce_kernel(AmcArgs a) {
         return;
     }
     const int nbatch = a.batch == 1 ? group : 1;
-    const int64_t maxc = kMaxChunksPerQuery / nbatch;
+    const int64_t maxc = max_chunks(nbatch);
     const bool staged = a.nq + 1 <= kSmemChunkBegin;
-    // the batches' sums, one query per warp at a time
+    // the batches' sums, one query per warp at a time; the first partial of
+    // every lane and batch is loaded before any is added (one round trip for
+    // the usual batch of at most 32 chunks), the rest lane-strided, then a
+    // warp reduction per batch
     for (int j = warp; j < kReduceQ; j += kWarps) {
         const int64_t q = q0 + j;
         if (q >= a.nq || a.st[q].status != ST_AMC) continue;
-        int64_t begin = a.chunk_begin[q], eta = a.st[q].eta;
-        for (int bi = 0; bi < nbatch; ++bi) {
-            int64_t ppc, nch;
-            chunk_layout(eta, maxc, &ppc, &nch);
-            double sz, sz2;
-            uint64_t cs;
-            batch_sums(a, begin, nch, lane, &sz, &sz2, &cs);
-            if (lane == 0) {
-                s_sz[bi][j] = sz;
-                s_sz2[bi][j] = sz2;
-                s_cs[bi][j] = cs;
+        int64_t begin[kAmcGroup], nch[kAmcGroup];
+        {
+            int64_t b = a.chunk_begin[q], eta = a.st[q].eta;
+#pragma unroll
+            for (int bi = 0; bi < kAmcGroup; ++bi) {
+                int64_t ppc = 0, n = 0;
+                if (bi < nbatch) chunk_layout(eta, maxc, &ppc, &n);
+                begin[bi] = b;
+                nch[bi] = n;
+                b += n;
+                eta *= 2;
             }
-            begin += nch;
-            eta *= 2;
+        }
+        Partial first[kAmcGroup];
+#pragma unroll
+        for (int bi = 0; bi < kAmcGroup; ++bi) {
+            first[bi].sz = first[bi].sz2 = 0.0;
+            first[bi].cs = 0ull;
+            if (lane < nch[bi]) first[bi] = a.partial[begin[bi] + lane];
+        }
+#pragma unroll
+        for (int bi = 0; bi < kAmcGroup; ++bi) {
+            if (bi >= nbatch) break;
+            double x = first[bi].sz, x2 = first[bi].sz2;
+            uint64_t c = first[bi].cs;
+            for (int64_t i = lane + 32; i < nch[bi]; i += 32) {
+                const Partial p = a.partial[begin[bi] + i];
+                x += p.sz;
+                x2 += p.sz2;
+                c += p.cs;
+            }
+            x = warp_sum(x);
+            x2 = warp_sum(x2);
+            c = warp_sum(c);
+            if (lane == 0) {
+                s_sz[bi][j] = x;
+                s_sz2[bi][j] = x2;
+                s_cs[bi][j] = c;
+            }
         }
     }
     __syncthreads();
@@ -639,8 +656,7 @@ __global__ void __launch_bounds__(kCta) amc_reduce_kernel(AmcArgs a) {
         const int64_t q = q0 + lane;
         QState* Q = a.st + q;
         if (q < a.nq && Q->status == ST_AMC) {
-            const double delta_b = a.delta / (double)a.tau;
-            const double Lg = log(3.0 / delta_b);
+            const double Lg = a.log_3tau_delta;  // log(3 / (delta / tau)), Eq. (7) at delta / tau
             const double psi = Q->psi, qeps = Q->eps, r_b = Q->r_b;
             const int32_t lf = Q->lf;
             int64_t eta = Q->eta, walks = Q->walks, steps = Q->walk_steps;
@@ -648,10 +664,11 @@ __global__ void __launch_bounds__(kCta) amc_reduce_kernel(AmcArgs a) {
             bool stop = false;
             for (int bi = 0; bi < nbatch && !stop; ++bi) {
                 const int batch = a.batch + bi;
-                const double Z = s_sz[bi][lane] / (double)eta;
-                double var = s_sz2[bi][lane] / (double)eta - Z * Z;
+                const double inv = 1.0 / (double)eta;
+                const double Z = s_sz[bi][lane] * inv;
+                double var = s_sz2[bi][lane] * inv - Z * Z;
                 if (var < 0.0) var = 0.0;
-                const double f = sqrt(2.0 * var * Lg / (double)eta) + 3.0 * psi * Lg / (double)eta;
+                const double f = sqrt(2.0 * var * Lg * inv) + 3.0 * psi * Lg * inv;
                 walks += eta;
                 steps += 2 * eta * (int64_t)lf;
                 chk += s_cs[bi][lane];

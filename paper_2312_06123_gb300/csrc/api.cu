@@ -653,6 +653,7 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
     m.seed = p.o.seed;
     m.tau = p.o.tau;
     m.delta = p.o.delta;
+    m.log_3tau_delta = std::log(3.0 * (double)m.tau / m.delta);
     m.dense_fp64 = fp64;
     m.err_flag = w.counters + 1;
 }

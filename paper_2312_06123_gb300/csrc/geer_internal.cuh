@@ -371,9 +371,19 @@ __device__ __forceinline__ void switch_features(const QState* Q, const QSmm* M, 
 // 16-byte FP16 vectors).
 constexpr int kMlpStaged = (kMlpParams + 7) / 8 * 8;
 
+// Where parameter p sits in the staged copy: W1 and W2 transposed (input k
+// of unit j at k * 64 + j), so the lanes of a warp evaluating units j and
+// j + 32 read consecutive floats; biases and W3 in place.
+__device__ __forceinline__ int mlp_staged_index(int p) {
+    if (p < kMlpOffB1) return kMlpOffW1 + ((p - kMlpOffW1) % kMlpIn) * kMlpH + (p - kMlpOffW1) / kMlpIn;
+    if (p >= kMlpOffW2 && p < kMlpOffB2) return kMlpOffW2 + ((p - kMlpOffW2) % kMlpH) * kMlpH + (p - kMlpOffW2) / kMlpH;
+    return p;
+}
+
 // The whole CTA converts the network's FP16 weights into FP32 in shared
 // memory (16-byte loads; the weight buffer is allocated with 16 bytes to
-// spare, so the last vector stays inside it).
+// spare, so the last vector stays inside it; the padding lands past the
+// parameters).
 __device__ __forceinline__ void mlp_stage(float* sw, const unsigned short* w) {
     const uint4* src = reinterpret_cast<const uint4*>(w);
     for (int i = threadIdx.x; i < kMlpStaged / 8; i += blockDim.x) {
@@ -382,41 +392,49 @@ __device__ __forceinline__ void mlp_stage(float* sw, const unsigned short* w) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u[e]));
-            sw[8 * i + 2 * e] = f.x;
-            sw[8 * i + 2 * e + 1] = f.y;
+            sw[mlp_staged_index(8 * i + 2 * e)] = f.x;
+            sw[mlp_staged_index(8 * i + 2 * e + 1)] = f.y;
         }
     }
 }
 
-// The network for one query, by one thread, from the staged weights (FP32
-// arithmetic; four partial sums per dot product).
-__device__ __forceinline__ float mlp_eval_staged(const float* sw, const float* norm, const float raw[kMlpIn]) {
+// The network for the query of lane `src` (its raw inputs in that lane's
+// raw[]), evaluated by the whole warp from the staged weights in FP32: lane
+// l computes hidden units l and l + 32 of both layers (four partial sums per
+// dot product of the second), the output is a warp sum. Every lane of the
+// warp must call it; every lane gets the output.
+__device__ __forceinline__ float mlp_eval_warp(const float* sw, const float* norm, const float (&raw)[kMlpIn],
+                                               int src) {
+    const int lane = threadIdx.x & 31;
     float x[kMlpIn];
 #pragma unroll
-    for (int k = 0; k < kMlpIn; ++k) x[k] = (raw[k] - __ldg(norm + k)) / __ldg(norm + kMlpIn + k);
-    float h1[kMlpH];
+    for (int k = 0; k < kMlpIn; ++k)
+        x[k] = (__shfl_sync(0xffffffffu, raw[k], src) - __ldg(norm + k)) / __ldg(norm + kMlpIn + k);
+    float a = sw[kMlpOffB1 + lane], b = sw[kMlpOffB1 + lane + 32];
 #pragma unroll
-    for (int j = 0; j < kMlpH; ++j) {
-        float z = sw[kMlpOffB1 + j];
-#pragma unroll
-        for (int k = 0; k < kMlpIn; ++k) z = fmaf(sw[kMlpOffW1 + j * kMlpIn + k], x[k], z);
-        h1[j] = fmaxf(z, 0.f);
+    for (int k = 0; k < kMlpIn; ++k) {
+        a = fmaf(sw[kMlpOffW1 + k * kMlpH + lane], x[k], a);
+        b = fmaf(sw[kMlpOffW1 + k * kMlpH + lane + 32], x[k], b);
     }
-    float y = sw[kMlpOffB3];
-#pragma unroll 4
-    for (int j = 0; j < kMlpH; ++j) {
-        const float* row = sw + kMlpOffW2 + j * kMlpH;
-        float z0 = sw[kMlpOffB2 + j], z1 = 0.f, z2 = 0.f, z3 = 0.f;
+    a = fmaxf(a, 0.f);
+    b = fmaxf(b, 0.f);
+    float za[4] = {sw[kMlpOffB2 + lane], 0.f, 0.f, 0.f};
+    float zb[4] = {sw[kMlpOffB2 + lane + 32], 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int k = 0; k < kMlpH; k += 4) {
-            z0 = fmaf(row[k], h1[k], z0);
-            z1 = fmaf(row[k + 1], h1[k + 1], z1);
-            z2 = fmaf(row[k + 2], h1[k + 2], z2);
-            z3 = fmaf(row[k + 3], h1[k + 3], z3);
+    for (int k = 0; k < kMlpH; k += 4) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const float hk = __shfl_sync(0xffffffffu, k + m < 32 ? a : b, (k + m) & 31);
+            za[m] = fmaf(sw[kMlpOffW2 + (k + m) * kMlpH + lane], hk, za[m]);
+            zb[m] = fmaf(sw[kMlpOffW2 + (k + m) * kMlpH + lane + 32], hk, zb[m]);
         }
-        y = fmaf(sw[kMlpOffW3 + j], fmaxf((z0 + z1) + (z2 + z3), 0.f), y);
     }
-    return y;
+    const float ya = fmaxf((za[0] + za[1]) + (za[2] + za[3]), 0.f);
+    const float yb = fmaxf((zb[0] + zb[1]) + (zb[2] + zb[3]), 0.f);
+    float y = fmaf(sw[kMlpOffW3 + lane], ya, sw[kMlpOffW3 + lane + 32] * yb);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+    return y + sw[kMlpOffB3];
 }
 
 // The outputs of one query (its record of the batch state): r' and, when

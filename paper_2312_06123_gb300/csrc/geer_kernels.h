@@ -109,6 +109,7 @@ struct AmcArgs {
     int32_t* group;        // batches walked by the first launch (set by the first schedule)
     int32_t dense_fp64;    // element type of dense-engine values
     double delta;
+    double log_3tau_delta;  // log(3 tau / delta): Eq. (7)'s logarithm at delta / tau
     int* err_flag;
     // the first walk launch lays out its own chunks (batches of up to
     // kSmemChunkBegin - 1 queries; no schedule launch)

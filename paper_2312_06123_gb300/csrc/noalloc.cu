@@ -15,9 +15,11 @@
 // query, each a power of two at least twice the iteration's push volume);
 // beyond them the call fails with GER_ERR_CAPACITY. The array lives in every
 // GPU that loads this module, until the process exits.
+#include <cmath>
 #include <mutex>
 
 #include "../../include/geer.h"
+
 #include "geer_internal.cuh"
 #include "geer_kernels.h"
 
@@ -211,6 +213,7 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     m.seed = o.seed;
     m.tau = o.tau;
     m.delta = o.delta;
+    m.log_3tau_delta = std::log(3.0 * (double)m.tau / m.delta);
     m.dense_fp64 = fp64;
     m.err_flag = counters + 1;
     m.group = counters + 6;  // inside the 64-byte counter region

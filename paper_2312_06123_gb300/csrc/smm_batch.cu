@@ -345,6 +345,84 @@ __device__ __forceinline__ bool continue_smm(const SmmArgs& a, int64_t q, QState
 // l >= 1, or as a fixed policy says); and the table of F_1 (whose push has
 // d(s) + d(t) pairs). Eq. (17)'s volume is d(s) + d(t) and max_1 = 1,
 // max_2 = 0 for both vectors (one non-zero entry each).
+// What the start kernel knows of a query before its first decision.
+struct StartState {
+    bool smm = false;  // the query enters the SMM loop
+    bool go = false;   // its first decision: one SMM iteration (else AMC alone)
+    bool ask = false;  // the learned switch takes that decision
+    double psi = 0.0, h = 0.0;
+    int64_t eta0 = 0, ell = 0;
+    unsigned long long vol = 0;
+    float f[kMlpIn];   // the learned switch's inputs at l_b = 0 (when ask)
+};
+
+template <typename T>
+__device__ __forceinline__ StartState start_query(const SmmArgs& a, int64_t q, bool learned) {
+    StartState S;
+    S.smm = setup_query(a, q);
+    // every F_0 table is written, so the push of iteration 1 reads no stale slot
+    const int64_t off = (int64_t)kF0Slots * q;
+    GEntry* tab = a.ent + off;
+    GEntry empty;
+    empty.v = -1;
+    empty.bits = 0u;
+    empty.g = 0.0;
+#pragma unroll
+    for (int k = 0; k < kF0Slots; ++k) tab[k] = empty;
+    if (!S.smm) return S;
+    T* ys = reinterpret_cast<T*>(a.ys);
+    T* yt = reinterpret_cast<T*>(a.yt);
+    QState* Q = a.st + q;
+    QSmm* M = a.sm + q;
+    const double ds = (double)Q->ds, dt = (double)Q->dt;
+    // linear probing in an 8-slot table, as table_insert would place them
+    const uint32_t hs = hash32((uint32_t)Q->s) & (kF0Slots - 1);
+    uint32_t ht = hash32((uint32_t)Q->t) & (kF0Slots - 1);
+    if (ht == hs) ht = (ht + 1) & (kF0Slots - 1);
+    GEntry es, et;
+    es.v = Q->s;
+    es.bits = 1u | ((uint32_t)q << 2);
+    es.g = 1.0 * M->inv_ds - 0.0 * M->inv_dt;
+    et.v = Q->t;
+    et.bits = 2u | ((uint32_t)q << 2);
+    et.g = 0.0 * M->inv_ds - 1.0 * M->inv_dt;
+    tab[hs] = es;
+    tab[ht] = et;
+    ys[off + hs] = T(1);
+    yt[off + hs] = T(0);
+    ys[off + ht] = T(0);
+    yt[off + ht] = T(1);
+    M->tab_off = off;
+    M->tab_cap = kF0Slots;
+    // F_0's filter: s and t
+    uint4* fz = reinterpret_cast<uint4*>(M->filt[0]);
+#pragma unroll
+    for (int k = 0; k < kFilterWords / 4; ++k) fz[k] = make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t bs = filter_bit(hash32((uint32_t)Q->s)), bt = filter_bit(hash32((uint32_t)Q->t));
+    M->filt[0][bs >> 5] |= 1u << (bs & 31u);
+    M->filt[0][bt >> 5] |= 1u << (bt & 31u);
+    // Algorithm 2 at i = 0: s*(s)/d(s) + t*(t)/d(t) - s*(t)/d(s) - t*(s)/d(t)
+    Q->r_b = 1.0 / ds + 1.0 / dt - 0.0 / ds - 0.0 / dt;
+    S.ell = Q->ell;
+    S.vol = (unsigned long long)Q->ds + (unsigned long long)Q->dt;
+    // Eq. (9) and h(l) at l_b = 0: max_1 = 1 and max_2 = 0 for both vectors
+    if (S.ell > 0)
+        switch_quantities(S.ell, 1.0, 0.0, 1.0, 0.0, ds, dt, Q->eps, a.delta, a.tau, &S.psi, &S.eta0, &S.h);
+    S.go = M->lb_target >= 0 ? (M->lb_target > 0) : (S.ell >= 1);  // the loop runs once when l >= 1
+    if (S.go && M->lb_target < 0 && learned) {
+        // the learned switch may stop before any SMM step (AMC alone, Algorithm 1):
+        // its inputs at l_b = 0 (those switch_features gives after an iteration)
+        S.ask = true;
+        S.f[0] = (float)log(ds);
+        S.f[1] = (float)log(dt);
+        S.f[2] = (float)S.ell;
+        S.f[3] = (float)log((double)S.vol);
+        S.f[4] = S.h > 0.0 ? (float)log(S.h) : 0.0f;
+        S.f[5] = (float)(1.0 / ds + 1.0 / dt);
+    }
+    return S;
+}
+
 template <typename T>
 __global__ void smm_start_kernel(SmmArgs a) {
     extern __shared__ float sw[];  // the staged network when it decides at l_b = 0
@@ -358,72 +436,24 @@ __global__ void smm_start_kernel(SmmArgs a) {
         mlp_stage(sw, a.mlp_w);
         __syncthreads();
     }
-    T* ys = reinterpret_cast<T*>(a.ys);
-    T* yt = reinterpret_cast<T*>(a.yt);
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < a.nq; q += (int64_t)gridDim.x * blockDim.x) {
-        const bool smm = setup_query(a, q);
-        // every F_0 table is written, so the push of iteration 1 reads no stale slot
-        const int64_t off = (int64_t)kF0Slots * q;
-        GEntry* tab = a.ent + off;
-        GEntry empty;
-        empty.v = -1;
-        empty.bits = 0u;
-        empty.g = 0.0;
-#pragma unroll
-        for (int k = 0; k < kF0Slots; ++k) tab[k] = empty;
-        if (!smm) continue;
+    // a loop of the same trip count for every thread: the network is evaluated by the whole warp
+    static_assert(kQueryCta == 32, "one warp per CTA");
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < a.nq; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = base + threadIdx.x;
+        StartState S;
+        if (q < a.nq) S = start_query<T>(a, q, learned);
+        if (learned) {
+            for (unsigned pend = __ballot_sync(0xffffffffu, S.ask); pend; pend &= pend - 1) {
+                const int src = __ffs(pend) - 1;
+                const float y = mlp_eval_warp(sw, a.mlp_norm, S.f, src);
+                if ((int)(threadIdx.x & 31) == src) S.go = y < 0.f;
+            }
+        }
+        if (!S.smm) continue;
         QState* Q = a.st + q;
         QSmm* M = a.sm + q;
-        const double ds = (double)Q->ds, dt = (double)Q->dt;
-        // linear probing in an 8-slot table, as table_insert would place them
-        const uint32_t hs = hash32((uint32_t)Q->s) & (kF0Slots - 1);
-        uint32_t ht = hash32((uint32_t)Q->t) & (kF0Slots - 1);
-        if (ht == hs) ht = (ht + 1) & (kF0Slots - 1);
-        GEntry es, et;
-        es.v = Q->s;
-        es.bits = 1u | ((uint32_t)q << 2);
-        es.g = 1.0 * M->inv_ds - 0.0 * M->inv_dt;
-        et.v = Q->t;
-        et.bits = 2u | ((uint32_t)q << 2);
-        et.g = 0.0 * M->inv_ds - 1.0 * M->inv_dt;
-        tab[hs] = es;
-        tab[ht] = et;
-        ys[off + hs] = T(1);
-        yt[off + hs] = T(0);
-        ys[off + ht] = T(0);
-        yt[off + ht] = T(1);
-        M->tab_off = off;
-        M->tab_cap = kF0Slots;
-        // F_0's filter: s and t
-        uint4* fz = reinterpret_cast<uint4*>(M->filt[0]);
-#pragma unroll
-        for (int k = 0; k < kFilterWords / 4; ++k) fz[k] = make_uint4(0u, 0u, 0u, 0u);
-        const uint32_t bs = filter_bit(hash32((uint32_t)Q->s)), bt = filter_bit(hash32((uint32_t)Q->t));
-        M->filt[0][bs >> 5] |= 1u << (bs & 31u);
-        M->filt[0][bt >> 5] |= 1u << (bt & 31u);
-        // Algorithm 2 at i = 0: s*(s)/d(s) + t*(t)/d(t) - s*(t)/d(s) - t*(s)/d(t)
-        Q->r_b = 1.0 / ds + 1.0 / dt - 0.0 / ds - 0.0 / dt;
-        const int64_t ell = Q->ell;
-        const unsigned long long vol = (unsigned long long)Q->ds + (unsigned long long)Q->dt;
-        // Eq. (9) and h(l) at l_b = 0: max_1 = 1 and max_2 = 0 for both vectors
-        double psi = 0.0, h = 0.0;
-        int64_t eta0 = 0;
-        if (ell > 0) switch_quantities(ell, 1.0, 0.0, 1.0, 0.0, ds, dt, Q->eps, a.delta, a.tau, &psi, &eta0, &h);
-        bool go = M->lb_target >= 0 ? (M->lb_target > 0) : (ell >= 1);  // the loop runs once when l >= 1
-        if (go && M->lb_target < 0 && learned) {
-            // the learned switch may stop before any SMM step (AMC alone, Algorithm 1):
-            // its inputs at l_b = 0 (those switch_features gives after an iteration)
-            float f[kMlpIn];
-            f[0] = (float)log(ds);
-            f[1] = (float)log(dt);
-            f[2] = (float)ell;
-            f[3] = (float)log((double)vol);
-            f[4] = h > 0.0 ? (float)log(h) : 0.0f;
-            f[5] = (float)(1.0 / ds + 1.0 / dt);
-            go = mlp_eval_staged(sw, a.mlp_norm, f) < 0.f;
-        }
-        if (go) continue_smm(a, q, Q, M, 0, vol);
-        else leave_smm(a, q, Q, M, 0, 0, ell, psi, (double)vol, h, eta0, 2);
+        if (S.go) continue_smm(a, q, Q, M, 0, S.vol);
+        else leave_smm(a, q, Q, M, 0, 0, S.ell, S.psi, (double)S.vol, S.h, S.eta0, 2);
     }
 }
 
@@ -700,7 +730,12 @@ __global__ void smm_decide_kernel(SmmArgs a) {
                 __syncthreads();
                 staged = true;
             }
-            if (need && mlp_eval_staged(sw, a.mlp_norm, f) >= 0.f) go = false;
+            // the network of each query that needs it, by the whole warp (the CTA)
+            for (unsigned pend = __ballot_sync(0xffffffffu, need); pend; pend &= pend - 1) {
+                const int src = __ffs(pend) - 1;
+                const float y = mlp_eval_warp(sw, a.mlp_norm, f, src);
+                if ((int)(threadIdx.x & 31) == src && y >= 0.f) go = false;
+            }
         }
         if (!active) continue;
         // the table just finished holds the current frontier
