@@ -603,6 +603,7 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
     a.lambda = g->lambda;
     a.delta = p.o.delta;
     a.tau = p.o.tau;
+    a.log_2tau_delta = std::log(2.0 * (double)a.tau / a.delta);
     a.ell_formula = p.o.ell_formula;
     a.policy = p.o.switch_policy;
     a.fixed_lb = p.o.fixed_ell_b;

@@ -310,13 +310,14 @@ __device__ __forceinline__ void warp_top2(double& a, double& b) {
 // ---------------------------------------------------------------------------
 
 // psi (Eq. 9), eta0 = max(1, ceil(eta*/2^(tau-1))) with eta* from Eq. (8),
-// h = (2^tau - 1) eta0
+// h = (2^tau - 1) eta0; log_2tau_delta = log(2 tau / delta), the same for
+// every query (computed on the host)
 __device__ __forceinline__ void switch_quantities(int64_t lf, double s1, double s2, double t1, double t2, double ds,
-                                                  double dt, double eps, double delta, int tau, double* psi,
+                                                  double dt, double eps, double log_2tau_delta, int tau, double* psi,
                                                   int64_t* eta0, double* h) {
     const double up = (double)((lf + 1) / 2), dn = (double)(lf / 2);
     const double p = 2.0 * up * (s1 / ds + t1 / dt) + 2.0 * dn * (s2 / ds + t2 / dt);
-    const double es = 2.0 * p * p * log(2.0 * (double)tau / delta) / (eps * eps);
+    const double es = 2.0 * p * p * log_2tau_delta / (eps * eps);
     int64_t e0 = (int64_t)ceil(es / ldexp(1.0, tau - 1));
     if (e0 < 1) e0 = 1;
     *psi = p;
@@ -346,25 +347,19 @@ constexpr int kMlpOffW3 = kMlpOffB2 + kMlpH;
 constexpr int kMlpOffB3 = kMlpOffW3 + kMlpH;
 constexpr int kMlpParams = kMlpOffB3 + 1;  // 4673
 
-// Raw inputs of the learned switch after SMM iteration lb (Eq. 17's state):
-// log d(s), log d(t), l - l_b, log(volume), log h(l - l_b),
-// max_1(s*)/d(s) + max_1(t*)/d(t). Returns h through *h_out.
-__device__ __forceinline__ void switch_features(const QState* Q, const QSmm* M, int64_t lb, double delta, int tau,
-                                                float f[kMlpIn], double* h_out) {
-    double s1, s2, t1, t2;
-    smm_maxima(M, &s1, &s2, &t1, &t2);
-    const double ds = (double)Q->ds, dt = (double)Q->dt;
-    const int64_t lf = (int64_t)Q->ell - lb;
-    double psi = 0.0, h = 0.0;
-    int64_t eta0 = 0;
-    if (lf > 0) switch_quantities(lf, s1, s2, t1, t2, ds, dt, Q->eps, delta, tau, &psi, &eta0, &h);
-    f[0] = (float)log(ds);
-    f[1] = (float)log(dt);
+// Raw inputs of the learned switch (the network's inputs are FP32, so they
+// are computed in FP32): log d(s), log d(t), l - l_b, log(volume), log h(l -
+// l_b) (0 when no walk is left), max_1(s*)/d(s) + max_1(t*)/d(t), from
+// Eq. (17)'s state after iteration l_b (h from switch_quantities).
+__device__ __forceinline__ void switch_features(int32_t ds, int32_t dt, int64_t lf, unsigned long long vol, double h,
+                                                double s1, double t1, float f[kMlpIn]) {
+    const float fds = (float)ds, fdt = (float)dt;
+    f[0] = logf(fds);
+    f[1] = logf(fdt);
     f[2] = (float)lf;
-    f[3] = (float)log((double)M->vol_paper);
-    f[4] = h > 0.0 ? (float)log(h) : 0.0f;
-    f[5] = (float)(s1 / ds + t1 / dt);
-    *h_out = h;
+    f[3] = logf((float)vol);
+    f[4] = h > 0.0 ? logf((float)h) : 0.0f;
+    f[5] = (float)s1 / fds + (float)t1 / fdt;
 }
 
 // Floats of the network's weights staged in shared memory (a whole number of
@@ -384,16 +379,30 @@ __device__ __forceinline__ int mlp_staged_index(int p) {
 // memory (16-byte loads; the weight buffer is allocated with 16 bytes to
 // spare, so the last vector stays inside it; the padding lands past the
 // parameters).
+// A thread's loads are issued in groups of kMlpStageGroup before any is
+// converted, so the staging waits for a few round trips, not one per vector.
+constexpr int kMlpStageGroup = 10;
 __device__ __forceinline__ void mlp_stage(float* sw, const unsigned short* w) {
+    constexpr int kVecs = kMlpStaged / 8;
     const uint4* src = reinterpret_cast<const uint4*>(w);
-    for (int i = threadIdx.x; i < kMlpStaged / 8; i += blockDim.x) {
-        const uint4 v = __ldg(src + i);
-        const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+    for (int i0 = threadIdx.x; i0 < kVecs; i0 += blockDim.x * kMlpStageGroup) {
+        uint4 v[kMlpStageGroup];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u[e]));
-            sw[mlp_staged_index(8 * i + 2 * e)] = f.x;
-            sw[mlp_staged_index(8 * i + 2 * e + 1)] = f.y;
+        for (int g = 0; g < kMlpStageGroup; ++g) {
+            const int i = i0 + g * (int)blockDim.x;
+            if (i < kVecs) v[g] = __ldg(src + i);
+        }
+#pragma unroll
+        for (int g = 0; g < kMlpStageGroup; ++g) {
+            const int i = i0 + g * (int)blockDim.x;
+            if (i >= kVecs) break;
+            const uint32_t u[4] = {v[g].x, v[g].y, v[g].z, v[g].w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u[e]));
+                sw[mlp_staged_index(8 * i + 2 * e)] = f.x;
+                sw[mlp_staged_index(8 * i + 2 * e + 1)] = f.y;
+            }
         }
     }
 }

@@ -155,6 +155,7 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     a.lambda = lambda;
     a.delta = o.delta;
     a.tau = o.tau;
+    a.log_2tau_delta = std::log(2.0 * (double)a.tau / a.delta);
     a.ell_formula = o.ell_formula;
     a.policy = o.switch_policy;
     a.fixed_lb = o.fixed_ell_b;

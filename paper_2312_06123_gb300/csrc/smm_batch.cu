@@ -407,18 +407,14 @@ __device__ __forceinline__ StartState start_query(const SmmArgs& a, int64_t q, b
     S.vol = (unsigned long long)Q->ds + (unsigned long long)Q->dt;
     // Eq. (9) and h(l) at l_b = 0: max_1 = 1 and max_2 = 0 for both vectors
     if (S.ell > 0)
-        switch_quantities(S.ell, 1.0, 0.0, 1.0, 0.0, ds, dt, Q->eps, a.delta, a.tau, &S.psi, &S.eta0, &S.h);
+        switch_quantities(S.ell, 1.0, 0.0, 1.0, 0.0, ds, dt, Q->eps, a.log_2tau_delta, a.tau, &S.psi, &S.eta0,
+                          &S.h);
     S.go = M->lb_target >= 0 ? (M->lb_target > 0) : (S.ell >= 1);  // the loop runs once when l >= 1
     if (S.go && M->lb_target < 0 && learned) {
         // the learned switch may stop before any SMM step (AMC alone, Algorithm 1):
         // its inputs at l_b = 0 (those switch_features gives after an iteration)
         S.ask = true;
-        S.f[0] = (float)log(ds);
-        S.f[1] = (float)log(dt);
-        S.f[2] = (float)S.ell;
-        S.f[3] = (float)log((double)S.vol);
-        S.f[4] = S.h > 0.0 ? (float)log(S.h) : 0.0f;
-        S.f[5] = (float)(1.0 / ds + 1.0 / dt);
+        switch_features(Q->ds, Q->dt, S.ell, S.vol, S.h, 1.0, 1.0, S.f);
     }
     return S;
 }
@@ -700,7 +696,8 @@ __global__ void smm_decide_kernel(SmmArgs a) {
             smm_maxima(M, &s1, &s2, &t1, &t2);
             vol = (double)M->vol_paper;
             lf = ell - lb;
-            if (lf > 0) switch_quantities(lf, s1, s2, t1, t2, ds, dt, Q->eps, a.delta, a.tau, &psi, &eta0, &h);
+            if (lf > 0)
+                switch_quantities(lf, s1, s2, t1, t2, ds, dt, Q->eps, a.log_2tau_delta, a.tau, &psi, &eta0, &h);
             if (iter == 0) {
                 go = M->lb_target >= 0 ? (M->lb_target > 0) : (ell >= 1);  // the loop runs once when l >= 1
             } else {
@@ -710,10 +707,8 @@ __global__ void smm_decide_kernel(SmmArgs a) {
                 const bool rule_stop = (lb >= ell) || vol > h;
                 go = M->lb_target >= 0 ? (lb < M->lb_target) : !rule_stop;
                 need = learned && M->lb_target < 0 && !rule_stop;
-                if (need || (a.trace && lb <= a.trace_steps)) {
-                    double hh;
-                    switch_features(Q, M, lb, a.delta, a.tau, f, &hh);
-                }
+                if (need || (a.trace && lb <= a.trace_steps))
+                    switch_features(Q->ds, Q->dt, lf, M->vol_paper, h, s1, t1, f);
                 if (a.trace && lb <= a.trace_steps) {
                     // cost log of the learned switch: its inputs and the next push's size
                     float* row = a.trace + ((int64_t)q * a.trace_steps + (lb - 1)) * kTraceWidth;
