@@ -38,9 +38,10 @@ WALK_STEP_BYTES = 20  # row_ptr pair 8 B + one col_idx 4 B + one (s*, t*) FP32 p
 # current kernel (dram__bytes_read.sum + dram__bytes_write.sum), per (workload, width)
 SPMM_TRAFFIC: dict = {("c2", 128): 6_261_000_000 + 501_000_000}
 # DRAM bytes per walk step of amc_walk (ncu one-pass DRAM counters over the 5 AMC launches of the
-# workload's batch, divided by their walk steps). A workload missing here, or a kernel changed
-# since its capture, reports its traffic as null.
-WALK_TRAFFIC_PER_STEP: dict = {"c2": (278_108_160 + 3_887_104) / 18_505_638}
+# workload's batch switching after one SMM iteration, the learned switch's choice on this workload,
+# divided by their walk steps). A workload missing here, or a kernel changed since its capture,
+# reports its traffic as null.
+WALK_TRAFFIC_PER_STEP: dict = {"c2": (193_202_944 + 3_296_512) / 25_144_286}
 
 
 def _peaks():
