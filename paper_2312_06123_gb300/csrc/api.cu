@@ -601,6 +601,7 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
     a.eps = p.eps ? p.eps + q0 : nullptr;
     a.eps_scalar = p.eps_scalar;
     a.lambda = g->lambda;
+    a.log_inv_lambda = a.lambda > 0.0 && a.lambda < 1.0 ? std::log(1.0 / a.lambda) : 0.0;
     a.delta = p.o.delta;
     a.tau = p.o.tau;
     a.log_2tau_delta = std::log(2.0 * (double)a.tau / a.delta);

@@ -19,6 +19,7 @@ struct SmmArgs {
     const double* eps;     // nullable: eps_scalar for every query
     double eps_scalar;
     double lambda, delta;
+    double log_inv_lambda;  // log(1 / lambda) (used for 0 < lambda < 1): Eq. (6)'s denominator
     double log_2tau_delta;  // log(2 tau / delta): Eq. (8)'s logarithm at delta / tau
     int32_t tau, ell_formula, policy, fixed_lb;
     int64_t max_table;     // largest table a query may request (slots)

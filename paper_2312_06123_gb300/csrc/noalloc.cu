@@ -153,6 +153,7 @@ extern "C" int ger_query_batch_dev_noalloc(ger_graph* g, int64_t q, const int32_
     a.eps = eps_dev;
     a.eps_scalar = 0.0;
     a.lambda = lambda;
+    a.log_inv_lambda = a.lambda > 0.0 && a.lambda < 1.0 ? std::log(1.0 / a.lambda) : 0.0;
     a.delta = o.delta;
     a.tau = o.tau;
     a.log_2tau_delta = std::log(2.0 * (double)a.tau / a.delta);

@@ -166,9 +166,10 @@ __device__ __forceinline__ bool setup_query(const SmmArgs& a, int64_t q) {
     } else if (lam <= 0.0) {
         ell = 0;
     } else {
+        // (log(1 / lambda) is the same for every query: computed on the host)
         const double v = a.ell_formula == 1
-                             ? ceil(log(4.0 / (eps - eps * lam)) / log(1.0 / lam) - 1.0)
-                             : ceil(log((2.0 / ds + 2.0 / dt) / (eps * (1.0 - lam))) / log(1.0 / lam) - 1.0);
+                             ? ceil(log(4.0 / (eps - eps * lam)) / a.log_inv_lambda - 1.0)
+                             : ceil(log((2.0 / ds + 2.0 / dt) / (eps * (1.0 - lam))) / a.log_inv_lambda - 1.0);
         ell = v < 0.0 ? 0 : (int64_t)v;
     }
     if (ell < 0) {
