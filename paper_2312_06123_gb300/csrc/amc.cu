@@ -205,6 +205,22 @@ __device__ __forceinline__ double resolve_g(const GEntry* tab, int32_t mask, int
     return 0.0;
 }
 
+// resolve_g for a step whose lookup runs: g is added to z only where v is
+// in the table (no FP64 addition of the zero of an absent node).
+__device__ __forceinline__ void resolve_add(const GEntry* tab, int32_t mask, int32_t v, int4 p, uint32_t h,
+                                            int* err_flag, double& z) {
+    for (uint32_t probe = 0; probe <= (uint32_t)mask; ++probe) {
+        if (p.x == v) {
+            z += __hiloint2double(p.w, p.z);
+            return;
+        }
+        if (p.x == -1) return;
+        h = (h + 1) & (uint32_t)mask;
+        p = __ldg(reinterpret_cast<const int4*>(tab + h));
+    }
+    atomicCAS(err_flag, 0, DERR_FULL);
+}
+
 // W walk pairs per lane pair and round: lanes 2i, 2i+1 walk pairs
 // k0 + i + 16 w (w < W), from s and from t. The W walks of a lane advance in
 // lockstep so that their loads overlap; each step issues the next node's
@@ -362,7 +378,7 @@ __device__ __forceinline__ void walk_chunk(const AmcArgs& a, const WalkQ* WQ, in
                     }
 #pragma unroll
                     for (int i = 0; i < W; ++i) {
-                        if (look[i]) z[i] += resolve_g(tab, mask, nx[i], pr[i], hh[i], a.err_flag);
+                        if (look[i]) resolve_add(tab, mask, nx[i], pr[i], hh[i], a.err_flag, z[i]);
                         w[i] = nx[i];
                     }
                 };

@@ -167,13 +167,15 @@ __host__ __device__ constexpr int pack_k_for(int64_t n) {
     return n <= (int64_t)1 << 16 ? 8 : (n <= (int64_t)1 << 21 ? 6 : (n <= (int64_t)1 << 25 ? 5 : 0));
 }
 
-// Entry e of the packed neighbour lists (one 16-byte load; the entry may
+// Entry e of the packed neighbour lists (one 16-byte load through L2 only:
+// a walk reads edges uniformly, so these loads almost never hit L1 and would
+// only evict the node records and lookup tables there; the entry may
 // straddle two 32-bit words of its unit, never the unit).
 template <int K>
 __device__ __forceinline__ int32_t packed_col(const uint4* cols, uint32_t e) {
     constexpr int B = pack_bits(K);
     const uint32_t u = e / K, j = e - u * K;
-    const uint4 w = __ldg(cols + u);
+    const uint4 w = __ldcg(cols + u);
     const uint32_t o = j * B, wi = o >> 5, sh = o & 31;
     const uint32_t lo = wi == 0 ? w.x : (wi == 1 ? w.y : (wi == 2 ? w.z : w.w));
     const uint32_t hi = wi == 0 ? w.y : (wi == 1 ? w.z : (wi == 2 ? w.w : 0u));
