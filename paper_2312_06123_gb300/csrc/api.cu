@@ -234,6 +234,7 @@ struct ger_graph {
     int32_t dense_nunits = 0, dense_nheavy = 0, dense_nslots = 0;
     bool dense_ready = false;        // SpMM kernels opted into their shared memory
     unsigned short* mlp_w = nullptr; // learned switch: FP16 weights (null: none installed)
+    float* mlp_wt = nullptr;         // learned switch: the same weights in FP32, as the decisions read them
     float* mlp_norm = nullptr;       // learned switch: input mean[6], std[6]
     geer::Workspace ws;
     geer::BatchGraph bg;
@@ -635,6 +636,7 @@ static void make_args(ger_graph* g, const Plan& p, int64_t q0, int64_t nq, bool 
     a.wq = w.wq + q0;
     a.mlp_norm = g->mlp_norm;
     a.mlp_w = p.o.switch_policy == GER_SWITCH_MLP ? g->mlp_w : nullptr;
+    a.mlp_wt = g->mlp_wt;
     a.mlp_at_start = p.o.mlp_at_start != 0;
     a.trace = p.trace ? p.trace + q0 * (int64_t)p.trace_steps * kTraceWidth : nullptr;
     a.trace_steps = p.trace_steps;
@@ -1220,6 +1222,7 @@ void ger_free(ger_graph* g) {
     cudaFree(g->dense_units);
     cudaFree(g->dense_heavy);
     cudaFree(g->mlp_w);
+    cudaFree(g->mlp_wt);
     cudaFree(g->mlp_norm);
     if (g->stream) cudaStreamDestroy(g->stream);
     if (g->stream2) cudaStreamDestroy(g->stream2);
@@ -1498,8 +1501,10 @@ int ger_set_switch_mlp(ger_graph* g, const float* norm, const uint16_t* weights)
     if (!weights) {
         if (g->stream) cudaStreamSynchronize(g->stream);
         cudaFree(g->mlp_w);
+        cudaFree(g->mlp_wt);
         cudaFree(g->mlp_norm);
         g->mlp_w = nullptr;
+        g->mlp_wt = nullptr;
         g->mlp_norm = nullptr;
         return GER_OK;
     }
@@ -1508,16 +1513,22 @@ int ger_set_switch_mlp(ger_graph* g, const float* norm, const uint16_t* weights)
         if (!(norm[kMlpIn + k] > 0.f) || !std::isfinite(norm[k])) return fail(GER_ERR_INVALID, "bad normalisation");
     if (!g->mlp_w) {
         if (cudaMalloc(&g->mlp_w, kMlpParams * sizeof(uint16_t) + 16) != cudaSuccess ||
+            cudaMalloc(&g->mlp_wt, kMlpStaged * sizeof(float)) != cudaSuccess ||
             cudaMalloc(&g->mlp_norm, 2 * kMlpIn * sizeof(float)) != cudaSuccess) {
             cudaGetLastError();
             cudaFree(g->mlp_w);
+            cudaFree(g->mlp_wt);
             g->mlp_w = nullptr;
+            g->mlp_wt = nullptr;
             return fail(GER_ERR_OOM, "switch network");
         }
     }
     if (g->stream) cudaStreamSynchronize(g->stream);
     GER_CUDA(cudaMemcpy(g->mlp_w, weights, kMlpParams * sizeof(uint16_t), cudaMemcpyHostToDevice));
     GER_CUDA(cudaMemcpy(g->mlp_norm, norm, 2 * kMlpIn * sizeof(float), cudaMemcpyHostToDevice));
+    launch_mlp_expand(g->mlp_w, g->mlp_wt, g->stream);
+    GER_CUDA(cudaGetLastError());
+    GER_CUDA(cudaStreamSynchronize(g->stream));
     return GER_OK;
 }
 

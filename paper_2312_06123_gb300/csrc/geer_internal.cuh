@@ -377,10 +377,10 @@ __device__ __forceinline__ int mlp_staged_index(int p) {
     return p;
 }
 
-// The whole CTA converts the network's FP16 weights into FP32 in shared
-// memory (16-byte loads; the weight buffer is allocated with 16 bytes to
-// spare, so the last vector stays inside it; the padding lands past the
-// parameters).
+// The whole CTA converts the network's FP16 weights into the FP32 copy the
+// decisions read (16-byte loads; the weight buffer is allocated with 16
+// bytes to spare, so the last vector stays inside it; the padding lands past
+// the parameters).
 // A thread's loads are issued in groups of kMlpStageGroup before any is
 // converted, so the staging waits for a few round trips, not one per vector.
 constexpr int kMlpStageGroup = 10;
@@ -409,43 +409,120 @@ __device__ __forceinline__ void mlp_stage(float* sw, const unsigned short* w) {
     }
 }
 
-// The network for the query of lane `src` (its raw inputs in that lane's
-// raw[]), evaluated by the whole warp from the staged weights in FP32: lane
-// l computes hidden units l and l + 32 of both layers (four partial sums per
-// dot product of the second), the output is a warp sum. Every lane of the
-// warp must call it; every lane gets the output.
-__device__ __forceinline__ float mlp_eval_warp(const float* sw, const float* norm, const float (&raw)[kMlpIn],
-                                               int src) {
-    const int lane = threadIdx.x & 31;
-    float x[kMlpIn];
+// TF32 bits of x, rounded to nearest (ties away)
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// d += a * b on the tensor cores: one 16x8 tile, k = 8, TF32 operands, FP32
+// accumulation (mma.sync m16n8k8: lane (g, t) = (lane / 4, lane % 4) holds
+// A rows g, g + 8 at columns t, t + 4; B rows t, t + 4 at column g; D rows
+// g, g + 8 at columns 2t, 2t + 1)
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// position of the n-th (0-based) set bit of m, -1 when m has fewer
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
+    for (int i = 0; i < n; ++i) m &= m - 1;
+    return m ? __ffs(m) - 1 : -1;
+}
+
+// The network's output for the query of every lane with `ask` set (the
+// lane's raw inputs in raw[]), the whole warp evaluating 16 queries per
+// pass; the lane gets its own query's output (0 where it did not ask).
+// Every lane of the warp must call it. Weights: the FP32 copy in global
+// memory (mlp_stage's layout). The first layer and the output in FP32 on
+// the CUDA cores; the 64 x 64 second layer on the tensor cores (TF32 mma):
+// the FP16 weights are exact in TF32, and each first-layer activation is
+// split into a TF32 part and a TF32 remainder, so the products are those of
+// FP32 arithmetic (only the order of the sums differs).
+__device__ __forceinline__ float mlp_eval_asked(const float* wt, const float* norm, const float (&raw)[kMlpIn],
+                                                bool ask) {
+    const int lane = threadIdx.x & 31, gq = lane >> 2, tq = lane & 3;
+    unsigned pend = __ballot_sync(0xffffffffu, ask);
+    float mine = 0.f;
+    while (pend) {
+        const int cnt = __popc(pend) < 16 ? __popc(pend) : 16;
+        // the lanes of this pass's rows gq and gq + 8 (a repeat of row 0 past the last)
+        const int first = __ffs(pend) - 1;
+        int sg = nth_set_bit(pend, gq), sh = nth_set_bit(pend, gq + 8);
+        if (gq >= cnt || sg < 0) sg = first;
+        if (gq + 8 >= cnt || sh < 0) sh = first;
+        float xg[kMlpIn], xh[kMlpIn];
 #pragma unroll
-    for (int k = 0; k < kMlpIn; ++k)
-        x[k] = (__shfl_sync(0xffffffffu, raw[k], src) - __ldg(norm + k)) / __ldg(norm + kMlpIn + k);
-    float a = sw[kMlpOffB1 + lane], b = sw[kMlpOffB1 + lane + 32];
-#pragma unroll
-    for (int k = 0; k < kMlpIn; ++k) {
-        a = fmaf(sw[kMlpOffW1 + k * kMlpH + lane], x[k], a);
-        b = fmaf(sw[kMlpOffW1 + k * kMlpH + lane + 32], x[k], b);
-    }
-    a = fmaxf(a, 0.f);
-    b = fmaxf(b, 0.f);
-    float za[4] = {sw[kMlpOffB2 + lane], 0.f, 0.f, 0.f};
-    float zb[4] = {sw[kMlpOffB2 + lane + 32], 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int k = 0; k < kMlpH; k += 4) {
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const float hk = __shfl_sync(0xffffffffu, k + m < 32 ? a : b, (k + m) & 31);
-            za[m] = fmaf(sw[kMlpOffW2 + (k + m) * kMlpH + lane], hk, za[m]);
-            zb[m] = fmaf(sw[kMlpOffW2 + (k + m) * kMlpH + lane + 32], hk, zb[m]);
+        for (int k = 0; k < kMlpIn; ++k) {
+            const float mean = __ldg(norm + k), sd = __ldg(norm + kMlpIn + k);
+            xg[k] = (__shfl_sync(0xffffffffu, raw[k], sg) - mean) / sd;
+            xh[k] = (__shfl_sync(0xffffffffu, raw[k], sh) - mean) / sd;
         }
-    }
-    const float ya = fmaxf((za[0] + za[1]) + (za[2] + za[3]), 0.f);
-    const float yb = fmaxf((zb[0] + zb[1]) + (zb[2] + zb[3]), 0.f);
-    float y = fmaf(sw[kMlpOffW3 + lane], ya, sw[kMlpOffW3 + lane + 32] * yb);
+        // first layer, straight into the A fragments of the second (k-tile n:
+        // hidden units 8n + tq and 8n + tq + 4), as TF32 part and remainder
+        uint32_t ahi[8][4], alo[8][4];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
-    return y + sw[kMlpOffB3];
+        for (int n = 0; n < 8; ++n) {
+            const int c0 = 8 * n + tq, c1 = c0 + 4;
+            float v[4] = {__ldg(wt + kMlpOffB1 + c0), __ldg(wt + kMlpOffB1 + c0), __ldg(wt + kMlpOffB1 + c1),
+                          __ldg(wt + kMlpOffB1 + c1)};
+#pragma unroll
+            for (int k = 0; k < kMlpIn; ++k) {
+                const float w0 = __ldg(wt + kMlpOffW1 + k * kMlpH + c0), w1 = __ldg(wt + kMlpOffW1 + k * kMlpH + c1);
+                v[0] = fmaf(w0, xg[k], v[0]);
+                v[1] = fmaf(w0, xh[k], v[1]);
+                v[2] = fmaf(w1, xg[k], v[2]);
+                v[3] = fmaf(w1, xh[k], v[3]);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float h = fmaxf(v[e], 0.f);
+                ahi[n][e] = to_tf32(h);
+                alo[n][e] = to_tf32(h - __uint_as_float(ahi[n][e]));
+            }
+        }
+        // second layer tile by tile (units 8 nt .. 8 nt + 7), then the output
+        // layer's terms of this lane's two units per row
+        float yg = 0.f, yh = 0.f;
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int kt = 0; kt < 8; ++kt) {
+                // B rows = inputs 8 kt + tq (+ 4), column = unit 8 nt + gq: W2[unit][input]
+                const uint32_t b0 = to_tf32(__ldg(wt + kMlpOffW2 + (8 * kt + tq) * kMlpH + 8 * nt + gq));
+                const uint32_t b1 = to_tf32(__ldg(wt + kMlpOffW2 + (8 * kt + tq + 4) * kMlpH + 8 * nt + gq));
+                mma_tf32(d, ahi[kt], b0, b1);
+                mma_tf32(d, alo[kt], b0, b1);
+            }
+            const int c = 8 * nt + 2 * tq;
+            const float b2a = __ldg(wt + kMlpOffB2 + c), b2b = __ldg(wt + kMlpOffB2 + c + 1);
+            const float w3a = __ldg(wt + kMlpOffW3 + c), w3b = __ldg(wt + kMlpOffW3 + c + 1);
+            yg = fmaf(w3a, fmaxf(d[0] + b2a, 0.f), yg);
+            yg = fmaf(w3b, fmaxf(d[1] + b2b, 0.f), yg);
+            yh = fmaf(w3a, fmaxf(d[2] + b2a, 0.f), yh);
+            yh = fmaf(w3b, fmaxf(d[3] + b2b, 0.f), yh);
+        }
+        // the sums over the quad's 64 units, plus the output bias
+        yg += __shfl_xor_sync(0xffffffffu, yg, 1);
+        yg += __shfl_xor_sync(0xffffffffu, yg, 2);
+        yh += __shfl_xor_sync(0xffffffffu, yh, 1);
+        yh += __shfl_xor_sync(0xffffffffu, yh, 2);
+        const float b3 = __ldg(wt + kMlpOffB3);
+        // each asking lane of this pass takes its row's output (row r: quad r mod 8)
+        const bool in_pass = ((pend >> lane) & 1u) && __popc(pend & ((1u << lane) - 1u)) < cnt;
+        const int r = in_pass ? __popc(pend & ((1u << lane) - 1u)) : 0;
+        const float vg = __shfl_sync(0xffffffffu, yg, (r & 7) * 4);
+        const float vh = __shfl_sync(0xffffffffu, yh, (r & 7) * 4);
+        if (in_pass) mine = (r < 8 ? vg : vh) + b3;
+        // drop this pass's rows
+        const int last = nth_set_bit(pend, cnt - 1);
+        pend = last >= 31 ? 0u : pend & ~((2u << last) - 1u);
+    }
+    return mine;
 }
 
 // The outputs of one query (its record of the batch state): r' and, when

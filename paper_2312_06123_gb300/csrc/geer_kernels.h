@@ -49,6 +49,7 @@ struct SmmArgs {
     // learned switch (policy 1): input normalisation (mean[6], std[6]) and FP16 weights
     const float* mlp_norm = nullptr;
     const unsigned short* mlp_w = nullptr;  // null: no network, the rule of Eq. (17) decides
+    const float* mlp_wt = nullptr;          // the same weights in FP32, W1 and W2 transposed (mlp_stage's layout)
     int32_t mlp_at_start = 0;               // also consult the network before the first SMM iteration
     // cost log: per query and SMM iteration 1..trace_steps, kTraceWidth floats
     float* trace = nullptr;
@@ -201,6 +202,8 @@ namespace geer {
 // accessors of api.cu for entry points in other translation units
 int graph_view(const ger_graph* g, DevGraph* dg, double* lambda, bool* has_lambda, int* device, int* sm_count);
 int set_error(int code, const char* msg);
+// The FP32 copy of a switch network's FP16 weights that the decisions read.
+void launch_mlp_expand(const unsigned short* w, float* out, cudaStream_t st);
 void launch_finalize(const QState* st, int64_t nq, double* r, ger_query_stats* stats, cudaStream_t s);
 
 }  // namespace geer

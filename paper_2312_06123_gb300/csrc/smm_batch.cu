@@ -422,17 +422,12 @@ __device__ __forceinline__ StartState start_query(const SmmArgs& a, int64_t q, b
 
 template <typename T>
 __global__ void smm_start_kernel(SmmArgs a) {
-    extern __shared__ float sw[];  // the staged network when it decides at l_b = 0
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctl->iter = 0;
         a.ctl->lo[0] = 0;
         a.ctl->hi[0] = (int64_t)kF0Slots * a.nq;
     }
     const bool learned = a.policy == 1 && a.mlp_w != nullptr && a.mlp_at_start;
-    if (learned) {
-        mlp_stage(sw, a.mlp_w);
-        __syncthreads();
-    }
     // a loop of the same trip count for every thread: the network is evaluated by the whole warp
     static_assert(kQueryCta == 32, "one warp per CTA");
     for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < a.nq; base += (int64_t)gridDim.x * blockDim.x) {
@@ -440,11 +435,8 @@ __global__ void smm_start_kernel(SmmArgs a) {
         StartState S;
         if (q < a.nq) S = start_query<T>(a, q, learned);
         if (learned) {
-            for (unsigned pend = __ballot_sync(0xffffffffu, S.ask); pend; pend &= pend - 1) {
-                const int src = __ffs(pend) - 1;
-                const float y = mlp_eval_warp(sw, a.mlp_norm, S.f, src);
-                if ((int)(threadIdx.x & 31) == src) S.go = y < 0.f;
-            }
+            const float y = mlp_eval_asked(a.mlp_wt, a.mlp_norm, S.f, S.ask);
+            if (S.ask) S.go = y < 0.f;
         }
         if (!S.smm) continue;
         QState* Q = a.st + q;
@@ -452,6 +444,14 @@ __global__ void smm_start_kernel(SmmArgs a) {
         if (S.go) continue_smm(a, q, Q, M, 0, S.vol);
         else leave_smm(a, q, Q, M, 0, 0, S.ell, S.psi, (double)S.vol, S.h, S.eta0, 2);
     }
+}
+
+// The FP32 copy of the switch network's weights (one CTA).
+__global__ void mlp_expand_kernel(const unsigned short* w, float* out) { mlp_stage(out, w); }
+
+void launch_mlp_expand(const unsigned short* w, float* out, cudaStream_t st) {
+    mlp_expand_kernel<<<1, 256, 0, st>>>(w, out);
+    note_launches(1);
 }
 
 constexpr int64_t kLightMax = 128;  // neighbours a single warp pushes
@@ -672,12 +672,10 @@ __global__ void __launch_bounds__(256) smm_top2_kernel(SmmArgs a) {
 // switch, the CTA stages the network's weights in shared memory once some
 // query of it needs the network (where Eq. (17) continues).
 __global__ void smm_decide_kernel(SmmArgs a) {
-    extern __shared__ float sw[];  // kMlpStaged floats with a learned switch, else none
     const int iter = a.ctl->iter;
     const bool learned = iter > 0 && a.policy == 1 && a.mlp_w != nullptr;
-    bool staged = false;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // a loop of the same trip count for every thread of the CTA (the staging is CTA-wide)
+    // a loop of the same trip count for every thread of the CTA (the network is evaluated by the whole warp)
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < a.nq; base += stride) {
         const int64_t q = base + threadIdx.x;
         const bool active = q < a.nq && a.sm[q].run && a.st[q].status == ST_SMM;
@@ -720,18 +718,10 @@ __global__ void smm_decide_kernel(SmmArgs a) {
                 }
             }
         }
-        if (learned && __syncthreads_or(need)) {
-            if (!staged) {
-                mlp_stage(sw, a.mlp_w);
-                __syncthreads();
-                staged = true;
-            }
+        if (learned) {
             // the network of each query that needs it, by the whole warp (the CTA)
-            for (unsigned pend = __ballot_sync(0xffffffffu, need); pend; pend &= pend - 1) {
-                const int src = __ffs(pend) - 1;
-                const float y = mlp_eval_warp(sw, a.mlp_norm, f, src);
-                if ((int)(threadIdx.x & 31) == src && y >= 0.f) go = false;
-            }
+            const float y = mlp_eval_asked(a.mlp_wt, a.mlp_norm, f, need);
+            if (need && y >= 0.f) go = false;
         }
         if (!active) continue;
         // the table just finished holds the current frontier
@@ -805,10 +795,9 @@ void launch_smm_setup(const SmmArgs& a, cudaStream_t st) {
 
 void launch_smm_start(bool fp64, const SmmArgs& a, cudaStream_t st) {
     const int grid = query_grid(a.nq);
-    const size_t smem = (a.policy == 1 && a.mlp_w && a.mlp_at_start) ? kMlpStaged * sizeof(float) : 0;
     prof_begin(FAM_SMM_SETUP, st);
-    if (fp64) smm_start_kernel<double><<<grid, kQueryCta, smem, st>>>(a);
-    else smm_start_kernel<float><<<grid, kQueryCta, smem, st>>>(a);
+    if (fp64) smm_start_kernel<double><<<grid, kQueryCta, 0, st>>>(a);
+    else smm_start_kernel<float><<<grid, kQueryCta, 0, st>>>(a);
     prof_end(FAM_SMM_SETUP, st);
     note_launches(1);
 }
@@ -844,9 +833,8 @@ void launch_smm_top2(bool fp64, const SmmArgs& a, int grid, cudaStream_t st) {
 void launch_smm_decide(const SmmArgs& a, cudaStream_t st, bool first) {
     const int grid = query_grid(a.nq);
     (void)first;
-    const size_t smem = (a.policy == 1 && a.mlp_w) ? kMlpStaged * sizeof(float) : 0;
     prof_begin(FAM_SMM_DECIDE, st);
-    smm_decide_kernel<<<grid, kQueryCta, smem, st>>>(a);
+    smm_decide_kernel<<<grid, kQueryCta, 0, st>>>(a);
     prof_end(FAM_SMM_DECIDE, st);
     note_launches(1);
 }
