@@ -320,7 +320,7 @@ __device__ __forceinline__ void switch_quantities(int64_t lf, double s1, double 
     const double up = (double)((lf + 1) / 2), dn = (double)(lf / 2);
     const double p = 2.0 * up * (s1 / ds + t1 / dt) + 2.0 * dn * (s2 / ds + t2 / dt);
     const double es = 2.0 * p * p * log_2tau_delta / (eps * eps);
-    int64_t e0 = (int64_t)ceil(es / ldexp(1.0, tau - 1));
+    int64_t e0 = (int64_t)ceil(es * ldexp(1.0, 1 - tau));  // (scaling by a power of two is exact)
     if (e0 < 1) e0 = 1;
     *psi = p;
     *eta0 = e0;

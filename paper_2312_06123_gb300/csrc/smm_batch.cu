@@ -256,8 +256,8 @@ __device__ __forceinline__ void leave_smm(const SmmArgs& a, int64_t q, QState* Q
         wr->mask = Q->table_mask;
         wr->dstride = Q->dense_stride;
         wr->dvals = Q->dense_vals;
-        wr->inv_ds = 1.0 / (double)Q->ds;
-        wr->inv_dt = 1.0 / (double)Q->dt;
+        wr->inv_ds = M->inv_ds;
+        wr->inv_dt = M->inv_dt;
         wr->filt = (!M->dense && M->tab_cap <= kFilterSlots) ? M->filt[lb & 1] : nullptr;
     } else {
         Q->status = ST_DONE;
@@ -403,7 +403,8 @@ __device__ __forceinline__ StartState start_query(const SmmArgs& a, int64_t q, b
     M->filt[0][bs >> 5] |= 1u << (bs & 31u);
     M->filt[0][bt >> 5] |= 1u << (bt & 31u);
     // Algorithm 2 at i = 0: s*(s)/d(s) + t*(t)/d(t) - s*(t)/d(s) - t*(s)/d(t)
-    Q->r_b = 1.0 / ds + 1.0 / dt - 0.0 / ds - 0.0 / dt;
+    // (1/d(s), 1/d(t) by the set-up's divisions; the zero terms subtract +0)
+    Q->r_b = M->inv_ds + M->inv_dt;
     S.ell = Q->ell;
     S.vol = (unsigned long long)Q->ds + (unsigned long long)Q->dt;
     // Eq. (9) and h(l) at l_b = 0: max_1 = 1 and max_2 = 0 for both vectors
