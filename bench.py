@@ -41,7 +41,7 @@ SPMM_TRAFFIC: dict = {("c2", 128): 6_261_000_000 + 501_000_000}
 # workload's batch switching after one SMM iteration, the learned switch's choice on this workload,
 # divided by their walk steps). A workload missing here, or a kernel changed since its capture,
 # reports its traffic as null.
-WALK_TRAFFIC_PER_STEP: dict = {"c2": (193_202_944 + 3_296_512) / 25_144_286}
+WALK_TRAFFIC_PER_STEP: dict = {"c2": (193_264_128 + 3_280_384) / 25_144_286}
 
 
 def _peaks():
