@@ -364,8 +364,8 @@ __device__ __forceinline__ void switch_features(int32_t ds, int32_t dt, int64_t 
     f[5] = (float)s1 / fds + (float)t1 / fdt;
 }
 
-// Floats of the network's weights staged in shared memory (a whole number of
-// 16-byte FP16 vectors).
+// Floats of the network's FP32 weight copy (a whole number of 16-byte FP16
+// vectors).
 constexpr int kMlpStaged = (kMlpParams + 7) / 8 * 8;
 
 // Where parameter p sits in the staged copy: W1 and W2 transposed (input k
